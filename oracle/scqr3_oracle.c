@@ -1,0 +1,222 @@
+/*
+ * scqr3_oracle.c -- plain FP64 CPU reference of shifted CholeskyQR3.
+ *
+ * TEST INFRASTRUCTURE ONLY: used by tests/, __graft_entry__.smoke() and the
+ * CPU legs of bench.py to check and time the CUDA library; never by the
+ * library itself. It shares no code with the CUDA path.
+ *
+ * Every routine is the textbook loop for the formula it cites, written for
+ * a reader checking it against the paper: no blocking, no reordering, no
+ * fused multiply-add (built with -ffp-contract=off).
+ */
+#include "scqr3_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Unit roundoff of IEEE binary64 (Sec. 6: u = 2^-53). */
+static const double ORC_U = 1.1102230246251565e-16;
+
+void orc_gram(int64_t m, int n, const double *X, int64_t ldx, double *A) {
+  /* a_jk = sum_i x_ij x_ik (Eq. gram). Rows are visited in ascending i, so
+   * every entry is the plain left-to-right sum of its m products. */
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) A[j * n + k] = 0.0;
+  for (int64_t i = 0; i < m; ++i) {
+    const double *x = X + i * ldx;
+    for (int j = 0; j < n; ++j)
+      for (int k = j; k < n; ++k) A[j * n + k] = A[j * n + k] + x[j] * x[k];
+  }
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < j; ++k) A[j * n + k] = A[k * n + j];
+}
+
+void orc_gram_oblique(int64_t m, int n, const double *X, int64_t ldx, int bs,
+                      const double *Bblk, double *A, double *fro2) {
+  /* A = X^T Y with Y = B X formed explicitly (Sec. 7.2 describes forming
+   * Y := B X and then X^T Y). B is block diagonal: y_i = sum over the rows
+   * l of i's block of b_il x_l. */
+  double *y = (double *)malloc(sizeof(double) * (size_t)n);
+  double f = 0.0;
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) A[j * n + k] = 0.0;
+  for (int64_t i = 0; i < m; ++i) {
+    const int64_t blk = i / bs;
+    const int r = (int)(i - blk * bs);
+    const double *b = Bblk + blk * (int64_t)bs * bs + (int64_t)r * bs;
+    for (int k = 0; k < n; ++k) {
+      double t = 0.0;
+      for (int l = 0; l < bs; ++l) t = t + b[l] * X[(blk * bs + l) * ldx + k];
+      y[k] = t;
+    }
+    const double *x = X + i * ldx;
+    for (int j = 0; j < n; ++j) {
+      f = f + x[j] * x[j];
+      for (int k = j; k < n; ++k) A[j * n + k] = A[j * n + k] + x[j] * y[k];
+    }
+  }
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < j; ++k) A[j * n + k] = A[k * n + j];
+  if (fro2) *fro2 = f;
+  free(y);
+}
+
+double orc_shift(int64_t m, int n, double normx2) {
+  /* Eq. (finds2). */
+  const double mn = (double)m * (double)n;
+  const double nn1 = (double)n * (double)(n + 1);
+  return 11.0 * (mn + nn1) * ORC_U * normx2;
+}
+
+double orc_shift_oblique(int64_t m, int n, double normx2, double normb) {
+  /* Eq. (finds2B). */
+  const double dm = (double)m;
+  const double t = 2.0 * dm * sqrt(dm * (double)n);
+  const double nn1 = (double)n * (double)(n + 1);
+  return 11.0 * (t + nn1) * ORC_U * normx2 * normb;
+}
+
+int orc_chol(int n, const double *A, double s, double *R) {
+  /* R^T R = A + sI: for column j, r_jj = sqrt(a_jj + s - sum_{k<j} r_kj^2)
+   * and r_jl = (a_jl - sum_{k<j} r_kj r_kl) / r_jj for l > j. */
+  for (int j = 0; j < n * n; ++j) R[j] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j] + s;
+    for (int k = 0; k < j; ++k) d = d - R[k * n + j] * R[k * n + j];
+    if (!(d > 0.0) || !isfinite(d)) return j + 1;
+    const double rjj = sqrt(d);
+    R[j * n + j] = rjj;
+    for (int l = j + 1; l < n; ++l) {
+      double t = A[j * n + l];
+      for (int k = 0; k < j; ++k) t = t - R[k * n + j] * R[k * n + l];
+      R[j * n + l] = t / rjj;
+    }
+  }
+  return 0;
+}
+
+void orc_trsm(int64_t m, int n, const double *X, int64_t ldx, const double *R,
+              double *Q, int64_t ldq) {
+  /* q_i^T R = x_i^T, i.e. x_ij = sum_{k<=j} q_ik r_kj, solved for
+   * j = 0, 1, ... in turn: q_ij = (x_ij - sum_{k<j} q_ik r_kj) / r_jj. */
+  for (int64_t i = 0; i < m; ++i) {
+    const double *x = X + i * ldx;
+    double *q = Q + i * ldq;
+    for (int j = 0; j < n; ++j) {
+      double t = x[j];
+      for (int k = 0; k < j; ++k) t = t - q[k] * R[k * n + j];
+      q[j] = t / R[j * n + j];
+    }
+  }
+}
+
+void orc_trmm(int n, const double *Rt, double *R) {
+  /* (Rt R)_ij = sum_{i<=k<=j} rt_ik r_kj for i <= j; the product of two
+   * upper triangular matrices is upper triangular. */
+  double *P = (double *)calloc((size_t)n * n, sizeof(double));
+  for (int i = 0; i < n; ++i)
+    for (int j = i; j < n; ++j) {
+      double t = 0.0;
+      for (int k = i; k <= j; ++k) t = t + Rt[i * n + k] * R[k * n + j];
+      P[i * n + j] = t;
+    }
+  memcpy(R, P, sizeof(double) * (size_t)n * n);
+  free(P);
+}
+
+double orc_normb_bound(int64_t m, int bs, const double *Bblk) {
+  /* ||B||_2 = max_j ||B_j||_2 <= max_j ||B_j||_F. */
+  double best = 0.0;
+  const int64_t nb = m / bs;
+  for (int64_t j = 0; j < nb; ++j) {
+    const double *b = Bblk + j * (int64_t)bs * bs;
+    double f = 0.0;
+    for (int l = 0; l < bs * bs; ++l) f = f + b[l] * b[l];
+    f = sqrt(f);
+    if (f > best) best = f;
+  }
+  return best;
+}
+
+int orc_scqr3(int64_t m, int n, const double *X, int64_t ldx, int bs,
+              const double *Bblk, double normx2, double normb, int max_passes,
+              double *Q, int64_t ldq, double *R, orc_trace *trace) {
+  if (m < n || n < 1 || ldx < n || ldq < n || max_passes < 3 ||
+      max_passes > ORC_MAX_PASSES || (bs > 0 && (m % bs) != 0))
+    return ORC_E_ARG;
+  const int oblique = bs > 0;
+  if (oblique && !(normb > 0.0)) normb = orc_normb_bound(m, bs, Bblk);
+
+  double *A = (double *)malloc(sizeof(double) * (size_t)n * n);
+  double *Rt = (double *)malloc(sizeof(double) * (size_t)n * n);
+  orc_trace tr;
+  memset(&tr, 0, sizeof(tr));
+  int status = ORC_E_MAXPASS;
+
+  /* Alg. 2 line 1 / Alg. 3 line 1: Q := X, R := I. */
+  if (Q != X)
+    for (int64_t i = 0; i < m; ++i)
+      memcpy(Q + i * ldq, X + i * ldx, sizeof(double) * (size_t)n);
+  for (int i = 0; i < n * n; ++i) R[i] = 0.0;
+  for (int i = 0; i < n; ++i) R[i * n + i] = 1.0;
+
+  int plain_in_a_row = 0;
+  for (int p = 0; p < max_passes; ++p) {
+    /* A := Q^T Q (or Q^T B Q); ||Q||^2 is estimated by ||Q||_F^2, which
+     * for B = I is the trace of the computed Gram matrix (Sec. 4.1). */
+    double nrm2 = 0.0;
+    if (oblique) {
+      orc_gram_oblique(m, n, Q, ldq, bs, Bblk, A, &nrm2);
+    } else {
+      orc_gram(m, n, Q, ldq, A);
+      for (int j = 0; j < n; ++j) nrm2 = nrm2 + A[j * n + j];
+    }
+    if (!isfinite(nrm2)) {
+      status = ORC_E_NONFINITE;
+      break;
+    }
+    if (p == 0 && normx2 > 0.0) nrm2 = normx2;
+    tr.norm2[p] = nrm2;
+
+    /* Pass 1 always shifts (Alg. 3 lines 3-4). Later passes try the plain
+     * Cholesky and shift only if it breaks down (Alg. 2 lines 4-8). */
+    int shifted = (p == 0);
+    if (!shifted) {
+      const int fail = orc_chol(n, A, 0.0, Rt);
+      tr.unshifted_fail[p] = fail;
+      shifted = (fail != 0);
+    }
+    double s = 0.0;
+    if (shifted) {
+      s = oblique ? orc_shift_oblique(m, n, nrm2, normb) : orc_shift(m, n, nrm2);
+      const int fail = orc_chol(n, A, s, Rt);
+      if (fail) {
+        tr.passes = p + 1;
+        tr.shifted[p] = 1;
+        tr.s[p] = s;
+        status = fail;
+        break;
+      }
+    }
+    tr.shifted[p] = shifted;
+    tr.s[p] = s;
+    tr.passes = p + 1;
+
+    /* Q := Q Rt^{-1}, R := Rt R (Alg. 2 line 9). */
+    orc_trsm(m, n, Q, ldq, Rt, Q, ldq);
+    orc_trmm(n, Rt, R);
+
+    /* Two plain CholeskyQR passes after the last shifted one complete
+     * CholeskyQR2 (Alg. 3 lines 6-7). */
+    plain_in_a_row = shifted ? 0 : plain_in_a_row + 1;
+    if (plain_in_a_row == 2) {
+      status = ORC_OK;
+      break;
+    }
+  }
+  if (trace) *trace = tr;
+  free(A);
+  free(Rt);
+  return status;
+}

@@ -1,0 +1,379 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test targets a mistake that could plausibly hide in the oracle (a
+dropped term of the shift, a transposed Gram, a wrong TRSM index, a reversed
+R accumulation, ...). None of them compares the oracle with itself.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_11085_gb300.testmat import (block_diag_spd, dense_spd, geometric_sigma,
+                                            repeated_small_sigma, testmat, testmat_factors)
+
+U = 2.0 ** -53
+
+
+def orth2(Q):
+    n = Q.shape[1]
+    return np.linalg.norm(Q.T @ Q - np.eye(n), 2)
+
+
+def resid(X, Q, R):
+    return np.linalg.norm(X - Q @ R) / np.linalg.norm(X)
+
+
+def signfix_qr(Y):
+    """Householder QR (LAPACK) with diag(R) > 0: the unique QR factorization."""
+    Qh, Rh = np.linalg.qr(Y)
+    d = np.sign(np.diag(Rh))
+    d[d == 0] = 1.0
+    return Qh * d, Rh * d[:, None]
+
+
+# --------------------------------------------------------------------------- building blocks, exact
+
+def test_gram_exact_on_integers():
+    rng = np.random.default_rng(0)
+    X = rng.integers(-50, 51, size=(173, 7)).astype(np.float64)
+    A = oracle.gram(X)
+    Xi = X.astype(np.int64)
+    assert np.array_equal(A, (Xi.T @ Xi).astype(np.float64))
+    # a non-square, non-symmetric-looking input: X^T X is n x n, not m x m
+    assert A.shape == (7, 7)
+
+
+def test_gram_oblique_exact_on_integers():
+    rng = np.random.default_rng(1)
+    bs, nb, n = 4, 9, 5
+    X = rng.integers(-9, 10, size=(bs * nb, n)).astype(np.float64)
+    G = rng.integers(-3, 4, size=(nb, bs, bs))
+    Bblk = (np.einsum("kij,kil->kjl", G, G) + np.eye(bs)[None]).astype(np.float64)
+    A, fro2 = oracle.gram_oblique(X, Bblk)
+    Bfull = np.zeros((bs * nb, bs * nb), dtype=np.int64)
+    for k in range(nb):
+        Bfull[k * bs:(k + 1) * bs, k * bs:(k + 1) * bs] = Bblk[k].astype(np.int64)
+    Xi = X.astype(np.int64)
+    assert np.array_equal(A, (Xi.T @ Bfull @ Xi).astype(np.float64))
+    assert fro2 == float((Xi * Xi).sum())
+
+
+def _int_upper(n, rng, diag=(1.0, 2.0, 4.0)):
+    """Upper triangular with power-of-two diagonal: substitution and Cholesky are exact."""
+    R = np.triu(rng.integers(-4, 5, size=(n, n))).astype(np.float64)
+    R[np.diag_indices(n)] = rng.choice(diag, size=n)
+    return R
+
+
+def test_chol_exact_and_shift_added_to_diagonal():
+    rng = np.random.default_rng(2)
+    for n in (1, 2, 5, 11):
+        R = _int_upper(n, rng)
+        A = R.T @ R
+        Rc, fail = oracle.chol(A)
+        assert fail == 0 and np.array_equal(Rc, R)
+        # chol(A' + sI) with A' = A - sI must give back R: the shift goes on the diagonal
+        Rc2, fail2 = oracle.chol(A - 0.5 * np.eye(n), 0.5)
+        assert fail2 == 0 and np.array_equal(Rc2, R)
+        assert np.array_equal(np.tril(Rc, -1), np.zeros((n, n)))
+
+
+def test_chol_breakdown_column():
+    A = np.diag([4.0, 1.0, -1.0, 2.0])
+    _, fail = oracle.chol(A)
+    assert fail == 3
+    _, fail = oracle.chol(A, 2.0)  # shift makes it SPD
+    assert fail == 0
+    A2 = np.eye(3)
+    A2[1, 1] = np.nan
+    assert oracle.chol(A2)[1] == 2
+    # exactly singular: radicand 0 counts as breakdown
+    v = np.array([[1.0, 1.0], [1.0, 1.0]])
+    assert oracle.chol(v)[1] == 2
+
+
+def test_trsm_exact_on_integers():
+    rng = np.random.default_rng(3)
+    for n in (1, 3, 8, 17):
+        R = _int_upper(n, rng)
+        Qi = rng.integers(-20, 21, size=(41, n)).astype(np.float64)
+        X = Qi @ R
+        assert np.array_equal(oracle.trsm(X, R), Qi)
+
+
+def test_trmm_exact_on_integers():
+    rng = np.random.default_rng(4)
+    n = 9
+    A = np.triu(rng.integers(-5, 6, size=(n, n))).astype(np.float64)
+    B = np.triu(rng.integers(-5, 6, size=(n, n))).astype(np.float64)
+    assert np.array_equal(oracle.trmm(A, B), (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64))
+
+
+# --------------------------------------------------------------------------- shift, pinned by printed values
+
+@pytest.mark.parametrize("key", ["table1", "table2"])
+def test_pass1_condition_matches_printed_table(golden, key):
+    """kappa_2(Q^(1)) printed in Tables 1-2 pins Eq. (finds2): both the mn and
+    the n(n+1) terms and the factor 11 (Table 2 has m = n, so dropping n(n+1)
+    would be off by 30%)."""
+    g = golden[key]
+    m, n, kappa = g["m"], g["n"], g["kappa"]
+    X = testmat(m, n, kappa, seed=11)
+    s = oracle.shift(m, n, 1.0)  # ||X||_2 = 1 by construction
+    R1, fail = oracle.chol(oracle.gram(X), s)
+    assert fail == 0
+    k1 = np.linalg.cond(oracle.trsm(X, R1))
+    assert abs(k1 / g["kappa_Q"][0] - 1.0) < 0.01
+
+
+def test_shift_remark_value(golden):
+    """The remark's ~6.1e-11 (m=1000, n=50) is 11 mn u; the formula with
+    n(n+1) gives 6.42e-11. The 5% gap is the paper's rounding of its own
+    example; we follow the formula (Eq. finds2), which Tables 1-2 confirm."""
+    g = golden["shift_remark"]
+    s = oracle.shift(g["m"], g["n"], 1.0)
+    assert 1.0 < s / g["s_printed"] < 1.07
+
+
+def test_oblique_shift_matches_table3(golden):
+    """Table 3's sqrt(alpha kappa_2(B)) = 8.41e-2 pins Eq. (finds2B)."""
+    g = golden["table3"]
+    alpha = oracle.shift_oblique(g["m"], g["n"], 1.0, 1.0)
+    assert abs(np.sqrt(alpha * g["kappa_b"]) / g["sqrt_alpha_kappa_b"] - 1.0) < 0.005
+    # scaling: s is linear in ||X||^2 and in ||B||
+    assert oracle.shift_oblique(300, 30, 3.0, 5.0) == pytest.approx(15.0 * alpha, rel=1e-15)
+    assert oracle.shift(77, 5, 2.5) == pytest.approx(2.5 * oracle.shift(77, 5, 1.0), rel=1e-15)
+
+
+# --------------------------------------------------------------------------- per-pass behaviour (Tables 1-3)
+
+@pytest.mark.parametrize("key", ["table1", "table2"])
+def test_per_pass_magnitudes_tables_1_2(golden, key):
+    g = golden[key]
+    m, n, kappa = g["m"], g["n"], g["kappa"]
+    X = testmat(m, n, kappa, seed=12)
+    Q, R, st, tr = oracle.scqr3(X, normx2=1.0)
+    assert st == 0 and tr["passes"] == 3 and tr["shifted"] == [1, 0, 0]
+    # replay the three passes with the building blocks to look at each iterate
+    Qk = X.copy()
+    for p in range(3):
+        Rt, fail = oracle.chol(oracle.gram(Qk), tr["s"][p])
+        assert fail == 0
+        Qk = oracle.trsm(Qk, Rt)
+        o = orth2(Qk)
+        want = g["orth2"][p]
+        if p == 0:
+            assert 0.9 < o < 1.0 + 1e-6  # ||Q^T Q - I||_2 = 1 - lambda_min
+        elif p == 1:
+            assert want / 30 < o < want * 30
+        else:
+            assert o < 10 * want and o < 1e-14
+        if p >= 1:
+            assert np.linalg.cond(Qk) < 1.2
+    assert np.array_equal(Qk, Q)
+
+
+def test_per_pass_magnitudes_table3(golden):
+    g = golden["table3"]
+    m, n = g["m"], g["n"]
+    X = testmat(m, n, g["kappa_x"], seed=13)
+    B = dense_spd(m, g["kappa_b"], seed=14)
+    Bblk = B[None]
+    sB = np.linalg.svd(B, compute_uv=False)
+    Bh = (np.linalg.eigh(B)[1] * np.sqrt(np.linalg.eigvalsh(B))) @ np.linalg.eigh(B)[1].T
+
+    def measure(Qk):
+        smin = np.linalg.svd(Bh @ Qk, compute_uv=False).min()
+        return np.linalg.norm(Qk, 2) * np.sqrt(sB.max()) / smin
+
+    Q, R, st, tr = oracle.scqr3(X, Bblk, normx2=1.0, normb=float(sB.max()))
+    assert st == 0 and tr["passes"] == 3
+    Qk = X.copy()
+    for p in range(3):
+        A, _ = oracle.gram_oblique(Qk, Bblk)
+        Rt, fail = oracle.chol(A, tr["s"][p])
+        assert fail == 0
+        Qk = oracle.trsm(Qk, Rt)
+        mk = measure(Qk)
+        assert g["measure"][p] / 3 < mk < g["measure"][p] * 3
+        ob = np.linalg.norm(Qk.T @ B @ Qk - np.eye(n), 2)
+        if p == 1:
+            assert g["orth2_b"][1] / 30 < ob < 1.0
+        if p == 2:
+            assert ob < 10 * g["orth2_b"][2]
+    assert resid(X, Q, R) < 16 * n * n * U * np.sqrt(g["kappa_b"]) ** 3
+
+
+# --------------------------------------------------------------------------- closed forms and invariants
+
+@pytest.mark.parametrize("kappa", [1e6, 1e9, 1e12, 1e14])
+def test_pass1_condition_closed_form(kappa):
+    """In exact arithmetic R1^T R1 = V(S^2 + sI)V^T, so the singular values of
+    X R1^{-1} are sigma_i / sqrt(sigma_i^2 + s) (Thm. on kappa reduction)."""
+    m, n = 500, 12
+    Uf, sig, V = testmat_factors(m, n, kappa, seed=21)
+    X = (Uf * sig) @ V.T
+    s = oracle.shift(m, n, 1.0)
+    R1, fail = oracle.chol(oracle.gram(X), s)
+    assert fail == 0
+    sv = sig / np.sqrt(sig ** 2 + s)
+    want = sv.max() / sv.min()
+    got = np.linalg.cond(oracle.trsm(X, R1))
+    assert abs(got / want - 1.0) < 0.05
+    # bound of Thm. (eq:kap2): kappa(Q1) <= 2 sqrt(3) sqrt(1 + alpha kappa^2)
+    assert got <= 2 * np.sqrt(3) * np.sqrt(1 + s * kappa ** 2)
+
+
+@pytest.mark.parametrize("m,n", [(300, 10), (1000, 30), (64, 64), (2000, 7)])
+@pytest.mark.parametrize("kappa", [1e2, 1e8, 1e12, 1e15])
+def test_end_to_end_bounds(m, n, kappa):
+    """Thm. (maincholqr3): ||Q^T Q - I||_F <= 6{mn + n(n+1)}u and
+    ||QR - X||_F / ||X||_2 <= 15 n^2 u; R upper triangular, diag(R) > 0."""
+    X = testmat(m, n, kappa, seed=int(np.log10(kappa)) * 7 + n)
+    Q, R, st, tr = oracle.scqr3(X)
+    assert st == 0
+    assert np.array_equal(np.tril(R, -1), np.zeros((n, n)))
+    assert (np.diag(R) > 0).all()
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 6 * (m * n + n * (n + 1)) * U
+    assert np.linalg.norm(Q @ R - X) / np.linalg.norm(X, 2) <= 15 * n * n * U
+    assert tr["shifted"][0] == 1 and tr["shifted"][-2:] == [0, 0]
+
+
+@pytest.mark.parametrize("kappa", [1e1, 1e4, 1e8])
+@pytest.mark.parametrize("m,n", [(50, 50), (200, 13), (300, 32)])
+def test_matches_householder_qr(m, n, kappa):
+    """Brute force: the QR factorization with diag(R) > 0 is unique; LAPACK's
+    Householder QR gives it to within kappa*u."""
+    X = testmat(m, n, kappa, seed=31 + n)
+    Q, R, st, _ = oracle.scqr3(X)
+    assert st == 0
+    Qh, Rh = signfix_qr(X)
+    tol = 50 * n * kappa * U
+    assert np.linalg.norm(R - Rh) / np.linalg.norm(Rh) < tol
+    assert np.linalg.norm(Q - Qh) < tol * np.sqrt(n)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e8])
+def test_R_equals_R_factor_of_sigma_vt(kappa):
+    """X = U S V^T with orthonormal U gives R = R-factor of S V^T exactly."""
+    m, n = 3000, 24
+    Uf, sig, V = testmat_factors(m, n, kappa, seed=41)
+    X = (Uf * sig) @ V.T
+    _, R, st, _ = oracle.scqr3(X)
+    assert st == 0
+    _, Rx = signfix_qr(sig[:, None] * V.T)
+    assert np.linalg.norm(R - Rx) / np.linalg.norm(Rx) < 100 * n * kappa * U
+
+
+def test_accumulation_order_R_is_Rtilde_times_R():
+    """R := Rt R (Alg. 2 line 9): the reversed product would break X = QR."""
+    X = testmat(400, 9, 1e11, seed=5)
+    Q, R, st, tr = oracle.scqr3(X)
+    assert st == 0 and tr["passes"] >= 3
+    assert resid(X, Q, R) < 1e-15 * 9
+
+
+def test_q_may_alias_x_and_trace_values():
+    X = testmat(256, 16, 1e10, seed=6)
+    Q, R, st, tr = oracle.scqr3(X.copy())
+    assert tr["s"][0] == pytest.approx(oracle.shift(256, 16, np.trace(X.T @ X)), rel=1e-12)
+    assert tr["s"][1:] == [0.0] * (tr["passes"] - 1)
+
+
+# --------------------------------------------------------------------------- Alg. 2 breakdown rule
+
+def test_extra_shifted_pass_when_cholqr_breaks_down():
+    """kappa = 1e15 at m=20000, n=32: kappa(Q1) ~ sqrt(alpha) kappa ~ 1e11 >
+    u^{-1/2}, so the plain Cholesky of pass 2 breaks down and Alg. 2 shifts
+    again; two plain passes then finish."""
+    m, n = 20000, 32
+    X = testmat(m, n, 1e15, seed=7)
+    Q, R, st, tr = oracle.scqr3(X)
+    assert st == 0
+    assert tr["passes"] == 4 and tr["shifted"] == [1, 1, 0, 0]
+    assert tr["unshifted_fail"][1] > 0
+    # recursive summation over 20000 rows: about sqrt(m) u in practice
+    assert orth2(Q) < 1e-13 and resid(X, Q, R) < 1e-15
+
+
+def test_repeated_small_singular_values():
+    m, n = 5000, 32
+    X = testmat(m, n, 0.0, seed=8, sigma=repeated_small_sigma(n, 8, 1e-14, 1e7))
+    Q, R, st, tr = oracle.scqr3(X)
+    assert st == 0 and tr["shifted"][0] == 1
+    assert orth2(Q) < 1e-13 and resid(X, Q, R) < 1e-15
+
+
+def test_max_passes_reported():
+    m, n = 20000, 32
+    X = testmat(m, n, 1e15, seed=7)
+    _, _, st, tr = oracle.scqr3(X, max_passes=3)
+    assert st == oracle.E_MAXPASS and tr["passes"] == 3
+
+
+def test_argument_and_input_errors():
+    X = np.ones((4, 5))
+    assert oracle.scqr3(X)[2] == oracle.E_ARG  # m < n
+    X = testmat(50, 4, 10.0, seed=9)
+    X[3, 2] = np.nan
+    assert oracle.scqr3(X)[2] == oracle.E_NONFINITE
+    Z = testmat(50, 4, 10.0, seed=9)
+    Z[:, 2] = 0.0  # rank deficient: even the shifted pass leaves the column zero
+    st = oracle.scqr3(Z)[2]
+    assert st != 0
+
+
+# --------------------------------------------------------------------------- oblique reductions
+
+def test_oblique_diagonal_B_reduces_to_standard():
+    """B = D diagonal: Q_B = D^{-1/2} Qt, R_B = Rt with Qt Rt = QR(D^{1/2} X)."""
+    m, n = 400, 10
+    rng = np.random.default_rng(51)
+    d = rng.uniform(0.5, 4.0, size=m)
+    X = testmat(m, n, 1e6, seed=52)
+    Q, R, st, _ = oracle.scqr3(X, d.reshape(m, 1, 1))
+    assert st == 0
+    Qt, Rt = signfix_qr(np.sqrt(d)[:, None] * X)
+    assert np.linalg.norm(R - Rt) / np.linalg.norm(Rt) < 1e-9
+    assert np.linalg.norm(Q - Qt / np.sqrt(d)[:, None]) < 1e-9
+    assert np.linalg.norm(Q.T @ (d[:, None] * Q) - np.eye(n), 2) < 1e-14
+
+
+def test_oblique_block_diagonal_reduces_to_standard():
+    """B = L L^T blockwise: Q_B = L^{-T} Qt, R_B = Rt with Qt Rt = QR(L^T X)."""
+    m, n, bs = 512, 16, 8
+    Bblk = block_diag_spd(m, bs, seed=53)
+    X = testmat(m, n, 1e6, seed=54)
+    Q, R, st, tr = oracle.scqr3(X, Bblk)
+    assert st == 0
+    L = np.linalg.cholesky(Bblk)  # lower, per block
+    LtX = np.einsum("kji,kjn->kin", L, X.reshape(-1, bs, n)).reshape(m, n)
+    Qt, Rt = signfix_qr(LtX)
+    assert np.linalg.norm(R - Rt) / np.linalg.norm(Rt) < 1e-8
+    QB = np.linalg.solve(np.transpose(L, (0, 2, 1)), Qt.reshape(-1, bs, n)).reshape(m, n)
+    assert np.linalg.norm(Q - QB) / np.linalg.norm(QB) < 1e-8
+    BQ = np.einsum("kij,kjn->kin", Bblk, Q.reshape(-1, bs, n)).reshape(m, n)
+    assert np.linalg.norm(Q.T @ BQ - np.eye(n), 2) < 1e-13
+    # the shift used ||B||_2 bounded by the largest block Frobenius norm
+    assert tr["s"][0] == pytest.approx(
+        oracle.shift_oblique(m, n, float((X * X).sum()), oracle.normb_bound(Bblk)), rel=1e-12)
+
+
+def test_normb_bound_is_an_upper_bound():
+    Bblk = block_diag_spd(64, 8, seed=55)
+    lam = max(np.linalg.eigvalsh(b).max() for b in Bblk)
+    nb = oracle.normb_bound(Bblk)
+    assert lam <= nb <= np.sqrt(8) * lam
+
+
+def test_deterministic():
+    X = testmat(1000, 20, 1e12, seed=56)
+    a = oracle.scqr3(X)
+    b = oracle.scqr3(X)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_geometric_sigma():
+    s = geometric_sigma(5, 1e4)
+    assert s[0] == 1.0 and s[-1] == pytest.approx(1e-4)
+    assert np.allclose(s[1:] / s[:-1], 10 ** -1.0)
