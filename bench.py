@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the shifted CholeskyQR3 hot path on GB300.
+
+One step = one FP64 shifted CholeskyQR3 factorization X = QR through the C
+ABI (scqr3_factor) of a 16,777,216 x 64 matrix X = U diag(sigma) V^T
+(sigma geometric 1 -> 1e-10), X and Q resident in HBM (8.6 GB each, far
+larger than the 129 MB L2, so no flush is needed between steps).
+
+Prints one JSON line (rank 0). Also reports:
+  * roofline of the dominant kernel (pass_kernel), timed live per launch with
+    CUDA events recorded by the library on its stream, against the FP64 peak
+    derived from unit counts and clocks (152 SMs x 2 DFMA/clk x 2 flop x
+    2.07 GHz = 1258.6 GFLOP/s); a cuBLAS DGEMM measurement is given beside it;
+  * e2e: the same metric with X copied from pinned host memory and Q, R
+    copied back inside every timed step;
+  * cpu_baseline: the CPU oracle timed on a bounded sample of the workload;
+  * kappa_sweep: one timed factorization per kappa of the scale-up sweep.
+
+`--impl reference` times the CPU oracle instead (no GPU), on a bounded
+sample per step. With --gpus N > 1 (torchrun) every rank factorizes its own
+matrix (independent replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sCQR3 rows/s & % roofline at m×n; mixed/batched vs FP64 at ‖QᵀQ−I‖≤1e-13"
+FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="scqr3", choices=["scqr3", "reference"])
+    ap.add_argument("--m", type=int, default=16777216)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--kappa", type=float, default=1e10)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def flops_of(m, n, passes):
+    """Algorithmic FP64 flops of one factorization that ran `passes` passes:
+    each pass is one Gram (n(n+1) flops per row: n(n+1)/2 FMAs) and one
+    substitution (n^2 flops per row: n(n-1)/2 FMAs and n multiplications)."""
+    return passes * m * (n * (n + 1) + n * n)
+
+
+def pass_kernel_flops(m, n, kernel, pass_idx, passes):
+    """Flops done by one pass_kernel launch (0 when the device skipped it)."""
+    from paper_1809_11085_gb300 import scqr3
+
+    if kernel == scqr3.KERNEL_GRAM:
+        return m * n * (n + 1)
+    if kernel == scqr3.KERNEL_PASS:
+        if pass_idx >= passes:
+            return 0
+        f = m * n * n
+        if pass_idx < passes - 1:
+            f += m * n * (n + 1)
+        return f
+    return 0
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) >= 9:
+                        rows.append(p)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle legs
+
+def oracle_rows_per_s(n, kappa, target_s, seed=77, max_rows=1 << 21):
+    """Time the CPU oracle (single thread, as it stands) on a sample sized for
+    about target_s seconds; returns (rows/s, rows, seconds)."""
+    import oracle
+    from paper_1809_11085_gb300.testmat import testmat
+
+    m0 = 32768
+    X = testmat(m0, n, kappa, seed=seed)
+    t0 = time.perf_counter()
+    oracle.scqr3(X)
+    t_small = time.perf_counter() - t0
+    rows = int(min(max_rows, max(m0, m0 * target_s / max(t_small, 1e-6))))
+    rows = max(n, (rows // 1024) * 1024)
+    X = testmat(rows, n, kappa, seed=seed + 1)
+    t0 = time.perf_counter()
+    _, _, st, tr = oracle.scqr3(X)
+    t = time.perf_counter() - t0
+    return rows / t, rows, t, tr["passes"]
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1809_11085_gb300.testmat import testmat
+
+    # size each step so that warmup + steps stay within a few minutes
+    per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    m0 = 32768
+    X = testmat(m0, args.n, args.kappa, seed=91)
+    t0 = time.perf_counter()
+    oracle.scqr3(X)
+    t_small = time.perf_counter() - t0
+    rows = int(min(1 << 21, max(m0, m0 * per_step / max(t_small, 1e-6))))
+    rows = max(args.n, (rows // 1024) * 1024)
+    X = testmat(rows, args.n, args.kappa, seed=92)
+    for _ in range(args.warmup):
+        oracle.scqr3(X)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.scqr3(X)
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts) / len(ts)
+    v = rows / t
+    sample = "%d x %d rows of the same U diag(sigma) V^T construction (kappa=%g), one factorization per step" % (
+        rows, args.n, args.kappa)
+    out = {"metric": METRIC, "value": v, "unit": "rows/s", "impl": "reference", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "sCQR3 FP64 on a bounded row sample of the %d x %d workload" % (args.m, args.n),
+                      "m_sample": rows, "n": args.n, "kappa": args.kappa},
+           "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU leg
+
+def dgemm_tflops(torch, dev):
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * 4096 ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_1809_11085_gb300 import build, scqr3
+    from paper_1809_11085_gb300.testmat import testmat_torch
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    m, n, kappa = args.m, args.n, args.kappa
+    X, _, _ = testmat_torch(m, n, kappa, seed=1000 + 100 * 1 + rank, device=dev)
+    Q = torch.empty_like(X)
+    ws = scqr3.Workspace(m, n, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        scqr3.factor(X, Q=Q, workspace=ws, read_info=False)
+    torch.cuda.synchronize(dev)
+    _, R, info = scqr3.factor(X, Q=Q, workspace=ws)
+    assert info.status == 0, info
+
+    # accuracy of the result the timed steps recompute
+    G = Q.T @ Q
+    G -= torch.eye(n, dtype=torch.float64, device=dev)
+    orth = torch.linalg.matrix_norm(G, 2).item()
+    resid = (torch.linalg.matrix_norm(X - Q @ R) / torch.linalg.matrix_norm(X)).item()
+    del G
+
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.4)
+    scqr3.timing_begin(64 * args.steps + 64)
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        scqr3.factor(X, Q=Q, workspace=ws, read_info=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    recs, launches = scqr3.timing_end(64 * args.steps + 64)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+
+    passes = info.passes
+    value = world * m / (ms * 1e-3)
+    # dominant kernel: pass_kernel launches that did work
+    kflops, kms, kl = 0.0, 0.0, 0
+    share = {}
+    for kernel, p, t in recs:
+        name = scqr3.KERNEL_NAMES.get(kernel, str(kernel))
+        share[name] = share.get(name, 0.0) + t
+        f = pass_kernel_flops(m, n, kernel, p, passes)
+        if f > 0:
+            kflops += f
+            kms += t
+            kl += 1
+    tot = sum(share.values()) or 1.0
+    achieved = kflops / (kms * 1e-3) / 1e12 if kms > 0 else None
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    dgemm = dgemm_tflops(torch, dev)
+
+    # e2e: pinned host X -> device, factorization, Q and R -> pinned host, every step
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        Xh.copy_(X)
+        Qh = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        Xd = torch.empty_like(X)
+        Rd = torch.empty((n, n), dtype=torch.float64, device=dev)
+        ksteps = max(2, min(args.steps, 4))
+        for it in range(1 + ksteps):
+            if it == 1:
+                torch.cuda.synchronize(dev)
+                f0, f1 = torch.cuda.Event(True), torch.cuda.Event(True)
+                f0.record(stream)
+            Xd.copy_(Xh, non_blocking=True)
+            scqr3.factor(Xd, Q=Xd, R=Rd, workspace=ws, read_info=False)
+            Qh.copy_(Xd, non_blocking=True)
+            Rh.copy_(Rd, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = f0.elapsed_time(f1) / ksteps
+        e2e = {"value": world * m / (ems * 1e-3), "unit": "rows/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": m * n * 8 + n * n * 8,
+               "path": "pinned host X -> scqr3_factor (in place) -> pinned host Q, R"}
+        del Xh, Qh, Xd
+
+    sweep = {}
+    if not args.no_sweep:
+        from paper_1809_11085_gb300.testmat import repeated_small_sigma
+
+        del X
+        torch.cuda.empty_cache()
+        for kk in (1e2, 1e6, 1e10, 1e14, 1e15, "repeated"):
+            sig = repeated_small_sigma(n, 8, 1e-14, 1e7) if kk == "repeated" else None
+            Xs, _, _ = testmat_torch(m, n, 0.0 if sig is not None else kk, seed=1150 + len(sweep),
+                                     device=dev, sigma=sig)
+            scqr3.factor(Xs, Q=Q, workspace=ws, read_info=False)
+            torch.cuda.synchronize(dev)
+            g0, g1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            g0.record(stream)
+            _, Rs, inf = scqr3.factor(Xs, Q=Q, workspace=ws, read_info=False)
+            g1.record(stream)
+            torch.cuda.synchronize(dev)
+            inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
+            Gs = Q.T @ Q
+            Gs -= torch.eye(n, dtype=torch.float64, device=dev)
+            o = torch.linalg.matrix_norm(Gs, 2).item()
+            sweep[str(kk)] = {"ms": round(g0.elapsed_time(g1), 2), "passes": inf.passes,
+                              "shifted": inf.shifted, "status": inf.status, "orth": o}
+            del Xs, Gs
+            torch.cuda.empty_cache()
+
+    cpu = None
+    if not args.no_cpu:
+        v, rows, t, p = oracle_rows_per_s(n, kappa, args.cpu_seconds)
+        cpu = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+               "sample": "%d x %d X = U diag(sigma) V^T, kappa=%g, one factorization (%d passes) in %.1f s"
+                         % (rows, n, kappa, p, t)}
+
+    fl = flops_of(m, n, passes)
+    out = {
+        "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "sCQR3 FP64, X = U diag(sigma) V^T, %d x %d, kappa=%g" % (m, n, kappa),
+                   "m": m, "n": n, "kappa": kappa, "passes": passes, "shifted": info.shifted,
+                   "l2": "inputs (%.1f GB) larger than the 129 MB L2; no flush" % (m * n * 8 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "kernel": "pass_kernel<64> (FP64 DFMA)",
+                     "achieved": achieved, "peak": FP64_PEAK_DERIVED_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved / FP64_PEAK_DERIVED_TFLOPS) if achieved else None,
+                     "traffic": None, "launches_timed": kl,
+                     "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; cuBLAS DGEMM measured beside it",
+                     "cublas_dgemm_tflops": dgemm},
+        "path_tflops": fl / (ms * 1e-3) / 1e12,
+        "gflops_6mn2": 6 * m * n * n / (ms * 1e-3) / 1e9,
+        "kernel_share": {k: round(v / tot, 4) for k, v in share.items()},
+        "orth": orth, "resid": resid,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "kappa_sweep": sweep,
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * scqr3.h -- C ABI of the GB300 (sm_103a) shifted CholeskyQR3 library.
+ *
+ * Computes the QR factorization X = QR of a tall-skinny m x n matrix
+ * (m >= n), with Q^T Q = I (or Q^T B Q = I for an oblique inner product) and
+ * R upper triangular with positive diagonal, by shifted CholeskyQR3
+ * (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa: Sec. 2 Alg. 1,
+ * Sec. 4 Alg. 3, Sec. 5 Alg. 4 and Alg. 5), with the breakdown rule of Alg. 2.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are row-major FP64: element (i, j) of X is X[i*ldx + j].
+ *    Row-major keeps each row x_i^T contiguous, which is what the row-wise
+ *    substitution Q = X R^{-1} (Eq. backward2) works on.
+ *  - Every pointer argument is DEVICE memory owned by the caller, except
+ *    the scqr3_B / scqr3_opts descriptors themselves, which are host structs
+ *    (their `blocks` pointer is device memory).
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL is the legacy default stream). No call synchronizes the host on the
+ *    compute path. The return value reports only errors detectable on the
+ *    host before any work is queued; everything found while computing is
+ *    written to the device-side scqr3_info and is valid once the stream has
+ *    been synchronized.
+ *  - No entry point allocates device memory: scratch comes from the
+ *    caller's `workspace` of at least scqr3_workspace_bytes() bytes,
+ *    256-byte aligned, not shared with a concurrent call.
+ */
+#ifndef SCQR3_H
+#define SCQR3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCQR3_MAX_PASSES 8   /* upper limit of opts.max_passes            */
+#define SCQR3_MAX_N 128      /* largest n of the FP64 path                 */
+
+/* Status codes (return values and scqr3_info.status).
+ *   > 0  : the SHIFTED Cholesky broke down at this 1-based column, i.e.
+ *          chol(A + sI) of Alg. 1 line 3 failed (X numerically rank
+ *          deficient beyond what the shift of Eq. (finds2) covers).
+ *   -1..-20 : argument k (1-based, in the order of the prototype) invalid. */
+#define SCQR3_OK 0
+#define SCQR3_E_NONFINITE (-100)  /* the Gram matrix has a NaN/Inf entry   */
+#define SCQR3_E_MAXPASS (-101)    /* max_passes reached before two plain
+                                     CholeskyQR passes followed the last
+                                     shifted one; Q, R are still X = QR   */
+#define SCQR3_E_CUDA (-103)       /* a CUDA launch failed                  */
+#define SCQR3_E_WORKSPACE (-104)  /* workspace too small or misaligned     */
+#define SCQR3_E_B_NOT_SPD (-105)  /* a diagonal block of B is not SPD      */
+#define SCQR3_E_UNSUPPORTED (-106)/* size not supported by this build      */
+
+#define SCQR3_PREC_FP64 0
+
+/* Oblique inner product (x, y)_B = x^T B y of Sec. 5, for block-diagonal
+ * SPD B = blockdiag(B_1, ..., B_{m/bs}). */
+typedef struct {
+  int bs;               /* block size, one of 1, 2, 4, 8, 16; m % bs == 0  */
+  const double *blocks; /* device: (m/bs) blocks of bs*bs row-major FP64    */
+  double norm2;         /* ||B||_2 if > 0; otherwise the bound
+                           max_j ||B_j||_F is computed on the device        */
+} scqr3_B;
+
+typedef struct {
+  int max_passes;  /* total CholeskyQR passes allowed, 3..SCQR3_MAX_PASSES;
+                      0 selects 6                                          */
+  int precision;   /* SCQR3_PREC_FP64                                      */
+  double norm_x2;  /* > 0: value of ||X||_2^2 used in the pass-1 shift of
+                      Eq. (finds2)/(finds2B); otherwise ||X||_F^2 (Sec. 4.1
+                      allows this more conservative substitute)             */
+} scqr3_opts;
+
+/* Per-call record, written on the device. */
+typedef struct {
+  int status;                            /* SCQR3_OK or a code above       */
+  int passes;                            /* CholeskyQR passes executed     */
+  int shifted[SCQR3_MAX_PASSES];         /* pass k used chol(A + sI)       */
+  int unshifted_fail[SCQR3_MAX_PASSES];  /* column where the plain chol(A)
+                                            of pass k broke down, else 0   */
+  double s[SCQR3_MAX_PASSES];            /* shift of pass k, 0 if none     */
+  double norm2[SCQR3_MAX_PASSES];        /* ||Q_{k-1}||^2 estimate used    */
+} scqr3_info;
+
+/* Bytes of device workspace that scqr3_factor needs for (m, n, B, opts).
+ * Writes *bytes; returns SCQR3_OK or a negative argument code. */
+int scqr3_workspace_bytes(int64_t m, int n, const scqr3_B *B,
+                          const scqr3_opts *opts, size_t *bytes);
+
+/* Shifted CholeskyQR3: X = QR (Alg. 3), or X = QR with Q^T B Q = I (Alg. 5).
+ *
+ *  X      m x n input, leading dimension ldx >= n. Read only.
+ *  B      NULL for B = I, else the block-diagonal SPD descriptor above.
+ *  Q      m x n output, ldq >= n. May alias X exactly (X == Q, ldx == ldq)
+ *         for an in-place factorization; any other overlap is an error.
+ *  R      n x n output, leading dimension n, upper triangular, positive
+ *         diagonal, strictly lower part set to zero: R = R_k ... R_2 R_1.
+ *  Rpass  NULL, or SCQR3_MAX_PASSES * n * n doubles receiving the per-pass
+ *         factors R_k (pass k at Rpass + k*n*n, row-major, lower part zero),
+ *         as the adjoint scqr3_backward needs them.
+ *  info   device scqr3_info filled by the call (required).
+ *
+ * Pass 1 always adds the shift s of Eq. (finds2) (Eq. finds2B if B != NULL)
+ * before its Cholesky factorization (Alg. 3 lines 3-4). A later pass whose
+ * plain Cholesky breaks down is redone with the shift recomputed from that
+ * pass's ||Q||^2 (Alg. 2 lines 5-7). The call ends after two consecutive
+ * plain passes (CholeskyQR2, Alg. 3 lines 6-7) or at max_passes
+ * (SCQR3_E_MAXPASS). Each pass's solve Q := Q R_k^{-1} is done row by row
+ * by substitution, as the row-wise analysis (Eq. backward2) assumes. */
+int scqr3_factor(const double *X, int64_t m, int n, int64_t ldx,
+                 const scqr3_B *B, double *Q, int64_t ldq, double *R,
+                 double *Rpass, void *workspace, size_t workspace_bytes,
+                 const scqr3_opts *opts, scqr3_info *info, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Launch timing (tracing). The paper reports per-routine times of each pass
+ * (Sec. 7, Table 7); this is the device counterpart. Between
+ * scqr3_timing_begin and scqr3_timing_end, every kernel that scqr3_factor
+ * queues (from any host thread) is bracketed by CUDA events recorded on the
+ * call's stream, so each record's time is that launch's device duration.
+ * Kernels of passes that the device decides to skip are still launched (they
+ * return at once) and are recorded too.
+ */
+#define SCQR3_KERNEL_GRAM 0     /* pass kernel: Gram of X (pass 1)          */
+#define SCQR3_KERNEL_PASS 1     /* pass kernel: Q := Q R_k^{-1} (+ Gram)    */
+#define SCQR3_KERNEL_REDUCE 2   /* fixed-order sum of partial Grams         */
+#define SCQR3_KERNEL_CHOL 3     /* shift, Cholesky, R := R_k R, bookkeeping */
+#define SCQR3_KERNEL_BFACTOR 4  /* per-block Cholesky of the oblique B      */
+
+typedef struct {
+  int kernel;  /* SCQR3_KERNEL_*                                          */
+  int pass;    /* 0-based pass index the launch belongs to                */
+  float ms;    /* device time from this launch's start event to the next  */
+} scqr3_launch_time;
+
+/* Start recording up to `capacity` launches (host-side; creates events).
+ * Returns SCQR3_OK, -1 for capacity < 1, or SCQR3_E_CUDA. */
+int scqr3_timing_begin(int capacity);
+
+/* Stop recording, wait for the recorded events, and copy up to `capacity`
+ * records (in launch order) to the HOST array `out`; *count receives the
+ * number of launches recorded (which may exceed capacity). */
+int scqr3_timing_end(scqr3_launch_time *out, int capacity, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCQR3_H */

@@ -1,0 +1,296 @@
+// scqr3_api.cu -- the C ABI of include/scqr3.h: argument checks, workspace
+// layout and the launch sequence of one factorization.
+//
+// A factorization is a fixed sequence of kernels on one stream, with no host
+// synchronization: the number of passes is decided on the device (the
+// Cholesky kernel of pass k sets flags that later launches read), so kernels
+// of passes that turn out not to be needed return at once. That keeps a call
+// capturable in a CUDA graph and free of host round trips.
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "scqr3_internal.cuh"
+
+namespace scqr3 {
+cudaError_t pass_setup(int np, int* ctas_per_sm, PassGeom* geo);
+void launch_pass(int np, int grid, cudaStream_t s, const double* src, int64_t lds, double* dst,
+                 int64_t ldd, const Params& P, int pass, const double* rk, const double* lt,
+                 double* partials, int part_stride, DevState* st);
+void launch_reduce(cudaStream_t s, const double* partials, int n_partials, int stride, double* out,
+                   const DevState* st, int pass);
+void launch_chol(int np, cudaStream_t s, const Params& P, int pass, const double* gram,
+                 double* rstack, double* racc, double* Rout, double* Rpass, DevState* st,
+                 scqr3_info* info);
+void launch_bfactor(cudaStream_t s, int bs, const double* B, int64_t nblk, double* lt, DevState* st,
+                    int sms);
+
+namespace {
+
+int padded_n(int n) {
+  if (n <= 16) return 16;
+  if (n <= 32) return 32;
+  if (n <= 64) return 64;
+  if (n <= 128) return 128;
+  return 0;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Per-device, per-size launch geometry (occupancy query and shared-memory
+// opt-in happen once).
+struct DevGeo {
+  bool ready = false;
+  int sms = 0;
+  int ctas_per_sm[5] = {0, 0, 0, 0, 0};
+  PassGeom geo[5];
+};
+constexpr int kMaxDevices = 64;
+DevGeo g_geo[kMaxDevices];
+std::mutex g_mu;
+
+int np_slot(int np) { return np == 16 ? 0 : np == 32 ? 1 : np == 64 ? 2 : np == 128 ? 3 : 4; }
+
+cudaError_t device_geo(int np, int* grid_max, PassGeom* geo) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevGeo& d = g_geo[dev];
+  if (!d.ready) {
+    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    for (int s : {16, 32, 64, 128}) {
+      e = pass_setup(s, &d.ctas_per_sm[np_slot(s)], &d.geo[np_slot(s)]);
+      if (e != cudaSuccess) return e;
+      if (d.ctas_per_sm[np_slot(s)] < 1) return cudaErrorInvalidConfiguration;
+    }
+    d.ready = true;
+  }
+  *grid_max = d.sms * d.ctas_per_sm[np_slot(np)];
+  *geo = d.geo[np_slot(np)];
+  return cudaSuccess;
+}
+
+int sm_count() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return (dev >= 0 && dev < kMaxDevices && g_geo[dev].ready) ? g_geo[dev].sms : 1;
+}
+
+int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
+  if (n < 1) return -3;
+  if (m < n) return -2;
+  if (B && (B->bs != 1 && B->bs != 2 && B->bs != 4 && B->bs != 8 && B->bs != 16)) return -5;
+  if (B && (m % B->bs) != 0) return -5;
+  if (B && !B->blocks) return -5;
+  if (opts && opts->max_passes != 0 && (opts->max_passes < 3 || opts->max_passes > SCQR3_MAX_PASSES))
+    return -12;
+  if (opts && opts->precision != SCQR3_PREC_FP64) return -12;
+  if (padded_n(n) == 0) return SCQR3_E_UNSUPPORTED;
+  return SCQR3_OK;
+}
+
+int make_layout(int64_t m, int n, const scqr3_B* B, Layout* L, int* grid, PassGeom* geo) {
+  const int np = padded_n(n);
+  int grid_max = 0;
+  if (device_geo(np, &grid_max, geo) != cudaSuccess) return SCQR3_E_CUDA;
+  const int64_t npanels = (m + geo->pr - 1) / geo->pr;
+  *grid = (int)(npanels < grid_max ? npanels : grid_max);
+  if (*grid < 1) *grid = 1;
+  const int E = pk_size(np);
+  L->part_stride = E + 1;
+  L->n_partials = *grid * geo->groups;
+  size_t off = 0;
+  L->state = off;
+  off = align256(off + sizeof(DevState));
+  L->gram = off;
+  off = align256(off + sizeof(double) * (E + 1));
+  L->rstack = off;
+  off = align256(off + sizeof(double) * (size_t)E * SCQR3_MAX_PASSES);
+  L->racc = off;
+  off = align256(off + sizeof(double) * E);
+  L->lt = off;
+  if (B) {
+    const int64_t nblk = m / B->bs;
+    off = align256(off + sizeof(double) * (size_t)nblk * (B->bs * (B->bs + 1) / 2));
+  }
+  L->partials = off;
+  off = align256(off + sizeof(double) * (size_t)L->n_partials * L->part_stride);
+  L->total = off;
+  return SCQR3_OK;
+}
+
+// ---- launch timing -------------------------------------------------------------------------
+struct Timer {
+  std::mutex mu;
+  bool on = false;
+  int cap = 0;
+  int used = 0;       // events used
+  int launches = 0;   // launches seen (may exceed what was recorded)
+  cudaEvent_t* ev = nullptr;
+  int* kind = nullptr;  // -1 marks the end of a call
+  int* pass = nullptr;
+};
+Timer g_timer;
+
+// Record an event before a launch (kind >= 0) or after a call's last one (-1).
+void tick(cudaStream_t s, int kind, int pass) {
+  if (!g_timer.on) return;
+  std::lock_guard<std::mutex> lk(g_timer.mu);
+  if (!g_timer.on) return;
+  if (kind >= 0) ++g_timer.launches;
+  if (g_timer.used >= g_timer.cap + 64) return;  // the pool has 64 spare end markers
+  cudaEventRecord(g_timer.ev[g_timer.used], s);
+  g_timer.kind[g_timer.used] = kind;
+  g_timer.pass[g_timer.used] = pass;
+  ++g_timer.used;
+}
+
+bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + bbytes && pb < pa + abytes;
+}
+
+}  // namespace
+}  // namespace scqr3
+
+using namespace scqr3;
+
+extern "C" int scqr3_workspace_bytes(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts,
+                                     size_t* bytes) {
+  if (!bytes) return -5;
+  const int a = check_args(m, n, B, opts);
+  if (a != SCQR3_OK) return a;
+  Layout L;
+  int grid;
+  PassGeom geo;
+  const int r = make_layout(m, n, B, &L, &grid, &geo);
+  if (r != SCQR3_OK) return r;
+  *bytes = L.total;
+  return SCQR3_OK;
+}
+
+extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, const scqr3_B* B,
+                            double* Q, int64_t ldq, double* R, double* Rpass, void* workspace,
+                            size_t workspace_bytes, const scqr3_opts* opts, scqr3_info* info,
+                            void* stream) {
+  const int a = check_args(m, n, B, opts);
+  if (a != SCQR3_OK) return a;
+  if (!X) return -1;
+  if (ldx < n) return -4;
+  if (!Q) return -6;
+  if (ldq < n) return -7;
+  if (!R) return -8;
+  if (!workspace) return -10;
+  if (!info) return -13;
+  // Q may be X itself (in place) but must not overlap it otherwise.
+  const size_t xbytes = sizeof(double) * (size_t)((m - 1) * ldx + n);
+  const size_t qbytes = sizeof(double) * (size_t)((m - 1) * ldq + n);
+  if ((const void*)Q != (const void*)X && overlaps(X, xbytes, Q, qbytes)) return -6;
+  if ((const void*)Q == (const void*)X && ldq != ldx) return -7;
+  if (((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
+
+  Layout L;
+  int grid;
+  PassGeom geo;
+  const int r = make_layout(m, n, B, &L, &grid, &geo);
+  if (r != SCQR3_OK) return r;
+  if (workspace_bytes < L.total) return SCQR3_E_WORKSPACE;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  DevState* st = (DevState*)(ws + L.state);
+  double* gram = (double*)(ws + L.gram);
+  double* rstack = (double*)(ws + L.rstack);
+  double* racc = (double*)(ws + L.racc);
+  double* lt = B ? (double*)(ws + L.lt) : nullptr;
+  double* partials = (double*)(ws + L.partials);
+
+  Params P;
+  P.m = m;
+  P.n = n;
+  P.np = padded_n(n);
+  P.max_passes = (opts && opts->max_passes) ? opts->max_passes : 6;
+  P.bs = B ? B->bs : 0;
+  P.norm_x2 = opts ? opts->norm_x2 : 0.0;
+  P.normb_in = B ? B->norm2 : 0.0;
+
+  if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return SCQR3_E_CUDA;
+  if (cudaMemsetAsync(info, 0, sizeof(scqr3_info), s) != cudaSuccess) return SCQR3_E_CUDA;
+  if (B) {
+    tick(s, SCQR3_KERNEL_BFACTOR, 0);
+    launch_bfactor(s, B->bs, B->blocks, m / B->bs, lt, st, sm_count());
+  }
+
+  // Pass 1, Alg. 3 line 2: A = X^T X (or X^T B X).
+  tick(s, SCQR3_KERNEL_GRAM, 0);
+  launch_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, lt, partials, L.part_stride, st);
+  tick(s, SCQR3_KERNEL_REDUCE, 0);
+  launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, -1);
+  tick(s, SCQR3_KERNEL_CHOL, 0);
+  launch_chol(P.np, s, P, 0, gram, rstack, racc, R, Rpass, st, info);
+  const int E = pk_size(P.np);
+  for (int k = 0; k < P.max_passes; ++k) {
+    const double* src = (k == 0) ? X : Q;
+    const int64_t lds = (k == 0) ? ldx : ldq;
+    tick(s, SCQR3_KERNEL_PASS, k);
+    launch_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, lt, partials,
+                L.part_stride, st);
+    if (k + 1 < P.max_passes) {
+      tick(s, SCQR3_KERNEL_REDUCE, k + 1);
+      launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, k);
+      tick(s, SCQR3_KERNEL_CHOL, k + 1);
+      launch_chol(P.np, s, P, k + 1, gram, rstack, racc, R, Rpass, st, info);
+    }
+  }
+  tick(s, -1, -1);
+  if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
+  return SCQR3_OK;
+}
+
+extern "C" int scqr3_timing_begin(int capacity) {
+  if (capacity < 1) return -1;
+  std::lock_guard<std::mutex> lk(g_timer.mu);
+  if (g_timer.ev) {
+    for (int i = 0; i < g_timer.cap + 64; ++i) cudaEventDestroy(g_timer.ev[i]);
+    delete[] g_timer.ev;
+    delete[] g_timer.kind;
+    delete[] g_timer.pass;
+    g_timer.ev = nullptr;
+  }
+  g_timer.cap = capacity;
+  g_timer.ev = new cudaEvent_t[capacity + 64];
+  g_timer.kind = new int[capacity + 64];
+  g_timer.pass = new int[capacity + 64];
+  for (int i = 0; i < capacity + 64; ++i)
+    if (cudaEventCreate(&g_timer.ev[i]) != cudaSuccess) return SCQR3_E_CUDA;
+  g_timer.used = 0;
+  g_timer.launches = 0;
+  g_timer.on = true;
+  return SCQR3_OK;
+}
+
+extern "C" int scqr3_timing_end(scqr3_launch_time* out, int capacity, int* count) {
+  std::lock_guard<std::mutex> lk(g_timer.mu);
+  g_timer.on = false;
+  if (count) *count = g_timer.launches;
+  if (!g_timer.ev) return SCQR3_OK;
+  if (g_timer.used > 0 && cudaEventSynchronize(g_timer.ev[g_timer.used - 1]) != cudaSuccess)
+    return SCQR3_E_CUDA;
+  int k = 0;
+  for (int i = 0; i + 1 < g_timer.used && k < capacity; ++i) {
+    if (g_timer.kind[i] < 0) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g_timer.ev[i], g_timer.ev[i + 1]) != cudaSuccess) return SCQR3_E_CUDA;
+    if (out) {
+      out[k].kernel = g_timer.kind[i];
+      out[k].pass = g_timer.pass[i];
+      out[k].ms = ms;
+    }
+    ++k;
+  }
+  return SCQR3_OK;
+}

@@ -1,0 +1,211 @@
+"""Python binding of the C ABI in include/scqr3.h (argument marshalling only).
+
+Every step of the factorization runs in libscqr3.so on the GPU; this module
+only turns torch tensors into device pointers, sizes the workspace and reads
+the per-call record back. There is no CPU fallback: if the library or a GPU
+is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+MAX_PASSES = 8
+MAX_N = 128
+
+OK = 0
+E_NONFINITE = -100
+E_MAXPASS = -101
+E_CUDA = -103
+E_WORKSPACE = -104
+E_B_NOT_SPD = -105
+E_UNSUPPORTED = -106
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libscqr3.so")
+
+
+class ScqrError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s failed with status %d" % (what, code))
+        self.code = code
+
+
+class _B(ctypes.Structure):
+    _fields_ = [("bs", ctypes.c_int), ("blocks", ctypes.c_void_p), ("norm2", ctypes.c_double)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("max_passes", ctypes.c_int), ("precision", ctypes.c_int),
+                ("norm_x2", ctypes.c_double)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("passes", ctypes.c_int),
+                ("shifted", ctypes.c_int * MAX_PASSES),
+                ("unshifted_fail", ctypes.c_int * MAX_PASSES),
+                ("s", ctypes.c_double * MAX_PASSES),
+                ("norm2", ctypes.c_double * MAX_PASSES)]
+
+
+INFO_BYTES = ctypes.sizeof(_Info)
+
+KERNEL_GRAM, KERNEL_PASS, KERNEL_REDUCE, KERNEL_CHOL, KERNEL_BFACTOR = 0, 1, 2, 3, 4
+KERNEL_NAMES = {0: "pass_kernel(gram)", 1: "pass_kernel(solve+gram)", 2: "reduce_kernel",
+                3: "chol_kernel", 4: "bfactor_kernel"}
+
+
+class _LaunchTime(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("pass_", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+@dataclass
+class Info:
+    status: int
+    passes: int
+    shifted: list = field(default_factory=list)
+    unshifted_fail: list = field(default_factory=list)
+    s: list = field(default_factory=list)
+    norm2: list = field(default_factory=list)
+
+    @staticmethod
+    def from_bytes(buf: bytes) -> "Info":
+        c = _Info.from_buffer_copy(buf)
+        k = max(0, min(c.passes, MAX_PASSES))
+        return Info(c.status, c.passes, list(c.shifted[:k]), list(c.unshifted_fail[:k]),
+                    list(c.s[:k]), list(c.norm2[:k]))
+
+
+_lib = None
+
+
+def lib():
+    """Load libscqr3.so (built by paper_1809_11085_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libscqr3.so is not built; run paper_1809_11085_gb300.build.build()")
+        L = ctypes.CDLL(_LIB_PATH)
+        i64, i32, p, sz = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+        L.scqr3_workspace_bytes.argtypes = [i64, i32, ctypes.POINTER(_B), ctypes.POINTER(_Opts),
+                                            ctypes.POINTER(sz)]
+        L.scqr3_workspace_bytes.restype = i32
+        L.scqr3_factor.argtypes = [p, i64, i32, i64, ctypes.POINTER(_B), p, i64, p, p, p, sz,
+                                   ctypes.POINTER(_Opts), p, p]
+        L.scqr3_factor.restype = i32
+        L.scqr3_timing_begin.argtypes = [i32]
+        L.scqr3_timing_begin.restype = i32
+        L.scqr3_timing_end.argtypes = [ctypes.POINTER(_LaunchTime), i32, ctypes.POINTER(i32)]
+        L.scqr3_timing_end.restype = i32
+        _lib = L
+    return _lib
+
+
+def _check_mat(t, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.dim() != 2:
+        raise TypeError("%s must be a 2-D float64 CUDA tensor" % name)
+    if t.stride(1) != 1:
+        raise ValueError("%s must be row-major (stride(1) == 1)" % name)
+
+
+def _b_struct(B, normb):
+    if B is None:
+        return None, None
+    import torch
+
+    if not (isinstance(B, torch.Tensor) and B.is_cuda and B.dtype == torch.float64 and B.dim() == 3
+            and B.shape[1] == B.shape[2] and B.is_contiguous()):
+        raise TypeError("B must be a contiguous (m/bs, bs, bs) float64 CUDA tensor")
+    b = _B(int(B.shape[1]), ctypes.c_void_p(B.data_ptr()), float(normb))
+    return b, ctypes.byref(b)
+
+
+def _opts(max_passes, norm_x2):
+    o = _Opts(int(max_passes), 0, float(norm_x2))
+    return o, ctypes.byref(o)
+
+
+def workspace_bytes(m: int, n: int, B=None, max_passes: int = 0, norm_x2: float = 0.0,
+                    normb: float = 0.0) -> int:
+    _, bp = _b_struct(B, normb)
+    _, op = _opts(max_passes, norm_x2)
+    out = ctypes.c_size_t(0)
+    r = lib().scqr3_workspace_bytes(int(m), int(n), bp, op, ctypes.byref(out))
+    if r != OK:
+        raise ScqrError(r, "scqr3_workspace_bytes")
+    return out.value
+
+
+class Workspace:
+    """Reusable device scratch for repeated calls of one shape."""
+
+    def __init__(self, m, n, B=None, max_passes=0, device=None):
+        import torch
+
+        self.bytes = workspace_bytes(m, n, B, max_passes)
+        self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=device or "cuda")
+        base = self.buf.data_ptr()
+        self.ptr = (base + 255) & ~255
+        self.info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=device or "cuda")
+
+
+def factor(X, B=None, *, max_passes: int = 0, norm_x2: float = 0.0, normb: float = 0.0,
+           Q=None, R=None, Rpass=None, workspace: Workspace | None = None, stream=None,
+           read_info: bool = True):
+    """Shifted CholeskyQR3 of X (m x n, float64 CUDA tensor) through scqr3_factor.
+
+    Returns (Q, R, info). Q may be passed as X for an in-place factorization.
+    With read_info=False nothing synchronizes and info is the raw device
+    buffer (decode later with Info.from_bytes(buf.cpu().numpy().tobytes())).
+    """
+    import torch
+
+    _check_mat(X, "X")
+    m, n = X.shape
+    if Q is None:
+        Q = torch.empty((m, n), dtype=torch.float64, device=X.device)
+    _check_mat(Q, "Q")
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=X.device)
+    if not (R.is_cuda and R.dtype == torch.float64 and R.is_contiguous() and tuple(R.shape) == (n, n)):
+        raise TypeError("R must be a contiguous n x n float64 CUDA tensor")
+    if Rpass is not None and not (Rpass.is_cuda and Rpass.dtype == torch.float64 and Rpass.is_contiguous()
+                                  and Rpass.numel() >= MAX_PASSES * n * n):
+        raise TypeError("Rpass must hold MAX_PASSES*n*n float64 on the device")
+    if workspace is None:
+        workspace = Workspace(m, n, B, max_passes, device=X.device)
+    b, bp = _b_struct(B, normb)
+    o, op = _opts(max_passes, norm_x2)
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device).cuda_stream
+    r = lib().scqr3_factor(X.data_ptr(), m, n, X.stride(0), bp, Q.data_ptr(), Q.stride(0),
+                           R.data_ptr(), Rpass.data_ptr() if Rpass is not None else None,
+                           workspace.ptr, workspace.bytes, op, workspace.info.data_ptr(),
+                           ctypes.c_void_p(stream))
+    if r != OK:
+        raise ScqrError(r, "scqr3_factor")
+    if not read_info:
+        return Q, R, workspace.info
+    info = Info.from_bytes(workspace.info.cpu().numpy().tobytes())
+    return Q, R, info
+
+
+def timing_begin(capacity: int = 4096) -> None:
+    """Record the device duration of every kernel the library launches from now on."""
+    r = lib().scqr3_timing_begin(int(capacity))
+    if r != OK:
+        raise ScqrError(r, "scqr3_timing_begin")
+
+
+def timing_end(capacity: int = 4096):
+    """Stop recording; returns (records, launches) with records = [(kernel, pass, ms), ...]."""
+    buf = (_LaunchTime * capacity)()
+    cnt = ctypes.c_int(0)
+    r = lib().scqr3_timing_end(buf, int(capacity), ctypes.byref(cnt))
+    if r != OK:
+        raise ScqrError(r, "scqr3_timing_end")
+    k = min(cnt.value, capacity)
+    return [(buf[i].kernel, buf[i].pass_, buf[i].ms) for i in range(k)], cnt.value

@@ -1,0 +1,70 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+function that include/*.h declares; host-side argument checks fire before any
+GPU work (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\bint\s+(scqr3_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1809_11085_gb300 import build, scqr3
+
+    build.build()
+    return scqr3.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    assert "scqr3_factor" in names and "scqr3_workspace_bytes" in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_info_struct_layout_matches_header():
+    from paper_1809_11085_gb300 import scqr3
+
+    # 2 ints + 2 x MAX_PASSES ints + 2 x MAX_PASSES doubles
+    assert scqr3.INFO_BYTES == 8 + 8 * scqr3.MAX_PASSES + 16 * scqr3.MAX_PASSES
+
+
+def test_argument_errors_are_reported_on_the_host(lib):
+    from paper_1809_11085_gb300 import scqr3
+
+    out = ctypes.c_size_t(0)
+    # m < n
+    assert lib.scqr3_workspace_bytes(3, 5, None, None, ctypes.byref(out)) == -2
+    # n < 1
+    assert lib.scqr3_workspace_bytes(3, 0, None, None, ctypes.byref(out)) == -3
+    # bad block size
+    b = scqr3._B(3, ctypes.c_void_p(8), 0.0)
+    assert lib.scqr3_workspace_bytes(30, 5, ctypes.byref(b), None, ctypes.byref(out)) == -5
+    # m not a multiple of bs
+    b = scqr3._B(8, ctypes.c_void_p(8), 0.0)
+    assert lib.scqr3_workspace_bytes(30, 5, ctypes.byref(b), None, ctypes.byref(out)) == -5
+    # bad max_passes
+    o = scqr3._Opts(2, 0, 0.0)
+    assert lib.scqr3_workspace_bytes(30, 5, None, ctypes.byref(o), ctypes.byref(out)) == -12
+    # n beyond the FP64 path
+    assert lib.scqr3_workspace_bytes(1000, 300, None, None, ctypes.byref(out)) == scqr3.E_UNSUPPORTED
+    # null pointers in scqr3_factor are rejected before any CUDA call
+    assert lib.scqr3_factor(None, 10, 2, 2, None, None, 2, None, None, None, 0, None, None,
+                            None) == -1
