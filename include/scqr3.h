@@ -51,6 +51,8 @@ extern "C" {
 #define SCQR3_E_WORKSPACE (-104)  /* workspace too small or misaligned     */
 #define SCQR3_E_B_NOT_SPD (-105)  /* a diagonal block of B is not SPD      */
 #define SCQR3_E_UNSUPPORTED (-106)/* size not supported by this build      */
+#define SCQR3_E_SCRATCH_LIMIT (-107) /* scqr3_factor_noalloc: the problem needs
+                                        more scratch than its fixed array   */
 
 #define SCQR3_PREC_FP64 0
 
@@ -112,6 +114,31 @@ int scqr3_factor(const double *X, int64_t m, int n, int64_t ldx,
                  const scqr3_B *B, double *Q, int64_t ldq, double *R,
                  double *Rpass, void *workspace, size_t workspace_bytes,
                  const scqr3_opts *opts, scqr3_info *info, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * scqr3_factor_noalloc: the same factorization (B = I, default options)
+ * without a workspace argument, for callers that cannot allocate device
+ * memory -- e.g. a host application that owns all device memory through its
+ * own pool and forbids allocation by plug-in code, a caller running so close
+ * to the memory limit that a late cudaMalloc could fail, or a C/Fortran code
+ * that receives device pointers but has no allocator. The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Scratch comes from a fixed array of SCQR3_NOALLOC_SCRATCH_BYTES inside the
+ * library, reserved on each device where this entry point is first used and
+ * held until the process exits. Problems whose scqr3_workspace_bytes()
+ * exceeds it (the scratch grows with n and with the number of CTAs, which
+ * is capped by the SM count) are rejected with SCQR3_E_SCRATCH_LIMIT, so
+ * scqr3_workspace_bytes() tells in advance whether a problem fits. The first call
+ * on a device looks up the array's device address; make it before any stream
+ * capture. All calls share the array, so calls whose GPU work overlaps (other
+ * streams or host threads) race; serialize them. The call allocates nothing
+ * (no cudaMalloc/cudaFree, no allocating library routine). X, Q, R, info:
+ * as for scqr3_factor. */
+#define SCQR3_NOALLOC_SCRATCH_BYTES (16u << 20)
+int scqr3_factor_noalloc(const double *X, int64_t m, int n, int64_t ldx,
+                         double *Q, int64_t ldq, double *R, scqr3_info *info,
+                         void *stream);
 
 /* ---------------------------------------------------------------------------
  * Launch timing (tracing). The paper reports per-routine times of each pass
