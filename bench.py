@@ -36,6 +36,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sCQR3 rows/s & % roofline at m×n; mixed/batched vs FP64 at ‖QᵀQ−I‖≤1e-13"
 FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
+# DRAM bytes per row of a fused solve+Gram launch of pass_kernel<64>, from the ncu capture
+# summarised in profiles/pass_kernel_fp64_1048576x64_full.md; valid only for that kernel source.
+PROFILED_KERNEL_SHA = "978be09c5236b282"
+PROFILED_BYTES_PER_ROW = 992.4
 
 
 def parse():
@@ -52,6 +56,17 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
+
+
+def profiled_traffic(m, n):
+    """roofline.traffic for a fused launch, or None if the kernel changed since the capture."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1809_11085_gb300", "csrc", "fp64_kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if sha != PROFILED_KERNEL_SHA or n != 64:
+        return None
+    return PROFILED_BYTES_PER_ROW * m
 
 
 def flops_of(m, n, passes):
@@ -359,7 +374,9 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": "pass_kernel<64> (FP64 DFMA)",
                      "achieved": achieved, "peak": FP64_PEAK_DERIVED_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_DERIVED_TFLOPS) if achieved else None,
-                     "traffic": None, "launches_timed": kl,
+                     "traffic": profiled_traffic(m, n), "traffic_note":
+                         "DRAM bytes of one fused solve+Gram launch (ncu, scaled by rows)",
+                     "launches_timed": kl,
                      "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; cuBLAS DGEMM measured beside it",
                      "cublas_dgemm_tflops": dgemm},
         "path_tflops": fl / (ms * 1e-3) / 1e12,
