@@ -116,6 +116,31 @@ int scqr3_factor(const double *X, int64_t m, int n, int64_t ldx,
                  const scqr3_opts *opts, scqr3_info *info, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Adjoint (reverse mode) of scqr3_factor for B = I. Not in the paper; it is
+ * the chain rule through the passes of Alg. 2/3 (Q_k = Q_{k-1} R_k^{-1},
+ * R_k = chol(Q_{k-1}^T Q_{k-1} + s_k I), R = R_P ... R_1) with each shift s_k
+ * held fixed: in exact arithmetic the factorization X -> (Q, R) does not
+ * depend on s (R_2 R_1 is the R factor of X for any s), so the shift carries
+ * no gradient. Per pass k, in reverse:
+ *   M_k = Q_k^T Qbar_k,  Rbar_k = triu(L_k^T dR Racc_{k-1}^T - M_k R_k^{-T}),
+ *   P_k = sym(Phi(Rbar_k R_k^T)),  Qbar_{k-1} = (Qbar_k + 2 Q_k P_k) R_k^{-T},
+ *   Q_{k-1} = Q_k R_k  (recomputed; no intermediate Q is stored),
+ * with L_k = R_P ... R_{k+1}, Racc_{k-1} = R_{k-1} ... R_1 and Phi the upper
+ * triangle with its diagonal halved. dX = Qbar_0.
+ *
+ *  Q       m x n result of scqr3_factor (ldq >= n), read only.
+ *  Rpass   per-pass factors as written by scqr3_factor (R_k at Rpass+(k-1)n^2).
+ *  passes  scqr3_info.passes of that call (1..SCQR3_MAX_PASSES).
+ *  dQ      m x n cotangent of Q (lddq >= n); dR: n x n cotangent of R or NULL.
+ *  dX      m x n output (lddx >= n); may alias dQ exactly.
+ * Device pointers; asynchronous on `stream`; n <= SCQR3_MAX_N. */
+int scqr3_backward_workspace_bytes(int64_t m, int n, size_t *bytes);
+int scqr3_backward(const double *Q, int64_t m, int n, int64_t ldq,
+                   const double *Rpass, int passes, const double *dQ,
+                   int64_t lddq, const double *dR, double *dX, int64_t lddx,
+                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
  * scqr3_factor_noalloc: the same factorization (B = I, default options)
  * without a workspace argument, for callers that cannot allocate device
  * memory -- e.g. a host application that owns all device memory through its

@@ -94,6 +94,10 @@ def lib():
         L.scqr3_factor.argtypes = [p, i64, i32, i64, ctypes.POINTER(_B), p, i64, p, p, p, sz,
                                    ctypes.POINTER(_Opts), p, p]
         L.scqr3_factor.restype = i32
+        L.scqr3_backward_workspace_bytes.argtypes = [i64, i32, ctypes.POINTER(sz)]
+        L.scqr3_backward_workspace_bytes.restype = i32
+        L.scqr3_backward.argtypes = [p, i64, i32, i64, p, i32, p, i64, p, p, i64, p, sz, p]
+        L.scqr3_backward.restype = i32
         L.scqr3_timing_begin.argtypes = [i32]
         L.scqr3_timing_begin.restype = i32
         L.scqr3_timing_end.argtypes = [ctypes.POINTER(_LaunchTime), i32, ctypes.POINTER(i32)]
@@ -209,3 +213,84 @@ def timing_end(capacity: int = 4096):
         raise ScqrError(r, "scqr3_timing_end")
     k = min(cnt.value, capacity)
     return [(buf[i].kernel, buf[i].pass_, buf[i].ms) for i in range(k)], cnt.value
+
+
+# --------------------------------------------------------------------------- adjoint
+
+class BackwardWorkspace:
+    def __init__(self, m, n, device=None):
+        import torch
+
+        out = ctypes.c_size_t(0)
+        r = lib().scqr3_backward_workspace_bytes(int(m), int(n), ctypes.byref(out))
+        if r != OK:
+            raise ScqrError(r, "scqr3_backward_workspace_bytes")
+        self.bytes = out.value
+        self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=device or "cuda")
+        self.ptr = (self.buf.data_ptr() + 255) & ~255
+
+
+def backward(Q, Rpass, passes: int, dQ, dR=None, *, dX=None, workspace: BackwardWorkspace | None = None,
+             stream=None):
+    """dL/dX of scqr3_factor given dL/dQ and dL/dR, through scqr3_backward."""
+    import torch
+
+    _check_mat(Q, "Q")
+    _check_mat(dQ, "dQ")
+    m, n = Q.shape
+    if dX is None:
+        dX = torch.empty((m, n), dtype=torch.float64, device=Q.device)
+    _check_mat(dX, "dX")
+    if dR is not None:
+        dR = dR.contiguous()
+    if workspace is None:
+        workspace = BackwardWorkspace(m, n, device=Q.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(Q.device).cuda_stream
+    r = lib().scqr3_backward(Q.data_ptr(), m, n, Q.stride(0), Rpass.data_ptr(), int(passes),
+                             dQ.data_ptr(), dQ.stride(0), dR.data_ptr() if dR is not None else None,
+                             dX.data_ptr(), dX.stride(0), workspace.ptr, workspace.bytes,
+                             ctypes.c_void_p(stream))
+    if r != OK:
+        raise ScqrError(r, "scqr3_backward")
+    return dX
+
+
+def _autograd_function():
+    import torch
+
+    class SCQR3(torch.autograd.Function):
+        """(Q, R) = shifted CholeskyQR3(X), differentiable; saves Q and the per-pass R_k."""
+
+        @staticmethod
+        def forward(ctx, X, max_passes=0):
+            n = X.shape[1]
+            Rpass = torch.zeros((MAX_PASSES, n, n), dtype=torch.float64, device=X.device)
+            Q, R, info = factor(X.contiguous(), max_passes=max_passes, Rpass=Rpass)
+            if info.status not in (OK, E_MAXPASS):
+                raise ScqrError(info.status, "scqr3_factor")
+            ctx.passes = info.passes
+            ctx.save_for_backward(Q, Rpass)
+            ctx.info = info
+            return Q, R
+
+        @staticmethod
+        def backward(ctx, dQ, dR):
+            Q, Rpass = ctx.saved_tensors
+            if dQ is None:
+                dQ = torch.zeros_like(Q)
+            dX = backward(Q, Rpass, ctx.passes, dQ.contiguous(), dR)
+            return dX, None
+
+    return SCQR3
+
+
+_SCQR3 = None
+
+
+def qr(X, max_passes: int = 0):
+    """Differentiable shifted CholeskyQR3: returns (Q, R) with X = QR."""
+    global _SCQR3
+    if _SCQR3 is None:
+        _SCQR3 = _autograd_function()
+    return _SCQR3.apply(X, max_passes)
