@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--m", type=int, default=16777216)
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--kappa", type=float, default=1e10)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="arithmetic of the timed factorization (mixed: FP32 pairs + FP64)")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -243,10 +245,11 @@ def run_gpu(args, rank, world, local_rank):
     ws = scqr3.Workspace(m, n, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    prec = scqr3.PREC_MIXED if args.precision == "mixed" else scqr3.PREC_FP64
     for _ in range(args.warmup):
-        scqr3.factor(X, Q=Q, workspace=ws, read_info=False)
+        scqr3.factor(X, Q=Q, workspace=ws, read_info=False, precision=prec)
     torch.cuda.synchronize(dev)
-    _, R, info = scqr3.factor(X, Q=Q, workspace=ws)
+    _, R, info = scqr3.factor(X, Q=Q, workspace=ws, precision=prec)
     assert info.status == 0, info
 
     # accuracy of the result the timed steps recompute
@@ -266,7 +269,7 @@ def run_gpu(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
     e0.record(stream)
     for _ in range(args.steps):
-        scqr3.factor(X, Q=Q, workspace=ws, read_info=False)
+        scqr3.factor(X, Q=Q, workspace=ws, read_info=False, precision=prec)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     recs, launches = scqr3.timing_end(64 * args.steps + 64)

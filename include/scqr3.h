@@ -55,6 +55,15 @@ extern "C" {
                                         more scratch than its fixed array   */
 
 #define SCQR3_PREC_FP64 0
+/* Mixed form (B = I only): the bulk Gram and substitution of every pass run
+ * on the FP32 pipe in pairs of floats (h, l), x ~ h + l, with error-free
+ * products and TwoSum accumulation (about 48 significant bits); the Gram
+ * partial sums are accumulated in FP64, and the shift of Eq. (finds2), the
+ * Cholesky factorizations and R = R_k ... R_1 are FP64. Intermediate
+ * iterates are held in Q as float pairs; Q and R are returned in FP64.
+ * Inputs must lie within the float exponent range. Not in the paper (which
+ * uses FP64 throughout, Sec. 6); expected orthogonality ~1e-14. */
+#define SCQR3_PREC_MIXED 1
 
 /* Oblique inner product (x, y)_B = x^T B y of Sec. 5, for block-diagonal
  * SPD B = blockdiag(B_1, ..., B_{m/bs}). */
@@ -68,7 +77,7 @@ typedef struct {
 typedef struct {
   int max_passes;  /* total CholeskyQR passes allowed, 3..SCQR3_MAX_PASSES;
                       0 selects 6                                          */
-  int precision;   /* SCQR3_PREC_FP64                                      */
+  int precision;   /* SCQR3_PREC_FP64 or SCQR3_PREC_MIXED                  */
   double norm_x2;  /* > 0: value of ||X||_2^2 used in the pass-1 shift of
                       Eq. (finds2)/(finds2B); otherwise ||X||_F^2 (Sec. 4.1
                       allows this more conservative substitute)             */

@@ -24,6 +24,13 @@ void launch_chol(int np, cudaStream_t s, const Params& P, int pass, const double
                  scqr3_info* info);
 void launch_bfactor(cudaStream_t s, int bs, const double* B, int64_t nblk, double* lt, DevState* st,
                     int sms);
+cudaError_t df_setup();
+cudaError_t df_occupancy(int np, int* per_sm);
+int df_groups(int np);
+int df_rows_per_panel(int np);
+void launch_df_pass(int np, int grid, cudaStream_t s, const double* src, int64_t lds, double* dst,
+                    int64_t ldd, const Params& P, int pass, const double* rk, float2* rk2,
+                    float2* rinv2, double* partials, int part_stride, DevState* st);
 
 namespace {
 
@@ -43,6 +50,7 @@ struct DevGeo {
   bool ready = false;
   int sms = 0;
   int ctas_per_sm[5] = {0, 0, 0, 0, 0};
+  int df_ctas_per_sm[5] = {0, 0, 0, 0, 0};
   PassGeom geo[5];
 };
 constexpr int kMaxDevices = 64;
@@ -66,11 +74,24 @@ cudaError_t device_geo(int np, int* grid_max, PassGeom* geo) {
       if (e != cudaSuccess) return e;
       if (d.ctas_per_sm[np_slot(s)] < 1) return cudaErrorInvalidConfiguration;
     }
+    e = df_setup();
+    if (e != cudaSuccess) return e;
+    for (int s : {16, 32, 64, 128}) {
+      e = df_occupancy(s, &d.df_ctas_per_sm[np_slot(s)]);
+      if (e != cudaSuccess) return e;
+      if (d.df_ctas_per_sm[np_slot(s)] < 1) return cudaErrorInvalidConfiguration;
+    }
     d.ready = true;
   }
   *grid_max = d.sms * d.ctas_per_sm[np_slot(np)];
   *geo = d.geo[np_slot(np)];
   return cudaSuccess;
+}
+
+int df_grid_max(int np) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return g_geo[dev].sms * g_geo[dev].df_ctas_per_sm[np_slot(np)];
 }
 
 int sm_count() {
@@ -87,21 +108,32 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
   if (B && !B->blocks) return -5;
   if (opts && opts->max_passes != 0 && (opts->max_passes < 3 || opts->max_passes > SCQR3_MAX_PASSES))
     return -12;
-  if (opts && opts->precision != SCQR3_PREC_FP64) return -12;
+  if (opts && opts->precision != SCQR3_PREC_FP64 && opts->precision != SCQR3_PREC_MIXED) return -12;
+  if (opts && opts->precision == SCQR3_PREC_MIXED && B) return -5;  // mixed form: B = I only
   if (padded_n(n) == 0) return SCQR3_E_UNSUPPORTED;
   return SCQR3_OK;
 }
 
-int make_layout(int64_t m, int n, const scqr3_B* B, Layout* L, int* grid, PassGeom* geo) {
+// Grid of the pass kernel and the workspace carve-up. The partial-slot area is
+// sized for the larger of the FP64 and mixed kernels' needs, so one workspace
+// serves either precision.
+int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, Layout* L, int* grid, PassGeom* geo) {
   const int np = padded_n(n);
   int grid_max = 0;
   if (device_geo(np, &grid_max, geo) != cudaSuccess) return SCQR3_E_CUDA;
   const int64_t npanels = (m + geo->pr - 1) / geo->pr;
-  *grid = (int)(npanels < grid_max ? npanels : grid_max);
-  if (*grid < 1) *grid = 1;
+  int grid64 = (int)(npanels < grid_max ? npanels : grid_max);
+  if (grid64 < 1) grid64 = 1;
+  const int df_max = df_grid_max(np);
+  const int64_t np_df = (m + df_rows_per_panel(np) - 1) / df_rows_per_panel(np);
+  int griddf = (int)(np_df < df_max ? np_df : df_max);
+  if (griddf < 1) griddf = 1;
+  const int slots64 = grid64 * geo->groups, slotsdf = griddf * df_groups(np);
+  *grid = mixed ? griddf : grid64;
   const int E = pk_size(np);
   L->part_stride = E + 1;
-  L->n_partials = *grid * geo->groups;
+  L->n_partials = mixed ? slotsdf : slots64;
+  const int slots_alloc = slots64 > slotsdf ? slots64 : slotsdf;
   size_t off = 0;
   L->state = off;
   off = align256(off + sizeof(DevState));
@@ -116,8 +148,10 @@ int make_layout(int64_t m, int n, const scqr3_B* B, Layout* L, int* grid, PassGe
     const int64_t nblk = m / B->bs;
     off = align256(off + sizeof(double) * (size_t)nblk * (B->bs * (B->bs + 1) / 2));
   }
+  L->dfr = off;  // R_k and 1/r_jj split into float pairs (mixed form)
+  off = align256(off + sizeof(float2) * (size_t)(E + np));
   L->partials = off;
-  off = align256(off + sizeof(double) * (size_t)L->n_partials * L->part_stride);
+  off = align256(off + sizeof(double) * (size_t)slots_alloc * L->part_stride);
   L->total = off;
   return SCQR3_OK;
 }
@@ -167,7 +201,7 @@ extern "C" int scqr3_workspace_bytes(int64_t m, int n, const scqr3_B* B, const s
   Layout L;
   int grid;
   PassGeom geo;
-  const int r = make_layout(m, n, B, &L, &grid, &geo);
+  const int r = make_layout(m, n, B, opts && opts->precision == SCQR3_PREC_MIXED, &L, &grid, &geo);
   if (r != SCQR3_OK) return r;
   *bytes = L.total;
   return SCQR3_OK;
@@ -193,10 +227,11 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   if ((const void*)Q == (const void*)X && ldq != ldx) return -7;
   if (((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
 
+  const bool mixed = opts && opts->precision == SCQR3_PREC_MIXED;
   Layout L;
   int grid;
   PassGeom geo;
-  const int r = make_layout(m, n, B, &L, &grid, &geo);
+  const int r = make_layout(m, n, B, mixed, &L, &grid, &geo);
   if (r != SCQR3_OK) return r;
   if (workspace_bytes < L.total) return SCQR3_E_WORKSPACE;
 
@@ -208,6 +243,8 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   double* racc = (double*)(ws + L.racc);
   double* lt = B ? (double*)(ws + L.lt) : nullptr;
   double* partials = (double*)(ws + L.partials);
+  float2* rk2 = (float2*)(ws + L.dfr);
+  float2* rinv2 = rk2 + pk_size(padded_n(n));
 
   Params P;
   P.m = m;
@@ -227,7 +264,11 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
 
   // Pass 1, Alg. 3 line 2: A = X^T X (or X^T B X).
   tick(s, SCQR3_KERNEL_GRAM, 0);
-  launch_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, lt, partials, L.part_stride, st);
+  if (mixed)
+    launch_df_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, rk2, rinv2, partials,
+                   L.part_stride, st);
+  else
+    launch_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, lt, partials, L.part_stride, st);
   tick(s, SCQR3_KERNEL_REDUCE, 0);
   launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, -1);
   tick(s, SCQR3_KERNEL_CHOL, 0);
@@ -237,8 +278,12 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
     const double* src = (k == 0) ? X : Q;
     const int64_t lds = (k == 0) ? ldx : ldq;
     tick(s, SCQR3_KERNEL_PASS, k);
-    launch_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, lt, partials,
-                L.part_stride, st);
+    if (mixed)
+      launch_df_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, rk2, rinv2,
+                     partials, L.part_stride, st);
+    else
+      launch_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, lt, partials,
+                  L.part_stride, st);
     if (k + 1 < P.max_passes) {
       tick(s, SCQR3_KERNEL_REDUCE, k + 1);
       launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, k);

@@ -127,8 +127,12 @@ def _b_struct(B, normb):
     return b, ctypes.byref(b)
 
 
-def _opts(max_passes, norm_x2):
-    o = _Opts(int(max_passes), 0, float(norm_x2))
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+
+def _opts(max_passes, norm_x2, precision=PREC_FP64):
+    o = _Opts(int(max_passes), int(precision), float(norm_x2))
     return o, ctypes.byref(o)
 
 
@@ -158,7 +162,7 @@ class Workspace:
 
 def factor(X, B=None, *, max_passes: int = 0, norm_x2: float = 0.0, normb: float = 0.0,
            Q=None, R=None, Rpass=None, workspace: Workspace | None = None, stream=None,
-           read_info: bool = True):
+           read_info: bool = True, precision: int = PREC_FP64):
     """Shifted CholeskyQR3 of X (m x n, float64 CUDA tensor) through scqr3_factor.
 
     Returns (Q, R, info). Q may be passed as X for an in-place factorization.
@@ -182,7 +186,7 @@ def factor(X, B=None, *, max_passes: int = 0, norm_x2: float = 0.0, normb: float
     if workspace is None:
         workspace = Workspace(m, n, B, max_passes, device=X.device)
     b, bp = _b_struct(B, normb)
-    o, op = _opts(max_passes, norm_x2)
+    o, op = _opts(max_passes, norm_x2, precision)
     if stream is None:
         stream = torch.cuda.current_stream(X.device).cuda_stream
     r = lib().scqr3_factor(X.data_ptr(), m, n, X.stride(0), bp, Q.data_ptr(), Q.stride(0),
