@@ -446,10 +446,8 @@ int df_rows_per_panel(int np) {
 }
 
 void launch_df_pass(int np, int grid, cudaStream_t s, const double* src, int64_t lds, double* dst,
-                    int64_t ldd, const Params& P, int pass, const double* rk, float2* rk2,
-                    float2* rinv2, double* partials, int part_stride, DevState* st) {
-  (void)rk2;
-  (void)rinv2;
+                    int64_t ldd, const Params& P, int pass, const double* rk, double* partials,
+                    int part_stride, DevState* st) {
   switch (np) {
 #define SCQR3_DF2(NPV)                                                                            \
   case NPV:                                                                                       \

@@ -29,8 +29,8 @@ cudaError_t df_occupancy(int np, int* per_sm);
 int df_groups(int np);
 int df_rows_per_panel(int np);
 void launch_df_pass(int np, int grid, cudaStream_t s, const double* src, int64_t lds, double* dst,
-                    int64_t ldd, const Params& P, int pass, const double* rk, float2* rk2,
-                    float2* rinv2, double* partials, int part_stride, DevState* st);
+                    int64_t ldd, const Params& P, int pass, const double* rk, double* partials,
+                    int part_stride, DevState* st);
 
 namespace {
 
@@ -148,8 +148,6 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, Layout* L, int* 
     const int64_t nblk = m / B->bs;
     off = align256(off + sizeof(double) * (size_t)nblk * (B->bs * (B->bs + 1) / 2));
   }
-  L->dfr = off;  // R_k and 1/r_jj split into float pairs (mixed form)
-  off = align256(off + sizeof(float2) * (size_t)(E + np));
   L->partials = off;
   off = align256(off + sizeof(double) * (size_t)slots_alloc * L->part_stride);
   L->total = off;
@@ -243,8 +241,6 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   double* racc = (double*)(ws + L.racc);
   double* lt = B ? (double*)(ws + L.lt) : nullptr;
   double* partials = (double*)(ws + L.partials);
-  float2* rk2 = (float2*)(ws + L.dfr);
-  float2* rinv2 = rk2 + pk_size(padded_n(n));
 
   Params P;
   P.m = m;
@@ -265,8 +261,7 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   // Pass 1, Alg. 3 line 2: A = X^T X (or X^T B X).
   tick(s, SCQR3_KERNEL_GRAM, 0);
   if (mixed)
-    launch_df_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, rk2, rinv2, partials,
-                   L.part_stride, st);
+    launch_df_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, partials, L.part_stride, st);
   else
     launch_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, lt, partials, L.part_stride, st);
   tick(s, SCQR3_KERNEL_REDUCE, 0);
@@ -279,8 +274,8 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
     const int64_t lds = (k == 0) ? ldx : ldq;
     tick(s, SCQR3_KERNEL_PASS, k);
     if (mixed)
-      launch_df_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, rk2, rinv2,
-                     partials, L.part_stride, st);
+      launch_df_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, partials,
+                     L.part_stride, st);
     else
       launch_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, lt, partials,
                   L.part_stride, st);

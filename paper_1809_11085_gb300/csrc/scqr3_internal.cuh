@@ -42,7 +42,7 @@ struct Params {
 
 // Workspace carve-up (byte offsets from the base, each 256-aligned).
 struct Layout {
-  size_t state, gram, rstack, racc, lt, dfr, partials, total;
+  size_t state, gram, rstack, racc, lt, partials, total;
   int n_partials;    // partial Gram slots used by this call (grid CTAs x groups)
   int part_stride;   // doubles per partial slot: pk_size(np) + 1 (||.||_F^2)
 };
