@@ -125,6 +125,53 @@ int scqr3_factor(const double *X, int64_t m, int n, int64_t ldx,
                  const scqr3_opts *opts, scqr3_info *info, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched form (FP64, B = I): many independent, uneven factorizations, each
+ * exactly as scqr3_factor would compute it (Alg. 3 with the breakdown rule
+ * of Alg. 2), in one fixed launch sequence. Not in the paper, whose
+ * experiments factor one matrix at a time.
+ *
+ * Each phase is one persistent launch: every CTA takes tiles (a run of row
+ * panels of one matrix) from an atomic queue, largest n first; each tile
+ * writes its own partial Gram matrix, and each matrix's tiles are summed in
+ * tile order, so results do not depend on scheduling. Shift, Cholesky and
+ * pass bookkeeping run with one CTA per matrix.
+ *
+ * Use: scqr3_batch_plan_create (host only: validates the items, builds the
+ * tile list, returns the workspace size); scqr3_batch_plan_upload (copies the
+ * tables into the workspace and synchronizes `stream`; call before any
+ * capture); then scqr3_factor_batched any number of times -- it only queues
+ * memsets and kernels on `stream`, so it can be captured in a CUDA graph and
+ * replayed; finally scqr3_batch_plan_destroy. The workspace and all item
+ * buffers must stay valid and unmoved while the plan is used. */
+typedef struct {
+  const double *X;    /* device, m x n row-major, ldx >= n                  */
+  double *Q;          /* device, m x n, ldq >= n (may equal X, ldq == ldx)   */
+  double *R;          /* device, n x n                                       */
+  double *Rpass;      /* device, SCQR3_MAX_PASSES * n * n, or NULL           */
+  scqr3_info *info;   /* device record of this matrix's call                 */
+  int64_t m;
+  int n;              /* 1 .. SCQR3_MAX_N                                    */
+  int64_t ldx, ldq;
+} scqr3_batch_item;
+
+typedef struct {
+  int ctas_per_sm;     /* persistent CTAs per SM (0: 1)                      */
+  int tile_panels[4];  /* row panels per tile for n padded to 16, 32, 64, 128
+                          (0: 8); panels are 256 rows (128 for n > 64)      */
+} scqr3_batch_tuning;
+
+typedef struct scqr3_batch_plan scqr3_batch_plan;
+
+int scqr3_batch_plan_create(const scqr3_batch_item *items, int count,
+                            const scqr3_opts *opts,
+                            const scqr3_batch_tuning *tuning,
+                            scqr3_batch_plan **plan, size_t *workspace_bytes);
+int scqr3_batch_plan_upload(scqr3_batch_plan *plan, void *workspace,
+                            size_t workspace_bytes, void *stream);
+int scqr3_factor_batched(const scqr3_batch_plan *plan, void *stream);
+void scqr3_batch_plan_destroy(scqr3_batch_plan *plan);
+
+/* ---------------------------------------------------------------------------
  * Adjoint (reverse mode) of scqr3_factor for B = I. Not in the paper; it is
  * the chain rule through the passes of Alg. 2/3 (Q_k = Q_{k-1} R_k^{-1},
  * R_k = chol(Q_{k-1}^T Q_{k-1} + s_k I), R = R_P ... R_1) with each shift s_k
