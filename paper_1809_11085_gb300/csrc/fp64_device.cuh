@@ -20,10 +20,13 @@ namespace scqr3 {
 // NP+1 entries in all, so every thread of a group does the same work and the
 // columns read by neighbouring lanes are neighbouring words of shared memory.
 template <int NP> struct Cfg;
-template <> struct Cfg<16>  { static constexpr int PR = 256, T = 8,   H = 1; };
-template <> struct Cfg<32>  { static constexpr int PR = 256, T = 16,  H = 1; };
-template <> struct Cfg<64>  { static constexpr int PR = 256, T = 32,  H = 1; };
-template <> struct Cfg<128> { static constexpr int PR = 128, T = 128, H = 2; };
+//   MINB  resident CTAs per SM the register budget is sized for (small n
+//         needs few registers; more CTAs let one CTA's loads overlap another's
+//         arithmetic)
+template <> struct Cfg<16>  { static constexpr int PR = 256, T = 8,   H = 1, MINB = 3; };
+template <> struct Cfg<32>  { static constexpr int PR = 256, T = 16,  H = 1, MINB = 2; };
+template <> struct Cfg<64>  { static constexpr int PR = 256, T = 32,  H = 1, MINB = 1; };
+template <> struct Cfg<128> { static constexpr int PR = 128, T = 128, H = 2, MINB = 1; };
 
 template <int NP> struct Geo {
   static constexpr int PR = Cfg<NP>::PR, T = Cfg<NP>::T, H = Cfg<NP>::H;
@@ -138,18 +141,34 @@ __device__ __forceinline__ void pass_segment(const double* src, int64_t lds, dou
 
     if (do_trsm) {
       // Row-wise substitution q_i^T R_k = x_i^T (Eq. backward2), one row per
-      // thread, updating the not-yet-solved entries right after each q_ij
-      // (same ascending-k summation as the left-looking form, but with
-      // n - j independent FMAs per step instead of one dependent chain).
+      // thread, left-looking in blocks of eight columns held in registers:
+      // t_c -= q_i r_ic for every solved q_i (ascending i, one load of q_i
+      // and eight broadcast loads of R_k per eight independent FMAs, no
+      // store in the loop), then the 8 x 8 diagonal block by substitution.
       if (tid < rows) {
         double* row = panel + tid * g::LD;
-        for (int j = 0; j < n; ++j) {
-          const double q = row[j] * rinv[j];
-          row[j] = q;
-          if (oblique) f2 = fma(q, q, f2);
-          const double* rj = rp + pk_row(NP, j) - j;  // rj[l] = R_k(j, l)
-#pragma unroll 4
-          for (int l = j + 1; l < n; ++l) row[l] = fma(-q, rj[l], row[l]);
+        const int nb = (n + 7) / 8;
+        for (int J = 0; J < nb; ++J) {
+          double t[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) t[c] = row[8 * J + c];
+          for (int i = 0; i < 8 * J; ++i) {
+            const double q = row[i];
+            const double* ri = rp + pk_row(NP, i) - i + 8 * J;  // R_k(i, 8J .. 8J+7)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) t[c] = fma(-q, ri[c], t[c]);
+          }
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const double q = t[c] * rinv[8 * J + c];
+            t[c] = q;
+            if (oblique && 8 * J + c < n) f2 = fma(q, q, f2);
+            const double* rc = rp + pk_row(NP, 8 * J + c) - (8 * J + c) + 8 * J;  // R_k(8J+c, 8J..)
+#pragma unroll
+            for (int c2 = c + 1; c2 < 8; ++c2) t[c2] = fma(-q, rc[c2], t[c2]);
+          }
+#pragma unroll
+          for (int c = 0; c < 8; ++c) row[8 * J + c] = t[c];
         }
       }
       __syncthreads();

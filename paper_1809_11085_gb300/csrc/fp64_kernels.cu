@@ -22,7 +22,7 @@
 namespace scqr3 {
 
 template <int NP>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, Cfg<NP>::MINB)
 pass_kernel(const double* src, int64_t lds, double* dst, int64_t ldd, Params P, int pass,
             const double* __restrict__ rk, const double* __restrict__ lt,
             double* __restrict__ partials, int part_stride, DevState* __restrict__ st) {
