@@ -35,7 +35,8 @@ extern "C" {
 #endif
 
 #define SCQR3_MAX_PASSES 8   /* upper limit of opts.max_passes            */
-#define SCQR3_MAX_N 128      /* largest n of the FP64 path                 */
+#define SCQR3_MAX_N 256      /* largest n (FP64, B = I); the oblique, mixed,
+                                batched and adjoint forms take n <= 128    */
 
 /* Status codes (return values and scqr3_info.status).
  *   > 0  : the SHIFTED Cholesky broke down at this 1-based column, i.e.
@@ -235,6 +236,7 @@ int scqr3_factor_noalloc(const double *X, int64_t m, int n, int64_t ldx,
 #define SCQR3_KERNEL_REDUCE 2   /* fixed-order sum of partial Grams         */
 #define SCQR3_KERNEL_CHOL 3     /* shift, Cholesky, R := R_k R, bookkeeping */
 #define SCQR3_KERNEL_BFACTOR 4  /* per-block Cholesky of the oblique B      */
+#define SCQR3_KERNEL_TRSM 5     /* Q := Q R_k^{-1} alone (n > 128)          */
 
 typedef struct {
   int kernel;  /* SCQR3_KERNEL_*                                          */

@@ -138,11 +138,12 @@ batched_chol_kernel(const BItem* __restrict__ items, int pass) {
     for (int e = threadIdx.x; e < (int)(sizeof(scqr3_info) / sizeof(int)); e += blockDim.x) w[e] = 0;
     __syncthreads();
   }
+  extern __shared__ __align__(16) double sm[];
   switch (it.P.np) {
-    case 16: chol_body<16>(it.P, pass, it.gram, it.rstack, it.racc, it.R, it.Rpass, it.st, it.info); break;
-    case 32: chol_body<32>(it.P, pass, it.gram, it.rstack, it.racc, it.R, it.Rpass, it.st, it.info); break;
-    case 64: chol_body<64>(it.P, pass, it.gram, it.rstack, it.racc, it.R, it.Rpass, it.st, it.info); break;
-    default: chol_body<128>(it.P, pass, it.gram, it.rstack, it.racc, it.R, it.Rpass, it.st, it.info); break;
+    case 16: chol_body<16>(it.P, pass, it.gram, it.rstack, it.racc, it.R, it.Rpass, it.st, it.info, sm, sm + pk_size(16)); break;
+    case 32: chol_body<32>(it.P, pass, it.gram, it.rstack, it.racc, it.R, it.Rpass, it.st, it.info, sm, sm + pk_size(32)); break;
+    case 64: chol_body<64>(it.P, pass, it.gram, it.rstack, it.racc, it.R, it.Rpass, it.st, it.info, sm, sm + pk_size(64)); break;
+    default: chol_body<128>(it.P, pass, it.gram, it.rstack, it.racc, it.R, it.Rpass, it.st, it.info, sm, sm + pk_size(128)); break;
   }
 }
 

@@ -278,15 +278,15 @@ __device__ int chol_packed(double* S, int n, int* fail_sh) {
   return 0;
 }
 
+// S (packed A, then R_k) and Ra (packed R accumulation) are E doubles each,
+// in shared memory for NP <= 128 and in workspace memory for NP = 256.
 template <int NP>
 __device__ __forceinline__ void chol_body(const Params& P, int pass, const double* __restrict__ gram,
                                           double* __restrict__ rstack, double* __restrict__ racc,
                                           double* __restrict__ Rout, double* __restrict__ Rpass,
-                                          DevState* __restrict__ st, scqr3_info* __restrict__ info) {
+                                          DevState* __restrict__ st, scqr3_info* __restrict__ info,
+                                          double* S, double* Ra) {
   constexpr int E = pk_size(NP);
-  extern __shared__ __align__(16) double sm[];
-  double* S = sm;        // packed A, then R_k
-  double* Ra = sm + E;   // packed R accumulation
   __shared__ int fail_sh;
   __shared__ double s_sh, nrm_sh;
   __shared__ int shifted_sh, ufail_sh;

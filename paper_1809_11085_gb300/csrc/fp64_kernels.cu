@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(512, 1)
 chol_kernel(Params P, int pass, const double* __restrict__ gram, double* __restrict__ rstack,
             double* __restrict__ racc, double* __restrict__ Rout, double* __restrict__ Rpass,
             DevState* __restrict__ st, scqr3_info* __restrict__ info) {
-  chol_body<NP>(P, pass, gram, rstack, racc, Rout, Rpass, st, info);
+  extern __shared__ __align__(16) double sm[];
+  chol_body<NP>(P, pass, gram, rstack, racc, Rout, Rpass, st, info, sm, sm + pk_size(NP));
 }
 
 // -------------------------------------------------------------------------------------------

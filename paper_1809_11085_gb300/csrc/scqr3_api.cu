@@ -24,6 +24,14 @@ void launch_chol(int np, cudaStream_t s, const Params& P, int pass, const double
                  scqr3_info* info);
 void launch_bfactor(cudaStream_t s, int bs, const double* B, int64_t nblk, double* lt, DevState* st,
                     int sms);
+cudaError_t n256_setup(int* trsm_per_sm, int* gram_per_sm);
+void launch_trsm256(int grid, cudaStream_t s, const double* src, int64_t lds, double* dst, int64_t ldd,
+                    const Params& P, int pass, const double* rk, const DevState* st);
+void launch_gram256(int grid, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
+                    double* partials, int part_stride, const DevState* st);
+void launch_chol256(cudaStream_t s, const Params& P, int pass, const double* gram, double* rstack,
+                    double* racc, double* Rout, double* Rpass, DevState* st, scqr3_info* info, double* S,
+                    double* Ra);
 cudaError_t df_setup();
 cudaError_t df_occupancy(int np, int* per_sm);
 int df_groups(int np);
@@ -39,6 +47,7 @@ int padded_n(int n) {
   if (n <= 32) return 32;
   if (n <= 64) return 64;
   if (n <= 128) return 128;
+  if (n <= 256) return 256;
   return 0;
 }
 
@@ -49,6 +58,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct DevGeo {
   bool ready = false;
   int sms = 0;
+  int trsm256_per_sm = 0, gram256_per_sm = 0;
   int ctas_per_sm[5] = {0, 0, 0, 0, 0};
   int df_ctas_per_sm[5] = {0, 0, 0, 0, 0};
   PassGeom geo[5];
@@ -74,6 +84,9 @@ cudaError_t device_geo(int np, int* grid_max, PassGeom* geo) {
       if (e != cudaSuccess) return e;
       if (d.ctas_per_sm[np_slot(s)] < 1) return cudaErrorInvalidConfiguration;
     }
+    e = n256_setup(&d.trsm256_per_sm, &d.gram256_per_sm);
+    if (e != cudaSuccess) return e;
+    if (d.trsm256_per_sm < 1 || d.gram256_per_sm < 1) return cudaErrorInvalidConfiguration;
     e = df_setup();
     if (e != cudaSuccess) return e;
     for (int s : {16, 32, 64, 128}) {
@@ -83,9 +96,23 @@ cudaError_t device_geo(int np, int* grid_max, PassGeom* geo) {
     }
     d.ready = true;
   }
+  if (np == 256) {
+    // gram256: two roles of one CTA per SM each half; trsm256 sized separately
+    *grid_max = d.sms * d.gram256_per_sm;
+    *geo = PassGeom{256, 64, 1, kThreads, 4, 65, 0};
+    return cudaSuccess;
+  }
   *grid_max = d.sms * d.ctas_per_sm[np_slot(np)];
   *geo = d.geo[np_slot(np)];
   return cudaSuccess;
+}
+
+int trsm256_grid(int64_t m) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int64_t np = (m + 255) / 256;
+  const int64_t g = (int64_t)g_geo[dev].sms * g_geo[dev].trsm256_per_sm;
+  return (int)(np < g ? (np < 1 ? 1 : np) : g);
 }
 
 int df_grid_max(int np) {
@@ -111,6 +138,8 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
   if (opts && opts->precision != SCQR3_PREC_FP64 && opts->precision != SCQR3_PREC_MIXED) return -12;
   if (opts && opts->precision == SCQR3_PREC_MIXED && B) return -5;  // mixed form: B = I only
   if (padded_n(n) == 0) return SCQR3_E_UNSUPPORTED;
+  // n > 128: FP64, B = I only
+  if (n > 128 && (B || (opts && opts->precision == SCQR3_PREC_MIXED))) return SCQR3_E_UNSUPPORTED;
   return SCQR3_OK;
 }
 
@@ -124,7 +153,11 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, Layout* L, int* 
   const int64_t npanels = (m + geo->pr - 1) / geo->pr;
   int grid64 = (int)(npanels < grid_max ? npanels : grid_max);
   if (grid64 < 1) grid64 = 1;
-  const int df_max = df_grid_max(np);
+  if (np == 256) {
+    grid64 = grid_max & ~1;  // two roles; even
+    if (grid64 < 2) grid64 = 2;
+  }
+  const int df_max = np == 256 ? 1 : df_grid_max(np);
   const int64_t np_df = (m + df_rows_per_panel(np) - 1) / df_rows_per_panel(np);
   int griddf = (int)(np_df < df_max ? np_df : df_max);
   if (griddf < 1) griddf = 1;
@@ -143,6 +176,8 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, Layout* L, int* 
   off = align256(off + sizeof(double) * (size_t)E * SCQR3_MAX_PASSES);
   L->racc = off;
   off = align256(off + sizeof(double) * E);
+  L->chol = off;  // Cholesky work buffers in global memory (n > 128)
+  if (np == 256) off = align256(off + sizeof(double) * 2 * (size_t)E);
   L->lt = off;
   if (B) {
     const int64_t nblk = m / B->bs;
@@ -256,6 +291,37 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   if (B) {
     tick(s, SCQR3_KERNEL_BFACTOR, 0);
     launch_bfactor(s, B->bs, B->blocks, m / B->bs, lt, st, sm_count());
+  }
+
+  if (P.np == 256) {
+    // Same sequence with the substitution and the Gram in separate kernels.
+    const int E256 = pk_size(256);
+    double* S = (double*)(ws + L.chol);
+    double* Ra = S + E256;
+    const int tg = trsm256_grid(m);
+    tick(s, SCQR3_KERNEL_GRAM, 0);
+    launch_gram256(grid, s, X, ldx, P, -1, partials, L.part_stride, st);
+    tick(s, SCQR3_KERNEL_REDUCE, 0);
+    launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, -1);
+    tick(s, SCQR3_KERNEL_CHOL, 0);
+    launch_chol256(s, P, 0, gram, rstack, racc, R, Rpass, st, info, S, Ra);
+    for (int k = 0; k < P.max_passes; ++k) {
+      const double* src = (k == 0) ? X : Q;
+      const int64_t lds = (k == 0) ? ldx : ldq;
+      tick(s, SCQR3_KERNEL_TRSM, k);
+      launch_trsm256(tg, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E256, st);
+      if (k + 1 < P.max_passes) {
+        tick(s, SCQR3_KERNEL_GRAM, k + 1);
+        launch_gram256(grid, s, Q, ldq, P, k, partials, L.part_stride, st);
+        tick(s, SCQR3_KERNEL_REDUCE, k + 1);
+        launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, k);
+        tick(s, SCQR3_KERNEL_CHOL, k + 1);
+        launch_chol256(s, P, k + 1, gram, rstack, racc, R, Rpass, st, info, S, Ra);
+      }
+    }
+    tick(s, -1, -1);
+    if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
+    return SCQR3_OK;
   }
 
   // Pass 1, Alg. 3 line 2: A = X^T X (or X^T B X).

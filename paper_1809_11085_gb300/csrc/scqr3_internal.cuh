@@ -33,7 +33,7 @@ struct DevState {
 struct Params {
   int64_t m;
   int n;
-  int np;            // padded n: 16, 32, 64 or 128
+  int np;            // padded n: 16, 32, 64, 128 or 256
   int max_passes;
   int bs;            // 0: B = I; else block size of B
   double norm_x2;    // opts.norm_x2
@@ -42,7 +42,7 @@ struct Params {
 
 // Workspace carve-up (byte offsets from the base, each 256-aligned).
 struct Layout {
-  size_t state, gram, rstack, racc, lt, partials, total;
+  size_t state, gram, rstack, racc, chol, lt, partials, total;
   int n_partials;    // partial Gram slots used by this call (grid CTAs x groups)
   int part_stride;   // doubles per partial slot: pk_size(np) + 1 (||.||_F^2)
 };

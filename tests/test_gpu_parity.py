@@ -218,3 +218,23 @@ def test_oblique_not_spd_block_is_reported():
     Bblk[3] = -np.eye(8)
     _, _, info = run_gpu(testmat(m, n, 10.0, seed=2501), Bblk)
     assert info.status == scqr3.E_B_NOT_SPD
+
+
+# ------------------------------------------------------------------------------- 128 < n <= 256
+
+@pytest.mark.parametrize("n", [129, 200, 256])
+@pytest.mark.parametrize("kappa", [1e4, 1e10])
+def test_wide_n(n, kappa):
+    m = 6000 + 37
+    Xh = testmat(m, n, kappa, seed=2600 + n)
+    check_pair(Xh, kappa)
+
+
+def test_wide_n_square_and_rejections():
+    Xh = testmat(256, 256, 1e6, seed=2700)
+    check_pair(Xh, 1e6)
+    X = torch.zeros((1024, 200), dtype=torch.float64, device="cuda")
+    with pytest.raises(scqr3.ScqrError):
+        scqr3.factor(X, precision=scqr3.PREC_MIXED)
+    with pytest.raises(scqr3.ScqrError):
+        scqr3.factor(torch.zeros((1024, 257), dtype=torch.float64, device="cuda"))
