@@ -38,7 +38,7 @@ METRIC = "sCQR3 rows/s & % roofline at mÃ—n; mixed/batched vs FP64 at â€–Qáµ€Qâˆ
 FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
 # DRAM bytes per row of a fused solve+Gram launch of pass_kernel<64>, from the ncu capture
 # summarised in profiles/pass_kernel_fp64_1048576x64_full.md; valid only for that kernel source.
-PROFILED_KERNEL_SHA = "978be09c5236b282"
+PROFILED_KERNEL_SHA = "97a248845d02384d"
 PROFILED_BYTES_PER_ROW = 992.4
 
 
@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--legs", default="all", choices=["all", "main"],
+                    help="main: only the headline workload; all: also the other configurations")
     return ap.parse_args()
 
 
@@ -64,8 +66,10 @@ def profiled_traffic(m, n):
     """roofline.traffic for a fused launch, or None if the kernel changed since the capture."""
     import hashlib
 
-    src = os.path.join(ROOT, "paper_1809_11085_gb300", "csrc", "fp64_kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("fp64_device.cuh", "fp64_kernels.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1809_11085_gb300", "csrc", f), "rb").read())
+    sha = h.hexdigest()[:16]
     if sha != PROFILED_KERNEL_SHA or n != 64:
         return None
     return PROFILED_BYTES_PER_ROW * m
@@ -365,6 +369,10 @@ def run_gpu(args, rank, world, local_rank):
                "sample": "%d x %d X = U diag(sigma) V^T, kappa=%g, one factorization (%d passes) in %.1f s"
                          % (rows, n, kappa, p, t)}
 
+    legs = {}
+    if args.legs == "all":
+        legs = extra_legs(torch, dev, stream, args)
+
     fl = flops_of(m, n, passes)
     out = {
         "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
@@ -391,10 +399,148 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "kappa_sweep": sweep,
+        **legs,
     }
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- other configurations
+
+def _time(torch, stream, fn, reps=1):
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def _orth(torch, Q, BQ=None):
+    n = Q.shape[1]
+    G = Q.T @ (Q if BQ is None else BQ)
+    G -= torch.eye(n, dtype=torch.float64, device=Q.device)
+    return torch.linalg.matrix_norm(G, 2).item()
+
+
+def extra_legs(torch, dev, stream, args):
+    """The other configurations, one factorization timed each (after one warm-up)."""
+    from paper_1809_11085_gb300 import batched, scqr3
+    from paper_1809_11085_gb300.testmat import (batched_shapes, block_diag_spd_torch,
+                                                repeated_small_sigma, testmat_torch)
+
+    legs = {}
+    free = lambda: torch.cuda.empty_cache()  # noqa: E731
+
+    # FP64 scale-up at n = 256
+    m, n = 1048576, 256
+    sweep = {}
+    for kk in (1e2, 1e6, 1e10, 1e14, 1e15, "repeated"):
+        sig = repeated_small_sigma(n, 8, 1e-14, 1e7) if kk == "repeated" else None
+        X, _, _ = testmat_torch(m, n, 0.0 if sig is not None else kk, seed=1250 + len(sweep), device=dev, sigma=sig)
+        Q = torch.empty_like(X)
+        ws = scqr3.Workspace(m, n, device=dev)
+        ms = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, workspace=ws, read_info=False))
+        inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
+        sweep[str(kk)] = {"ms": round(ms, 2), "rows_per_s": m / (ms * 1e-3), "passes": inf.passes,
+                          "status": inf.status, "orth": _orth(torch, Q),
+                          "tflops": flops_of(m, n, inf.passes) / (ms * 1e-3) / 1e12}
+        del X, Q, ws
+        free()
+    legs["scaleup_n256"] = {"workload": "FP64 sCQR3, X = U diag(sigma) V^T, 1048576 x 256", "kappa": sweep}
+
+    # mixed form vs FP64 on the same matrices
+    mixed = {}
+    for (mm, nn, kk) in ((16777216, 64, 1e10), (8388608, 128, 1e4), (8388608, 128, 1e7), (8388608, 128, 1e10)):
+        X, _, _ = testmat_torch(mm, nn, kk, seed=1400 + nn, device=dev)
+        Q = torch.empty_like(X)
+        ws = scqr3.Workspace(mm, nn, device=dev)
+        R64 = torch.empty((nn, nn), dtype=torch.float64, device=dev)
+        Rmx = torch.empty_like(R64)
+        t64 = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, R=R64, workspace=ws, read_info=False))
+        o64 = _orth(torch, Q)
+        tmx = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, R=Rmx, workspace=ws, read_info=False,
+                                                        precision=scqr3.PREC_MIXED))
+        inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
+        res = (torch.linalg.matrix_norm(X - Q @ Rmx) / torch.linalg.matrix_norm(X)).item()
+        dR = (torch.linalg.matrix_norm(Rmx - R64) / torch.linalg.matrix_norm(R64)).item()
+        mixed["%dx%d_kappa%g" % (mm, nn, kk)] = {
+            "fp64_ms": round(t64, 2), "mixed_ms": round(tmx, 2), "speedup": t64 / tmx,
+            "mixed_rows_per_s": mm / (tmx * 1e-3), "orth_fp64": o64, "orth_mixed": _orth(torch, Q),
+            "resid_mixed": res, "dR_vs_fp64": dR, "passes": inf.passes}
+        del X, Q, ws
+        free()
+    legs["mixed"] = {"workload": "same X through precision=FP64 and precision=MIXED (FP32 pairs + FP64)",
+                     "results": mixed}
+
+    # oblique inner product, block-diagonal B (8 x 8 blocks G^T G + 0.1 I)
+    mm, nn = 4194304, 128
+    X, _, _ = testmat_torch(mm, nn, 1e10, seed=1300, device=dev)
+    B = block_diag_spd_torch(mm, 8, seed=1301, device=dev)
+    Q = torch.empty_like(X)
+    ws = scqr3.Workspace(mm, nn, B, device=dev)
+    ms = _time(torch, stream, lambda: scqr3.factor(X, B, Q=Q, workspace=ws, read_info=False))
+    inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
+    BQ = torch.matmul(B, Q.view(-1, 8, nn)).view(mm, nn)
+    legs["oblique"] = {"workload": "FP64 sCQR3 in the B inner product, X 4194304 x 128 (kappa 1e10), "
+                                   "B block diagonal 8x8 G^T G + 0.1 I",
+                       "ms": round(ms, 2), "rows_per_s": mm / (ms * 1e-3), "passes": inf.passes,
+                       "status": inf.status, "orth_B": _orth(torch, Q, BQ)}
+    del X, B, Q, ws, BQ
+    free()
+
+    # backward pass at the headline size
+    mm, nn = 16777216, 64
+    X, _, _ = testmat_torch(mm, nn, 1e10, seed=1500, device=dev)
+    Rpass = torch.zeros((scqr3.MAX_PASSES, nn, nn), dtype=torch.float64, device=dev)
+    Q, R, inf = scqr3.factor(X, Rpass=Rpass)
+    dQ = torch.randn(X.shape, dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(3))
+    dR = torch.randn((nn, nn), dtype=torch.float64, device=dev)
+    del X
+    bws = scqr3.BackwardWorkspace(mm, nn, device=dev)
+    dX = torch.empty_like(Q)
+    ms = _time(torch, stream, lambda: scqr3.backward(Q, Rpass, inf.passes, dQ, dR, dX=dX, workspace=bws))
+    legs["backward"] = {"workload": "adjoint of the 16777216 x 64 factorization (3 passes)", "ms": round(ms, 2),
+                        "rows_per_s": mm / (ms * 1e-3),
+                        "tflops": inf.passes * mm * 6 * nn * nn / (ms * 1e-3) / 1e12}
+    del Q, R, dQ, dX, bws, Rpass
+    free()
+
+    # batched: 512 uneven matrices, one graph vs 512 single calls
+    shapes = batched_shapes(512, seed=5)
+    Xs = [testmat_torch(a, b, c, seed=100 + i, device=dev)[0] for i, (a, b, c) in enumerate(shapes)]
+    fl = sum(6 * a * b * b for a, b, _ in shapes)
+    wss = {}
+    Qs = [torch.empty_like(X) for X in Xs]
+
+    def seq():
+        for X, Qi in zip(Xs, Qs):
+            key = tuple(X.shape)
+            if key not in wss:
+                wss[key] = scqr3.Workspace(*key, device=dev)
+            scqr3.factor(X, Q=Qi, workspace=wss[key], read_info=False)
+
+    tseq = _time(torch, stream, seq)
+    del Qs, wss
+    free()
+    tune, _ = batched.autotune(Xs, candidates=(8, 32), reps=1)
+    bq = batched.BatchedQR(Xs, tune=tune, graph=True)
+    tb = _time(torch, stream, bq.run)
+    infos = bq.infos()
+    worst = max(_orth(torch, Q) for Q in bq.Qs)
+    legs["batched"] = {"workload": "512 X_i, m_i ~ U[2000, 200000], n_i in {16,32,64,128}, log10 kappa_i ~ U[2,12]",
+                       "graph_ms": round(tb, 2), "sequential_ms": round(tseq, 2), "speedup": tseq / tb,
+                       "tflops_6mn2": fl / (tb * 1e-3) / 1e12, "worst_orth": worst,
+                       "all_ok": all(i.status == 0 for i in infos), "tuning": tune}
+    del bq, Xs
+    free()
+    return legs
 
 
 def main():
