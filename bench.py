@@ -75,6 +75,20 @@ def profiled_traffic(m, n):
     return PROFILED_BYTES_PER_ROW * m
 
 
+def max_over_ranks(ms, dist, device):
+    """Slowest rank's time (every rank gets it): the job ends when the last replica does."""
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def replica_value(m, world, ms):
+    """Whole-job rows/s of `world` independent replicas of m rows, timed by the slowest."""
+    return world * m / (ms * 1e-3)
+
+
 def flops_of(m, n, passes):
     """Algorithmic FP64 flops of one factorization that ran `passes` passes:
     each pass is one Gram (n(n+1) flops per row: n(n+1)/2 FMAs) and one
@@ -282,12 +296,10 @@ def run_gpu(args, rank, world, local_rank):
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+        ms = max_over_ranks(ms, dist, dev)
 
     passes = info.passes
-    value = world * m / (ms * 1e-3)
+    value = replica_value(m, world, ms)
     # dominant kernel: pass_kernel launches that did work
     kflops, kms, kl = 0.0, 0.0, 0
     share = {}
