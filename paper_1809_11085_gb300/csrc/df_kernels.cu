@@ -395,6 +395,222 @@ df2_pass_kernel(const double* src, int64_t lds, double* dst, int64_t ldd, Params
   if (tid < g::G) partials[((int64_t)blockIdx.x * g::G + tid) * part_stride + g::E] = 0.0;
 }
 
+// -------------------------------------------------------------------------------------------
+// Version for NP = 64 and 128: panels of 128 rows,
+//  * two threads per row in the solve (adjacent lanes; each owns four of the
+//    eight columns of a block, the first lane hands its four solved values to
+//    the second by shuffle), so every thread of the CTA solves;
+//  * R_k staged one 8-column block at a time (the panel with its mirrored
+//    tail fills most of shared memory for NP = 128);
+//  * cyclic Gram. NP = 128: the whole CTA is one group, thread (j, half) owns
+//    the entries (j, j+d) for d in [33 half, 33 half + 33) (d <= 64; d = 64
+//    only for j < 64). NP = 64: four groups of 64 threads, each over 32 rows
+//    of the panel, thread j owning d = 0..31 plus d = 32 for j < 32;
+//  * NP = 64 fits two CTAs per SM, so one CTA's loads overlap the other's
+//    arithmetic.
+template <int NP> struct DfpCfg;
+template <> struct DfpCfg<64>  { static constexpr int GT = 64,  MINB = 2; };
+template <> struct DfpCfg<128> { static constexpr int GT = 256, MINB = 1; };
+
+template <int NP> struct DfpGeo {
+  static constexpr int PR = 128, HALF = NP / 2;
+  static constexpr int GT = DfpCfg<NP>::GT;       // threads of a Gram group
+  static constexpr int G = kThreads / GT;         // groups
+  static constexpr int RG = PR / G;               // panel rows per group
+  static constexpr int C = NP == 128 ? 33 : HALF + 1;  // accumulator pairs per thread
+  static constexpr int LD = NP + HALF - 1;        // odd
+  static constexpr int E = pk_size(NP);
+  static constexpr int FLUSH = 256 / RG;          // panels per FP64 flush (256 rows)
+  static constexpr size_t smem = sizeof(float2) * ((size_t)PR * LD + NP * 8 + NP);
+};
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads, DfpCfg<NP>::MINB)
+dfp_pass_kernel(const double* src, int64_t lds, double* dst, int64_t ldd, Params P, int pass,
+                const double* __restrict__ rk, double* __restrict__ partials, int part_stride,
+                DevState* __restrict__ st) {
+  using g = DfpGeo<NP>;
+  constexpr int PR = g::PR, HALF = g::HALF, C = g::C, LD = g::LD, E = g::E;
+  extern __shared__ __align__(16) float2 fsm[];
+  float2* panel = fsm;                // PR x LD
+  float2* rb = panel + PR * LD;       // R_k(0 .. 8J+7, 8J .. 8J+7), row-major 8 wide
+  float2* rinv = rb + NP * 8;
+
+  const int tid = threadIdx.x;
+  const int n = P.n;
+  const int64_t m = P.m;
+  bool do_trsm = false, do_gram = true;
+  if (pass >= 0) {
+    if (!st->run_trsm[pass]) return;
+    do_trsm = true;
+    do_gram = st->gram_after[pass] != 0;
+  }
+  const bool src_fp64 = pass <= 0;
+  const bool dst_fp64 = !do_gram;
+  const float2* srcf = reinterpret_cast<const float2*>(src);
+  float2* dstf = reinterpret_cast<float2*>(dst);
+  if (do_trsm && tid < NP) rinv[tid] = df_split(1.0 / rk[pk_row(NP, tid)]);
+  const int nb = (n + 7) / 8;
+
+  const int srow = tid >> 1, sh = tid & 1;  // solve: row, and which four columns
+  // Gram: row j of the entries, first d and count; group and its rows
+  const int j = tid % NP;
+  const int grp = tid / g::GT;
+  int d0, dn;
+  if (NP == 128) {
+    const int gh = tid >> 7;
+    d0 = gh * C;
+    dn = gh == 0 ? C : (j < HALF ? C - 1 : C - 2);
+  } else {
+    d0 = 0;
+    dn = j < HALF ? C : C - 1;
+  }
+  float aS[C], aC[C];
+#pragma unroll
+  for (int d = 0; d < C; ++d) { aS[d] = 0.f; aC[d] = 0.f; }
+  double* part = partials + ((int64_t)blockIdx.x * g::G + grp) * part_stride;
+  bool first_flush = true;
+  int since_flush = 0;
+
+  auto flush = [&]() {
+#pragma unroll
+    for (int dd = 0; dd < C; ++dd) {
+      if (dd >= dn) continue;
+      const int d = d0 + dd;
+      int r = j, c = j + d;
+      if (c >= NP) { c -= NP; const int t = r; r = c; c = t; }
+      const double v = (double)aS[dd] + (double)aC[dd];
+      double* p = part + pk_idx(NP, r, c);
+      *p = first_flush ? v : *p + v;
+      aS[dd] = 0.f;
+      aC[dd] = 0.f;
+    }
+    first_flush = false;
+  };
+
+  const int64_t npanels = (m + PR - 1) / PR;
+  for (int64_t pnl = blockIdx.x; pnl < npanels; pnl += gridDim.x) {
+    const int64_t row0 = pnl * PR;
+    const int rows = (int)((m - row0) < (int64_t)PR ? (m - row0) : (int64_t)PR);
+    __syncthreads();
+    for (int idx = tid; idx < PR * NP; idx += kThreads) {
+      const int r = idx / NP, c = idx % NP;
+      float2 v = make_float2(0.f, 0.f);
+      if (r < rows && c < n) {
+        if (src_fp64)
+          v = df_split(src[(row0 + r) * lds + c]);
+        else
+          v = srcf[(row0 + r) * lds + c];
+      }
+      panel[r * LD + c] = v;
+    }
+
+    if (do_trsm) {
+      float2* row = panel + srow * LD;
+      for (int J = 0; J < nb; ++J) {
+        __syncthreads();  // panel loaded / previous block of R_k consumed
+        for (int idx = tid; idx < (8 * J + 8) * 8; idx += kThreads) {
+          const int i = idx >> 3, c = idx & 7;
+          const int col = 8 * J + c;
+          rb[idx] = df_split(col >= i ? rk[pk_idx(NP, i, col)] : 0.0);
+        }
+        __syncthreads();
+        float th[4], tl[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { const float2 v = row[8 * J + 4 * sh + c]; th[c] = v.x; tl[c] = v.y; }
+        for (int i = 0; i < 8 * J; ++i) {
+          const float2 q = row[i];
+          const float2* ri = rb + i * 8 + 4 * sh;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) df_sub(th[c], tl[c], q, ri[c]);
+        }
+        // diagonal block: lane sh = 0 solves columns 0..3 and hands them to sh = 1
+        float2 q4[4];
+        if (sh == 0) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float2 q = df_mul(make_float2(th[c], tl[c]), rinv[8 * J + c]);
+            q4[c] = q;
+#pragma unroll
+            for (int c2 = c + 1; c2 < 4; ++c2) df_sub(th[c2], tl[c2], q, rb[(8 * J + c) * 8 + c2]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          q4[c].x = __shfl_sync(0xffffffffu, q4[c].x, tid & ~1);
+          q4[c].y = __shfl_sync(0xffffffffu, q4[c].y, tid & ~1);
+        }
+        if (sh == 1) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2) df_sub(th[c2], tl[c2], q4[c], rb[(8 * J + c) * 8 + 4 + c2]);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float2 q = df_mul(make_float2(th[c], tl[c]), rinv[8 * J + 4 + c]);
+            th[c] = q.x;
+            tl[c] = q.y;
+#pragma unroll
+            for (int c2 = c + 1; c2 < 4; ++c2) df_sub(th[c2], tl[c2], q, rb[(8 * J + 4 + c) * 8 + 4 + c2]);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) { th[c] = q4[c].x; tl[c] = q4[c].y; }
+        }
+        if (srow < rows) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) row[8 * J + 4 * sh + c] = make_float2(th[c], tl[c]);
+        }
+      }
+      __syncthreads();
+      for (int idx = tid; idx < PR * NP; idx += kThreads) {
+        const int r = idx / NP, c = idx % NP;
+        if (r < rows && c < n) {
+          const float2 v = panel[r * LD + c];
+          if (dst_fp64)
+            dst[(row0 + r) * ldd + c] = df_join(v);
+          else
+            dstf[(row0 + r) * ldd + c] = v;
+        }
+      }
+    }
+    if (!do_gram) continue;
+    __syncthreads();
+    for (int idx = tid; idx < PR * (HALF - 1); idx += kThreads) {
+      const int r = idx / (HALF - 1), c = idx % (HALF - 1);
+      panel[r * LD + NP + c] = panel[r * LD + c];
+    }
+    __syncthreads();
+    const int rbeg = grp * g::RG;
+    const int rend = min(rbeg + g::RG, rows);
+    for (int r = rbeg; r < rend; ++r) {
+      const float2* rbase = panel + r * LD + j;
+      const float2 a = rbase[0];
+      const float2* p2 = rbase + d0;
+#pragma unroll
+      for (int dd = 0; dd < C - 2; ++dd) df_acc(aS[dd], aC[dd], a, p2[dd]);
+      if (dn > C - 2) df_acc(aS[C - 2], aC[C - 2], a, p2[C - 2]);
+      if (dn > C - 1) df_acc(aS[C - 1], aC[C - 1], a, p2[C - 1]);
+    }
+    if (++since_flush == g::FLUSH || pnl + gridDim.x >= npanels) {
+      since_flush = 0;
+      flush();
+    }
+  }
+  if (pass >= 0 && !do_gram) return;
+  if (first_flush) {
+#pragma unroll
+    for (int dd = 0; dd < C; ++dd) {
+      if (dd >= dn) continue;
+      const int d = d0 + dd;
+      int r = j, c = j + d;
+      if (c >= NP) { c -= NP; const int t = r; r = c; c = t; }
+      part[pk_idx(NP, r, c)] = 0.0;
+    }
+  }
+  if (tid < g::G) partials[((int64_t)blockIdx.x * g::G + tid) * part_stride + E] = 0.0;
+}
+
 template <int NP>
 static cudaError_t df_setup_one() {
   return cudaFuncSetAttribute(df_pass_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -411,8 +627,11 @@ cudaError_t df_setup() {
   cudaError_t e;
   if ((e = df2_setup_one<16>()) != cudaSuccess) return e;
   if ((e = df2_setup_one<32>()) != cudaSuccess) return e;
-  if ((e = df2_setup_one<64>()) != cudaSuccess) return e;
-  return df_setup_one<128>();
+  if ((e = cudaFuncSetAttribute(dfp_pass_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)DfpGeo<64>::smem)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(dfp_pass_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)DfpGeo<128>::smem);
 }
 
 // Resident CTAs per SM of the df pass kernel for a padded size.
@@ -420,8 +639,8 @@ cudaError_t df_occupancy(int np, int* per_sm) {
   switch (np) {
     case 16: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, df2_pass_kernel<16>, kThreads, Df2Geo<16>::smem);
     case 32: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, df2_pass_kernel<32>, kThreads, Df2Geo<32>::smem);
-    case 64: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, df2_pass_kernel<64>, kThreads, Df2Geo<64>::smem);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, df_pass_kernel<128>, kThreads, DfGeo<128>::smem);
+    case 64: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, dfp_pass_kernel<64>, kThreads, DfpGeo<64>::smem);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, dfp_pass_kernel<128>, kThreads, DfpGeo<128>::smem);
   }
 }
 
@@ -430,8 +649,8 @@ int df_groups(int np) {
   switch (np) {
     case 16: return Df2Geo<16>::G;
     case 32: return Df2Geo<32>::G;
-    case 64: return Df2Geo<64>::G;
-    default: return DfGeo<128>::G;
+    case 64: return DfpGeo<64>::G;
+    default: return DfpGeo<128>::G;
   }
 }
 
@@ -440,8 +659,8 @@ int df_rows_per_panel(int np) {
   switch (np) {
     case 16: return Df2Geo<16>::PR;
     case 32: return Df2Geo<32>::PR;
-    case 64: return Df2Geo<64>::PR;
-    default: return DfGeo<128>::PR;
+    case 64: return DfpGeo<64>::PR;
+    default: return DfpGeo<128>::PR;
   }
 }
 
@@ -456,11 +675,14 @@ void launch_df_pass(int np, int grid, cudaStream_t s, const double* src, int64_t
     break;
     SCQR3_DF2(16)
     SCQR3_DF2(32)
-    SCQR3_DF2(64)
 #undef SCQR3_DF2
-    case 128:
-      df_pass_kernel<128><<<grid, kThreads, DfGeo<128>::smem, s>>>(src, lds, dst, ldd, P, pass, rk,
+    case 64:
+      dfp_pass_kernel<64><<<grid, kThreads, DfpGeo<64>::smem, s>>>(src, lds, dst, ldd, P, pass, rk,
                                                                    partials, part_stride, st);
+      break;
+    case 128:
+      dfp_pass_kernel<128><<<grid, kThreads, DfpGeo<128>::smem, s>>>(src, lds, dst, ldd, P, pass, rk,
+                                                                     partials, part_stride, st);
       break;
     default: break;
   }
