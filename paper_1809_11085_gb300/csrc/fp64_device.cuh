@@ -145,7 +145,63 @@ __device__ __forceinline__ void pass_segment(const double* src, int64_t lds, dou
       // t_c -= q_i r_ic for every solved q_i (ascending i, one load of q_i
       // and eight broadcast loads of R_k per eight independent FMAs, no
       // store in the loop), then the 8 x 8 diagonal block by substitution.
-      if (tid < rows) {
+      if (NP == 128) {
+        // 128-row panels: two threads per row (adjacent lanes, four of the
+        // eight columns of each block each), so all eight warps solve
+        const int srow = tid >> 1, sh = tid & 1;
+        double* row = panel + srow * g::LD;
+        const int nb = (n + 7) / 8;
+        for (int J = 0; J < nb; ++J) {
+          double t[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) t[c] = row[8 * J + 4 * sh + c];
+          for (int i = 0; i < 8 * J; ++i) {
+            const double q = row[i];
+            const double* ri = rp + pk_row(NP, i) - i + 8 * J + 4 * sh;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) t[c] = fma(-q, ri[c], t[c]);
+          }
+          double q4[4];
+          if (sh == 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const double q = t[c] * rinv[8 * J + c];
+              q4[c] = q;
+              if (oblique && 8 * J + c < n) f2 = fma(q, q, f2);
+              const double* rc = rp + pk_row(NP, 8 * J + c) - (8 * J + c) + 8 * J;
+#pragma unroll
+              for (int c2 = c + 1; c2 < 4; ++c2) t[c2] = fma(-q, rc[c2], t[c2]);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) q4[c] = __shfl_sync(0xffffffffu, q4[c], tid & ~1);
+          if (sh == 1) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const double* rc = rp + pk_row(NP, 8 * J + c) - (8 * J + c) + 8 * J + 4;
+#pragma unroll
+              for (int c2 = 0; c2 < 4; ++c2) t[c2] = fma(-q4[c], rc[c2], t[c2]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const double q = t[c] * rinv[8 * J + 4 + c];
+              t[c] = q;
+              if (oblique && 8 * J + 4 + c < n) f2 = fma(q, q, f2);
+              const double* rc = rp + pk_row(NP, 8 * J + 4 + c) - (8 * J + 4 + c) + 8 * J + 4;
+#pragma unroll
+              for (int c2 = c + 1; c2 < 4; ++c2) t[c2] = fma(-q, rc[c2], t[c2]);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) t[c] = q4[c];
+          }
+          if (srow < rows) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) row[8 * J + 4 * sh + c] = t[c];
+          }
+          __syncwarp();  // the partner lane reads these solved values in the next block
+        }
+      } else if (tid < rows) {
         double* row = panel + tid * g::LD;
         const int nb = (n + 7) / 8;
         for (int J = 0; J < nb; ++J) {
