@@ -70,6 +70,9 @@ def lib():
         L.orc_scqr3.argtypes = [i64, i32, p, i64, i32, p, f64, f64, i32, p, i64, p,
                                 ctypes.POINTER(_Trace)]
         L.orc_scqr3.restype = i32
+        L.orc_scqr3_ex.argtypes = [i64, i32, p, i64, i32, p, f64, f64, i32, f64, i32, f64, p, i64,
+                                   p, ctypes.POINTER(_Trace)]
+        L.orc_scqr3_ex.restype = i32
         _lib = L
     return _lib
 
@@ -148,11 +151,16 @@ def normb_bound(Bblk: np.ndarray) -> float:
 
 
 def scqr3(X: np.ndarray, Bblk: np.ndarray | None = None, normx2: float = 0.0,
-          normb: float = 0.0, max_passes: int = 6):
+          normb: float = 0.0, max_passes: int = 6, shift_scale: float = 0.0, algorithm: int = 3,
+          tol: float = 0.0):
     """Shifted CholeskyQR3 (Alg. 3 / Alg. 5 with the breakdown rule of Alg. 2).
 
-    Returns (Q, R, status, trace) where trace is a dict with the per-pass
-    record (passes, shifted, unshifted_fail, s, norm2).
+    shift_scale = c > 0 first tries the smaller shift c u ||X||^2 of the
+    Sec. 6.1 remark (c = 1 is the remark's u ||X||^2), falling back to the safe
+    shift of Eq. (finds2) on breakdown; algorithm 2 runs Alg. 2 with its
+    orthogonality stopping test (tol <= 0: 6{mn + n(n+1)} u, the bound of
+    Thm. maincholqr3). Returns (Q, R, status, trace) where trace is a dict with
+    the per-pass record (passes, shifted, unshifted_fail, s, norm2).
     """
     X = _c(X)
     m, n = X.shape
@@ -164,8 +172,8 @@ def scqr3(X: np.ndarray, Bblk: np.ndarray | None = None, normx2: float = 0.0,
     else:
         Bblk = _c(Bblk)
         bs, bp = Bblk.shape[1], _ptr(Bblk)
-    st = lib().orc_scqr3(m, n, _ptr(X), n, bs, bp, normx2, normb, max_passes,
-                         _ptr(Q), n, _ptr(R), ctypes.byref(tr))
+    st = lib().orc_scqr3_ex(m, n, _ptr(X), n, bs, bp, normx2, normb, max_passes, shift_scale,
+                            algorithm, tol, _ptr(Q), n, _ptr(R), ctypes.byref(tr))
     k = tr.passes
     trace = {"passes": k,
              "shifted": list(tr.shifted[:k]),

@@ -142,9 +142,23 @@ double orc_normb_bound(int64_t m, int bs, const double *Bblk) {
 int orc_scqr3(int64_t m, int n, const double *X, int64_t ldx, int bs,
               const double *Bblk, double normx2, double normb, int max_passes,
               double *Q, int64_t ldq, double *R, orc_trace *trace) {
+  return orc_scqr3_ex(m, n, X, ldx, bs, Bblk, normx2, normb, max_passes, 0.0, 3, 0.0,
+                      Q, ldq, R, trace);
+}
+
+int orc_scqr3_ex(int64_t m, int n, const double *X, int64_t ldx, int bs,
+                 const double *Bblk, double normx2, double normb, int max_passes,
+                 double shift_scale, int algorithm, double tol, double *Q,
+                 int64_t ldq, double *R, orc_trace *trace) {
   if (m < n || n < 1 || ldx < n || ldq < n || max_passes < 3 ||
-      max_passes > ORC_MAX_PASSES || (bs > 0 && (m % bs) != 0))
+      max_passes > ORC_MAX_PASSES || (bs > 0 && (m % bs) != 0) ||
+      (algorithm != 2 && algorithm != 3))
     return ORC_E_ARG;
+  /* Alg. 2's printed tolerance sqrt(n) u lies below the rounding error of a
+   * computed Gram matrix of orthonormal columns, so tol <= 0 selects the
+   * orthogonality bound that Thm. (maincholqr3) proves for the final Q,
+   * 6 {mn + n(n+1)} u. */
+  if (!(tol > 0.0)) tol = 6.0 * ((double)m * (double)n + (double)n * (double)(n + 1)) * ORC_U;
   const int oblique = bs > 0;
   if (oblique && !(normb > 0.0)) normb = orc_normb_bound(m, bs, Bblk);
 
@@ -177,11 +191,27 @@ int orc_scqr3(int64_t m, int n, const double *X, int64_t ldx, int bs,
       break;
     }
     if (p == 0 && normx2 > 0.0) nrm2 = normx2;
+
+    /* Alg. 2 line 10: stop when the current iterate is orthonormal enough
+     * (its Gram matrix A is already at hand). */
+    if (algorithm == 2 && p > 0) {
+      double d2 = 0.0;
+      for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) {
+          const double e = A[j * n + k] - (j == k ? 1.0 : 0.0);
+          d2 = d2 + e * e;
+        }
+      if (sqrt(d2) <= tol) {
+        status = ORC_OK;
+        break;
+      }
+    }
     tr.norm2[p] = nrm2;
 
-    /* Pass 1 always shifts (Alg. 3 lines 3-4). Later passes try the plain
-     * Cholesky and shift only if it breaks down (Alg. 2 lines 4-8). */
-    int shifted = (p == 0);
+    /* Alg. 3: pass 1 always shifts (lines 3-4). Alg. 2 and the later passes of
+     * Alg. 3 try the plain Cholesky and shift only if it breaks down (Alg. 2
+     * lines 4-8). */
+    int shifted = (algorithm == 3 && p == 0);
     if (!shifted) {
       const int fail = orc_chol(n, A, 0.0, Rt);
       tr.unshifted_fail[p] = fail;
@@ -189,8 +219,17 @@ int orc_scqr3(int64_t m, int n, const double *X, int64_t ldx, int bs,
     }
     double s = 0.0;
     if (shifted) {
-      s = oblique ? orc_shift_oblique(m, n, nrm2, normb) : orc_shift(m, n, nrm2);
-      const int fail = orc_chol(n, A, s, Rt);
+      const double safe = oblique ? orc_shift_oblique(m, n, nrm2, normb) : orc_shift(m, n, nrm2);
+      int fail = 1;
+      if (shift_scale > 0.0) {
+        /* the smaller shift c u ||X||^2 (x ||B||) of the remark in Sec. 6.1 */
+        s = oblique ? shift_scale * ORC_U * nrm2 * normb : shift_scale * ORC_U * nrm2;
+        fail = orc_chol(n, A, s, Rt);
+      }
+      if (fail) {
+        s = safe;
+        fail = orc_chol(n, A, s, Rt);
+      }
       if (fail) {
         tr.passes = p + 1;
         tr.shifted[p] = 1;
@@ -207,10 +246,10 @@ int orc_scqr3(int64_t m, int n, const double *X, int64_t ldx, int bs,
     orc_trsm(m, n, Q, ldq, Rt, Q, ldq);
     orc_trmm(n, Rt, R);
 
-    /* Two plain CholeskyQR passes after the last shifted one complete
-     * CholeskyQR2 (Alg. 3 lines 6-7). */
+    /* Alg. 3: two plain CholeskyQR passes after the last shifted one complete
+     * CholeskyQR2 (lines 6-7). */
     plain_in_a_row = shifted ? 0 : plain_in_a_row + 1;
-    if (plain_in_a_row == 2) {
+    if (algorithm == 3 && plain_in_a_row == 2) {
       status = ORC_OK;
       break;
     }

@@ -86,6 +86,26 @@ int orc_scqr3(int64_t m, int n, const double *X, int64_t ldx, int bs,
               const double *Bblk, double normx2, double normb, int max_passes,
               double *Q, int64_t ldq, double *R, orc_trace *trace);
 
+/* Options of the generalized driver below.
+ *  shift_scale <= 0: the shift of Eq. (finds2)/(finds2B) (safe);
+ *             c > 0: first the smaller shift c u ||X||^2 (c u ||X||^2 ||B|| in
+ *                the oblique case) -- the remark of Sec. 6.1 and the conclusion
+ *                suggest s = O(u ||X||^2), c = 1 being the remark's choice --
+ *                then the safe shift if that Cholesky breaks down.
+ *  algorithm  3: Alg. 3 -- pass 1 always shifted, end after two consecutive
+ *                unshifted passes;
+ *             2: Alg. 2 -- every pass first tries the plain Cholesky and
+ *                shifts only on breakdown; the iteration ends as soon as
+ *                ||Q^T Q - I||_F <= tol (||Q^T B Q - I||_F for oblique B),
+ *                tested on the Gram matrix of the current iterate; tol <= 0
+ *                selects 6 {mn + n(n+1)} u, the bound of Thm. (maincholqr3)
+ *                (the printed sqrt(n) u is below the rounding error of the
+ *                computed Gram matrix and is reached only by chance). */
+int orc_scqr3_ex(int64_t m, int n, const double *X, int64_t ldx, int bs,
+                 const double *Bblk, double normx2, double normb, int max_passes,
+                 double shift_scale, int algorithm, double tol, double *Q,
+                 int64_t ldq, double *R, orc_trace *trace);
+
 #ifdef __cplusplus
 }
 #endif

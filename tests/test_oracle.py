@@ -377,3 +377,113 @@ def test_geometric_sigma():
     s = geometric_sigma(5, 1e4)
     assert s[0] == 1.0 and s[-1] == pytest.approx(1e-4)
     assert np.allclose(s[1:] / s[:-1], 10 ** -1.0)
+
+
+# --------------------------------------------------------------------------- options: the smaller shift of the
+# remark in Sec. 6.1 and the adaptive Alg. 2
+
+def _fig3_input(seed):
+    """The setup of the Sec. 6.1 remark (its Fig. 3): m=1000, n=50, kappa 1e15, ||X||_2=1."""
+    Uf, sig, V = testmat_factors(1000, 50, 1e15, seed=seed)
+    return (Uf * sig) @ V.T, sig
+
+
+def test_small_shift_reduces_passes_fig3_setup():
+    """With the safe shift 11{mn+n(n+1)}u the remark notes that kappa(Q^(1)) is
+    too large for CholeskyQR2 and more passes follow (here one more shifted
+    pass). With s = c u ||X||^2 (c = 100) the first Cholesky succeeds, s is
+    exactly c u, kappa(Q^(1)) follows sigma_i / sqrt(sigma_i^2 + s) from the SVD
+    of X, and CholeskyQR2 finishes: three passes in all."""
+    X, sig = _fig3_input(3)
+    m, n = X.shape
+    _, _, st, tr = oracle.scqr3(X, normx2=1.0)
+    assert st == 0 and tr["passes"] == 4 and tr["shifted"] == [1, 1, 0, 0]
+    Q, R, st, tr = oracle.scqr3(X, normx2=1.0, shift_scale=100.0)
+    assert st == 0 and tr["passes"] == 3 and tr["shifted"] == [1, 0, 0]
+    assert tr["s"][0] == 100.0 * U
+    R1, fail = oracle.chol(oracle.gram(X), tr["s"][0])
+    assert fail == 0
+    sv = sig / np.sqrt(sig ** 2 + tr["s"][0])
+    assert abs(np.linalg.cond(oracle.trsm(X, R1)) / (sv.max() / sv.min()) - 1.0) < 0.05
+    assert orth2(Q) < 1e-14 and resid(X, Q, R) < 1e-15
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5])
+def test_small_shift_falls_back_when_shifted_gram_is_indefinite(seed):
+    """The remark gives no guarantee for chol(A + u||X||^2 I). On the Fig. 3
+    setup the computed Gram matrix has an eigenvalue near -2u (its rounding
+    error), so A + uI is indefinite (numpy's eigvalsh, independent of the
+    oracle), the Cholesky must break down, and the safe shift of Eq. (finds2)
+    is used instead, exactly."""
+    X, _ = _fig3_input(seed)
+    m, n = X.shape
+    A = oracle.gram(X)
+    assert np.linalg.eigvalsh(A + U * np.eye(n)).min() < 0.0
+    _, _, st, tr = oracle.scqr3(X, normx2=1.0, shift_scale=1.0)
+    assert st == 0
+    assert tr["s"][0] == oracle.shift(m, n, 1.0)
+
+
+def test_small_shift_oblique_scales_with_normb():
+    """The oblique form of the smaller shift is c u ||X||^2 ||B||."""
+    m, n, bs = 512, 16, 8
+    Bblk = block_diag_spd(m, bs, seed=57)
+    X = testmat(m, n, 1e6, seed=58)
+    _, _, st, tr = oracle.scqr3(X, Bblk, normx2=2.0, normb=3.0, shift_scale=1e4)
+    assert st == 0 and tr["s"][0] == 1e4 * U * 2.0 * 3.0
+
+
+@pytest.mark.parametrize("key", ["table1", "table2"])
+def test_alg2_reproduces_table_iterates(golden, key):
+    """Tables 1-2 list three iterates of Alg. 2: the plain Cholesky of X^T X
+    breaks down (kappa^2 >> 1/u), the shifted pass follows, then two plain
+    passes, after which ||Q^T Q - I||_F is at rounding level and the loop ends.
+    The computation is then pass for pass the one of Alg. 3, bit for bit."""
+    g = golden[key]
+    X = testmat(g["m"], g["n"], g["kappa"], seed=12)
+    Q2, R2, st2, tr2 = oracle.scqr3(X, normx2=1.0, algorithm=2)
+    assert st2 == 0 and tr2["passes"] == 3 and tr2["shifted"] == [1, 0, 0]
+    assert tr2["unshifted_fail"][0] > 0
+    Q3, R3, st3, tr3 = oracle.scqr3(X, normx2=1.0)
+    assert np.array_equal(Q2, Q3) and np.array_equal(R2, R3) and tr2["s"] == tr3["s"]
+
+
+@pytest.mark.parametrize("kappa,passes", [(1.0, 1), (1e3, 2), (1e7, 2)])
+def test_alg2_stops_when_orthogonal_enough(kappa, passes):
+    """Alg. 2 needs no shift for kappa(X) < u^{-1/2}: one plain CholeskyQR when
+    X is already orthonormal, two (CholeskyQR2) otherwise. The stopping test
+    is replayed with the building blocks: the iterate it stops at is the first
+    whose ||Q^T Q - I||_F is below 6{mn+n(n+1)}u, and the one before is not."""
+    m, n = 2000, 20
+    X = testmat(m, n, kappa, seed=1)
+    Q, R, st, tr = oracle.scqr3(X, algorithm=2)
+    assert st == 0 and tr["passes"] == passes and tr["shifted"] == [0] * passes
+    tol = 6 * (m * n + n * (n + 1)) * U
+    Qk = X.copy()
+    devs = []
+    for p in range(passes):
+        Rt, fail = oracle.chol(oracle.gram(Qk), 0.0)
+        assert fail == 0
+        Qk = oracle.trsm(Qk, Rt)
+        devs.append(np.linalg.norm(oracle.gram(Qk) - np.eye(n)))
+    assert np.array_equal(Qk, Q)
+    assert devs[-1] <= tol and all(d > tol for d in devs[:-1])
+    assert resid(X, Q, R) < 1e-15
+
+
+def test_alg2_printed_tolerance_is_below_gram_rounding():
+    """With the printed tolerance sqrt(n) u the test is compared with the
+    computed Gram matrix, whose own rounding error (about sqrt(m) u per entry)
+    is larger, so the iteration runs to the pass limit."""
+    m, n = 1000, 30
+    X = testmat(m, n, 1e12, seed=12)
+    Q, _, st, tr = oracle.scqr3(X, normx2=1.0, algorithm=2, tol=np.sqrt(n) * U, max_passes=5)
+    assert st == oracle.E_MAXPASS and tr["passes"] == 5
+    assert np.linalg.norm(oracle.gram(Q) - np.eye(n)) > np.sqrt(n) * U
+    assert orth2(Q) < 1e-14
+
+
+def test_option_arguments_checked():
+    X = testmat(100, 4, 10.0, seed=9)
+    assert oracle.scqr3(X, algorithm=1)[2] == oracle.E_ARG
+    assert oracle.scqr3(X, algorithm=4)[2] == oracle.E_ARG
