@@ -40,7 +40,7 @@ extern "C" {
 
 /* Status codes (return values and scqr3_info.status).
  *   > 0  : the SHIFTED Cholesky broke down at this 1-based column, i.e.
- *          chol(A + sI) of Alg. 1 line 3 failed (X numerically rank
+ *          chol(A + sI) of Alg. 1 failed (X numerically rank
  *          deficient beyond what the shift of Eq. (finds2) covers).
  *   -1..-20 : argument k (1-based, in the order of the prototype) invalid. */
 #define SCQR3_OK 0
@@ -82,7 +82,32 @@ typedef struct {
   double norm_x2;  /* > 0: value of ||X||_2^2 used in the pass-1 shift of
                       Eq. (finds2)/(finds2B); otherwise ||X||_F^2 (Sec. 4.1
                       allows this more conservative substitute)             */
+  double shift_scale; /* > 0: a shifted pass first tries the smaller shift
+                      s = shift_scale * u * ||Q||^2 (times ||B|| for oblique
+                      B) that the remark of Sec. 6.1 and Sec. 8 suggest
+                      (shift_scale = 1 is the remark's u ||X||^2), and uses
+                      Eq. (finds2)/(finds2B) only if that Cholesky breaks
+                      down; <= 0: Eq. (finds2)/(finds2B) only. A smaller
+                      shift leaves kappa(Q_1) smaller and can save a pass
+                      for kappa(X) near 1/u, with no guarantee (Sec. 6.1)    */
+  int algorithm;   /* SCQR3_ALG_SCQR3 (or 0): Alg. 3; SCQR3_ALG_ADAPTIVE:
+                      Alg. 2                                               */
+  double tol;      /* Alg. 2 only: stop once ||Q^T Q - I||_F <= tol
+                      (||Q^T B Q - I||_F for oblique B), tested on the Gram
+                      matrix of the current iterate; <= 0 selects
+                      6 {mn + n(n+1)} u, the orthogonality bound of
+                      Thm. (maincholqr3) (the printed sqrt(n) u is below the
+                      rounding error of a computed Gram matrix)             */
 } scqr3_opts;
+
+/* scqr3_opts.algorithm. Alg. 3 shifts pass 1 unconditionally and ends after
+ * two consecutive unshifted passes. Alg. 2 tries the plain Cholesky in every
+ * pass (shifting only on breakdown) and ends on its orthogonality test, so a
+ * well-conditioned X takes one or two passes; its test needs the Gram matrix
+ * of every iterate, including the last. Both end with SCQR3_E_MAXPASS when
+ * max_passes passes did not finish. */
+#define SCQR3_ALG_ADAPTIVE 2
+#define SCQR3_ALG_SCQR3 3
 
 /* Per-call record, written on the device. */
 typedef struct {
@@ -113,13 +138,17 @@ int scqr3_workspace_bytes(int64_t m, int n, const scqr3_B *B,
  *         as the adjoint scqr3_backward needs them.
  *  info   device scqr3_info filled by the call (required).
  *
- * Pass 1 always adds the shift s of Eq. (finds2) (Eq. finds2B if B != NULL)
- * before its Cholesky factorization (Alg. 3 lines 3-4). A later pass whose
- * plain Cholesky breaks down is redone with the shift recomputed from that
- * pass's ||Q||^2 (Alg. 2 lines 5-7). The call ends after two consecutive
- * plain passes (CholeskyQR2, Alg. 3 lines 6-7) or at max_passes
- * (SCQR3_E_MAXPASS). Each pass's solve Q := Q R_k^{-1} is done row by row
- * by substitution, as the row-wise analysis (Eq. backward2) assumes. */
+ * By default (opts->algorithm = SCQR3_ALG_SCQR3) pass 1 always adds the
+ * shift s of Eq. (finds2) (Eq. finds2B if B != NULL) before its Cholesky
+ * factorization (Alg. 3). A later pass whose plain Cholesky breaks down is
+ * redone with the shift recomputed from that pass's ||Q||^2 (the breakdown
+ * rule of Alg. 2). The call ends after two consecutive plain passes
+ * (CholeskyQR2, the last two steps of Alg. 3) or at max_passes
+ * (SCQR3_E_MAXPASS). SCQR3_ALG_ADAPTIVE runs Alg. 2 instead (see
+ * scqr3_opts). Each pass's solve Q := Q R_k^{-1} is done row by row by
+ * substitution, as the row-wise analysis (Eq. backward2) assumes. When a
+ * pass fails (status > 0 or a negative code found on the device), Q holds
+ * the last completed iterate in FP64, or is untouched if pass 1 failed. */
 int scqr3_factor(const double *X, int64_t m, int n, int64_t ldx,
                  const scqr3_B *B, double *Q, int64_t ldq, double *R,
                  double *Rpass, void *workspace, size_t workspace_bytes,
@@ -237,6 +266,8 @@ int scqr3_factor_noalloc(const double *X, int64_t m, int n, int64_t ldx,
 #define SCQR3_KERNEL_CHOL 3     /* shift, Cholesky, R := R_k R, bookkeeping */
 #define SCQR3_KERNEL_BFACTOR 4  /* per-block Cholesky of the oblique B      */
 #define SCQR3_KERNEL_TRSM 5     /* Q := Q R_k^{-1} alone (n > 128)          */
+#define SCQR3_KERNEL_FINISH 6   /* mixed form: float-pair Q to FP64, if the
+                                   last solve left it in pairs             */
 
 typedef struct {
   int kernel;  /* SCQR3_KERNEL_*                                          */

@@ -168,7 +168,7 @@ int orc_scqr3_ex(int64_t m, int n, const double *X, int64_t ldx, int bs,
   memset(&tr, 0, sizeof(tr));
   int status = ORC_E_MAXPASS;
 
-  /* Alg. 2 line 1 / Alg. 3 line 1: Q := X, R := I. */
+  /* Alg. 2 and Alg. 3 start from Q := X, R := I. */
   if (Q != X)
     for (int64_t i = 0; i < m; ++i)
       memcpy(Q + i * ldq, X + i * ldx, sizeof(double) * (size_t)n);
@@ -192,7 +192,7 @@ int orc_scqr3_ex(int64_t m, int n, const double *X, int64_t ldx, int bs,
     }
     if (p == 0 && normx2 > 0.0) nrm2 = normx2;
 
-    /* Alg. 2 line 10: stop when the current iterate is orthonormal enough
+    /* Alg. 2's loop test: stop when the current iterate is orthonormal enough
      * (its Gram matrix A is already at hand). */
     if (algorithm == 2 && p > 0) {
       double d2 = 0.0;
@@ -208,9 +208,9 @@ int orc_scqr3_ex(int64_t m, int n, const double *X, int64_t ldx, int bs,
     }
     tr.norm2[p] = nrm2;
 
-    /* Alg. 3: pass 1 always shifts (lines 3-4). Alg. 2 and the later passes of
+    /* Alg. 3: pass 1 always shifts. Alg. 2 and the later passes of
      * Alg. 3 try the plain Cholesky and shift only if it breaks down (Alg. 2
-     * lines 4-8). */
+     * breakdown rule). */
     int shifted = (algorithm == 3 && p == 0);
     if (!shifted) {
       const int fail = orc_chol(n, A, 0.0, Rt);
@@ -242,12 +242,12 @@ int orc_scqr3_ex(int64_t m, int n, const double *X, int64_t ldx, int bs,
     tr.s[p] = s;
     tr.passes = p + 1;
 
-    /* Q := Q Rt^{-1}, R := Rt R (Alg. 2 line 9). */
+    /* Q := Q Rt^{-1}, R := Rt R (the update of Alg. 2). */
     orc_trsm(m, n, Q, ldq, Rt, Q, ldq);
     orc_trmm(n, Rt, R);
 
     /* Alg. 3: two plain CholeskyQR passes after the last shifted one complete
-     * CholeskyQR2 (lines 6-7). */
+     * CholeskyQR2 (the last two steps of Alg. 3). */
     plain_in_a_row = shifted ? 0 : plain_in_a_row + 1;
     if (algorithm == 3 && plain_in_a_row == 2) {
       status = ORC_OK;

@@ -39,12 +39,12 @@ typedef struct {
   double norm2[ORC_MAX_PASSES];       /* ||Q_{k-1}||^2 estimate used       */
 } orc_trace;
 
-/* Gram matrix A = X^T X (Eq. gram; Alg. 1 line 1). A is n x n full
+/* Gram matrix A = X^T X (Eq. gram; the first step of Alg. 1). A is n x n full
  * symmetric; the upper triangle is computed, the lower mirrored. Each entry
  * is the sum over rows i = 0..m-1 in ascending order. */
 void orc_gram(int64_t m, int n, const double *X, int64_t ldx, double *A);
 
-/* Oblique Gram A = X^T (B X) (Alg. 4 line 1) for block-diagonal B made of
+/* Oblique Gram A = X^T (B X) (the first step of Alg. 4) for block-diagonal B made of
  * m/bs dense bs x bs blocks (row-major, block j at Bblk + j*bs*bs). Y = B X
  * is formed block by block, then the upper triangle of X^T Y, ascending
  * rows, mirrored. Also returns sum_ij x_ij^2 in *fro2 (may be NULL). */
@@ -58,8 +58,8 @@ double orc_shift(int64_t m, int n, double normx2);
  * Eq. (finds2B). */
 double orc_shift_oblique(int64_t m, int n, double normx2, double normb);
 
-/* Cholesky factor R (upper, R^T R = A + sI), column by column (Alg. 1
- * line 3). Returns 0, or the 1-based column j at which the radicand
+/* Cholesky factor R (upper, R^T R = A + sI), column by column (the shifted
+ * Cholesky of Alg. 1). Returns 0, or the 1-based column j at which the radicand
  * a_jj + s - sum_{k<j} r_kj^2 is not a positive finite number. */
 int orc_chol(int n, const double *A, double s, double *R);
 
@@ -68,7 +68,7 @@ int orc_chol(int n, const double *A, double s, double *R);
 void orc_trsm(int64_t m, int n, const double *X, int64_t ldx, const double *R,
               double *Q, int64_t ldq);
 
-/* R := Rt R for upper triangular Rt, R (Alg. 2 line 9). */
+/* R := Rt R for upper triangular Rt, R (the R update of Alg. 2). */
 void orc_trmm(int n, const double *Rt, double *R);
 
 /* Upper bound of ||B||_2 for block-diagonal B: max over blocks of the

@@ -293,6 +293,7 @@ extern "C" int scqr3_batch_plan_upload(scqr3_batch_plan* p, void* workspace, siz
     b.P.bs = 0;
     b.P.norm_x2 = 0.0;
     b.P.normb_in = 0.0;
+    set_options(&b.P, nullptr);
     b.ldx = a.ldx;
     b.ldq = a.ldq;
     b.tile_lo = b.tile_hi = -1;

@@ -623,6 +623,34 @@ static cudaError_t df2_setup_one() {
                               (int)Df2Geo<NP>::smem);
 }
 
+// After the last solve that ran: if it left Q as float pairs (a Gram step was
+// still planned after it -- Alg. 2's stopping test, or a later pass that broke
+// down), convert Q to FP64 in place, element by element.
+__global__ void __launch_bounds__(kThreads)
+df_finish_kernel(double* Q, int64_t ldq, int64_t m, int n, int max_passes, const DevState* st) {
+  int last = -1;
+  for (int k = max_passes - 1; k >= 0; --k)
+    if (st->run_trsm[k]) {
+      last = k;
+      break;
+    }
+  if (last < 0 || !st->gram_after[last]) return;
+  const int64_t total = m * (int64_t)n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / n;
+    const int c = (int)(idx - r * n);
+    double* e = Q + r * ldq + c;
+    const float2 v = *reinterpret_cast<const float2*>(e);
+    *e = df_join(v);
+  }
+}
+
+void launch_df_finish(int grid, cudaStream_t s, double* Q, int64_t ldq, int64_t m, int n,
+                      int max_passes, const DevState* st) {
+  df_finish_kernel<<<grid, kThreads, 0, s>>>(Q, ldq, m, n, max_passes, st);
+}
+
 cudaError_t df_setup() {
   cudaError_t e;
   if ((e = df2_setup_one<16>()) != cudaSuccess) return e;

@@ -45,7 +45,7 @@ PassGeom pass_geom() {
 }
 
 // In-place Z = L^T Q for each bs-row block of the panel (B = L L^T), so that
-// Z^T Z = Q^T B Q is the oblique Gram matrix of Alg. 4 line 1.
+// Z^T Z = Q^T B Q is the oblique Gram matrix of Alg. 4.
 template <int NP, int BS>
 __device__ __forceinline__ void apply_lt(double* panel, int rows, int n, int64_t blk0,
                                          int64_t nblk_total, const double* __restrict__ lt) {
@@ -84,7 +84,7 @@ __device__ __forceinline__ void apply_lt_bs(double* panel, int rows, int n, int 
 }
 
 // One CTA's share of a pass over one matrix: panels p_begin, p_begin + p_step,
-// ... < p_end. pass < 0: Gram of X only (pass 1's Alg. 3 line 2). pass >= 0:
+// ... < p_end. pass < 0: Gram of X only (the first Gram of Alg. 3). pass >= 0:
 // solve with R_pass (packed) and, when the state asks for it, the next Gram
 // matrix, whose partial sums go to part + group * part_stride (group 0's slot
 // also receives the sum of squares used by the oblique shift).
@@ -304,6 +304,34 @@ __device__ __forceinline__ double shift_value(const Params& P, double nrm2, doub
   return s;
 }
 
+// The smaller shift c u ||Q||^2 (times ||B||) of the remark in Sec. 6.1.
+__device__ __forceinline__ double small_shift_value(const Params& P, double nrm2, double normb) {
+  const double u = 1.1102230246251565e-16;
+  double s = __dmul_rn(__dmul_rn(P.shift_scale, u), nrm2);
+  if (P.bs > 0) s = __dmul_rn(s, normb);
+  return s;
+}
+
+// ||A - I||_F^2 of the packed symmetric A (off-diagonal entries count twice),
+// summed over the whole block; the result is valid in every thread.
+template <int NP>
+__device__ double dev_from_identity2(const double* S, int n, double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double d = 0.0;
+  for (int j = warp; j < n; j += nw)
+    for (int k = j + lane; k < n; k += 32) {
+      const double v = S[pk_idx(NP, j, k)] - (k == j ? 1.0 : 0.0);
+      d = fma(k == j ? v : 2.0 * v, v, d);
+    }
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = d;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  return t;
+}
+
 // Cholesky of the packed matrix S in place (upper factor), columns < n.
 // Returns 0 or the 1-based breakdown column (radicand not positive/finite).
 template <int NP>
@@ -346,6 +374,7 @@ __device__ __forceinline__ void chol_body(const Params& P, int pass, const doubl
   __shared__ int fail_sh;
   __shared__ double s_sh, nrm_sh;
   __shared__ int shifted_sh, ufail_sh;
+  __shared__ double red_sh[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int n = P.n;
 
@@ -370,7 +399,8 @@ __device__ __forceinline__ void chol_body(const Params& P, int pass, const doubl
     if (pass == 0 && P.bs > 0)
       st->normb = P.normb_in > 0.0 ? P.normb_in : st->normb_bits_max;
     nrm_sh = nrm2;
-    shifted_sh = (pass == 0);
+    // Alg. 3 shifts pass 1 unconditionally; Alg. 2 tries the plain Cholesky first
+    shifted_sh = (pass == 0 && P.algorithm != 2);
     ufail_sh = 0;
   }
   __syncthreads();
@@ -381,8 +411,20 @@ __device__ __forceinline__ void chol_body(const Params& P, int pass, const doubl
     }
     return;
   }
+  if (P.algorithm == 2 && pass > 0) {
+    // Alg. 2's stopping test, on the Gram matrix of the current iterate
+    const double d2 = dev_from_identity2<NP>(S, n, red_sh);
+    if (sqrt(d2) <= P.tol) {
+      if (tid == 0) {
+        st->status = SCQR3_OK;
+        info->status = SCQR3_OK;
+        info->passes = pass;
+      }
+      return;
+    }
+  }
 
-  if (!shifted_sh) {  // Alg. 2 line 4: plain Cholesky first
+  if (!shifted_sh) {  // Alg. 2: plain Cholesky first
     const int f = chol_packed<NP>(S, n, &fail_sh);
     if (f) {
       if (tid == 0) {
@@ -395,13 +437,29 @@ __device__ __forceinline__ void chol_body(const Params& P, int pass, const doubl
     }
   }
   if (tid == 0) s_sh = 0.0;
-  if (shifted_sh) {  // Alg. 1 line 3 / Alg. 2 lines 6-7
-    if (tid == 0) {
-      s_sh = shift_value(P, nrm_sh, st->normb);
-      for (int j = 0; j < n; ++j) S[pk_idx(NP, j, j)] = S[pk_idx(NP, j, j)] + s_sh;
+  if (shifted_sh) {  // Alg. 1 / Alg. 2: shifted Cholesky
+    int f = 1;
+    if (P.shift_scale > 0.0) {  // the smaller shift first (remark of Sec. 6.1)
+      if (tid == 0) {
+        s_sh = small_shift_value(P, nrm_sh, st->normb);
+        for (int j = 0; j < n; ++j) S[pk_idx(NP, j, j)] = S[pk_idx(NP, j, j)] + s_sh;
+      }
+      __syncthreads();
+      f = chol_packed<NP>(S, n, &fail_sh);
+      if (f) {
+        __syncthreads();
+        for (int e = tid; e < E; e += nt) S[e] = gram[e];
+        __syncthreads();
+      }
     }
-    __syncthreads();
-    const int f = chol_packed<NP>(S, n, &fail_sh);
+    if (f) {
+      if (tid == 0) {
+        s_sh = shift_value(P, nrm_sh, st->normb);
+        for (int j = 0; j < n; ++j) S[pk_idx(NP, j, j)] = S[pk_idx(NP, j, j)] + s_sh;
+      }
+      __syncthreads();
+      f = chol_packed<NP>(S, n, &fail_sh);
+    }
     if (f) {
       if (tid == 0) {
         st->status = f;
@@ -436,7 +494,7 @@ __device__ __forceinline__ void chol_body(const Params& P, int pass, const doubl
     }
   }
 
-  // R := R_k R (Alg. 2 line 9); row i of the product needs rows >= i of the
+  // R := R_k R (the update of Alg. 2); row i of the product needs rows >= i of the
   // old R, so rows are formed in ascending order, in place.
   if (pass == 0) {
     for (int e = tid; e < E; e += nt) Ra[e] = S[e];
@@ -465,9 +523,12 @@ __device__ __forceinline__ void chol_body(const Params& P, int pass, const doubl
     st->plain_in_a_row = plain;
     st->passes = pass + 1;
     st->run_trsm[pass] = 1;
-    const bool more = plain < 2 && pass + 1 < P.max_passes;
+    // Alg. 3 ends after two consecutive plain passes; Alg. 2 needs the Gram
+    // of every iterate for its stopping test
+    const bool done = P.algorithm != 2 && plain >= 2;
+    const bool more = !done && pass + 1 < P.max_passes;
     st->gram_after[pass] = more ? 1 : 0;
-    if (plain < 2 && !more) st->status = SCQR3_E_MAXPASS;
+    if (!done && !more) st->status = SCQR3_E_MAXPASS;
     info->status = st->status;
     info->passes = pass + 1;
     info->shifted[pass] = shifted_sh;

@@ -8,7 +8,7 @@
 // memory traffic are nearly free next to that.
 //
 //   pass_kernel   one streaming pass over the rows: the substitution
-//                 Q_k = Q_{k-1} R_k^{-1} of pass k (Alg. 3 lines 5-7) and,
+//                 Q_k = Q_{k-1} R_k^{-1} of pass k (Alg. 3) and,
 //                 fused with it, the Gram matrix Q_k^T Q_k of pass k+1
 //                 (or Q_k^T B Q_k, Alg. 5), as per-CTA partial sums.
 //   reduce_kernel fixed-order sum of the partial Gram matrices.

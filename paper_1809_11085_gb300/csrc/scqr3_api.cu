@@ -36,6 +36,8 @@ cudaError_t df_setup();
 cudaError_t df_occupancy(int np, int* per_sm);
 int df_groups(int np);
 int df_rows_per_panel(int np);
+void launch_df_finish(int grid, cudaStream_t s, double* Q, int64_t ldq, int64_t m, int n,
+                      int max_passes, const DevState* st);
 void launch_df_pass(int np, int grid, cudaStream_t s, const double* src, int64_t lds, double* dst,
                     int64_t ldd, const Params& P, int pass, const double* rk, double* partials,
                     int part_stride, DevState* st);
@@ -137,6 +139,9 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
     return -12;
   if (opts && opts->precision != SCQR3_PREC_FP64 && opts->precision != SCQR3_PREC_MIXED) return -12;
   if (opts && opts->precision == SCQR3_PREC_MIXED && B) return -5;  // mixed form: B = I only
+  if (opts && opts->algorithm != 0 && opts->algorithm != SCQR3_ALG_SCQR3 &&
+      opts->algorithm != SCQR3_ALG_ADAPTIVE)
+    return -12;
   if (padded_n(n) == 0) return SCQR3_E_UNSUPPORTED;
   // n > 128: FP64, B = I only
   if (n > 128 && (B || (opts && opts->precision == SCQR3_PREC_MIXED))) return SCQR3_E_UNSUPPORTED;
@@ -222,6 +227,20 @@ bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
 }
 
 }  // namespace
+
+void set_options(Params* P, const scqr3_opts* opts) {
+  const double u = 1.1102230246251565e-16;
+  P->shift_scale = (opts && opts->shift_scale > 0.0) ? opts->shift_scale : 0.0;
+  P->algorithm = (opts && opts->algorithm == SCQR3_ALG_ADAPTIVE) ? 2 : 3;
+  // default Alg. 2 tolerance: the bound 6 {mn + n(n+1)} u of Thm. (maincholqr3)
+  // (volatile: every product rounded on its own, never contracted into an FMA)
+  const double dm = (double)P->m, dn = (double)P->n;
+  const volatile double mn = dm * dn, nn1 = dn * (double)(P->n + 1);
+  const volatile double sum = mn + nn1;
+  const double dflt = 6.0 * sum * u;
+  P->tol = (opts && opts->tol > 0.0) ? opts->tol : dflt;
+}
+
 }  // namespace scqr3
 
 using namespace scqr3;
@@ -285,6 +304,7 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   P.bs = B ? B->bs : 0;
   P.norm_x2 = opts ? opts->norm_x2 : 0.0;
   P.normb_in = B ? B->norm2 : 0.0;
+  set_options(&P, opts);
 
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return SCQR3_E_CUDA;
   if (cudaMemsetAsync(info, 0, sizeof(scqr3_info), s) != cudaSuccess) return SCQR3_E_CUDA;
@@ -324,7 +344,7 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
     return SCQR3_OK;
   }
 
-  // Pass 1, Alg. 3 line 2: A = X^T X (or X^T B X).
+  // Pass 1 of Alg. 3: A = X^T X (or X^T B X).
   tick(s, SCQR3_KERNEL_GRAM, 0);
   if (mixed)
     launch_df_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, partials, L.part_stride, st);
@@ -351,6 +371,10 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
       tick(s, SCQR3_KERNEL_CHOL, k + 1);
       launch_chol(P.np, s, P, k + 1, gram, rstack, racc, R, Rpass, st, info);
     }
+  }
+  if (mixed) {
+    tick(s, SCQR3_KERNEL_FINISH, -1);
+    launch_df_finish(sm_count() * 4, s, Q, ldq, m, n, P.max_passes, st);
   }
   tick(s, -1, -1);
   if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;

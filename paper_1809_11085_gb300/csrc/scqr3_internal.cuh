@@ -38,7 +38,13 @@ struct Params {
   int bs;            // 0: B = I; else block size of B
   double norm_x2;    // opts.norm_x2
   double normb_in;   // B->norm2 (<= 0: compute)
+  double shift_scale;  // opts.shift_scale (<= 0: Eq. (finds2)/(finds2B) only)
+  int algorithm;       // 2 (Alg. 2) or 3 (Alg. 3)
+  double tol;          // Alg. 2 stopping tolerance (resolved on the host, > 0)
 };
+
+// Params fields set from the options (shared by the single and batched paths).
+void set_options(Params* P, const scqr3_opts* opts);
 
 // Workspace carve-up (byte offsets from the base, each 256-aligned).
 struct Layout {

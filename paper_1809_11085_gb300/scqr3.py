@@ -38,7 +38,8 @@ class _B(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("max_passes", ctypes.c_int), ("precision", ctypes.c_int),
-                ("norm_x2", ctypes.c_double)]
+                ("norm_x2", ctypes.c_double), ("shift_scale", ctypes.c_double),
+                ("algorithm", ctypes.c_int), ("tol", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -53,7 +54,7 @@ INFO_BYTES = ctypes.sizeof(_Info)
 
 KERNEL_GRAM, KERNEL_PASS, KERNEL_REDUCE, KERNEL_CHOL, KERNEL_BFACTOR = 0, 1, 2, 3, 4
 KERNEL_NAMES = {0: "pass_kernel(gram)", 1: "pass_kernel(solve+gram)", 2: "reduce_kernel",
-                3: "chol_kernel", 4: "bfactor_kernel"}
+                3: "chol_kernel", 4: "bfactor_kernel", 5: "trsm256_kernel", 6: "df_finish_kernel"}
 
 
 class _LaunchTime(ctypes.Structure):
@@ -129,10 +130,13 @@ def _b_struct(B, normb):
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+ALG_ADAPTIVE = 2  # Alg. 2: shift only on breakdown, stop on the orthogonality test
+ALG_SCQR3 = 3     # Alg. 3: shifted pass, then CholeskyQR2
 
 
-def _opts(max_passes, norm_x2, precision=PREC_FP64):
-    o = _Opts(int(max_passes), int(precision), float(norm_x2))
+def _opts(max_passes, norm_x2, precision=PREC_FP64, shift_scale=0.0, algorithm=ALG_SCQR3, tol=0.0):
+    o = _Opts(int(max_passes), int(precision), float(norm_x2), float(shift_scale), int(algorithm),
+              float(tol))
     return o, ctypes.byref(o)
 
 
@@ -162,10 +166,13 @@ class Workspace:
 
 def factor(X, B=None, *, max_passes: int = 0, norm_x2: float = 0.0, normb: float = 0.0,
            Q=None, R=None, Rpass=None, workspace: Workspace | None = None, stream=None,
-           read_info: bool = True, precision: int = PREC_FP64):
+           read_info: bool = True, precision: int = PREC_FP64, shift_scale: float = 0.0,
+           algorithm: int = ALG_SCQR3, tol: float = 0.0):
     """Shifted CholeskyQR3 of X (m x n, float64 CUDA tensor) through scqr3_factor.
 
     Returns (Q, R, info). Q may be passed as X for an in-place factorization.
+    shift_scale, algorithm and tol are the scqr3_opts fields of the same names
+    (the smaller first shift of the Sec. 6.1 remark; Alg. 2 and its tolerance).
     With read_info=False nothing synchronizes and info is the raw device
     buffer (decode later with Info.from_bytes(buf.cpu().numpy().tobytes())).
     """
@@ -186,7 +193,7 @@ def factor(X, B=None, *, max_passes: int = 0, norm_x2: float = 0.0, normb: float
     if workspace is None:
         workspace = Workspace(m, n, B, max_passes, device=X.device)
     b, bp = _b_struct(B, normb)
-    o, op = _opts(max_passes, norm_x2, precision)
+    o, op = _opts(max_passes, norm_x2, precision, shift_scale, algorithm, tol)
     if stream is None:
         stream = torch.cuda.current_stream(X.device).cuda_stream
     r = lib().scqr3_factor(X.data_ptr(), m, n, X.stride(0), bp, Q.data_ptr(), Q.stride(0),

@@ -266,7 +266,7 @@ def test_R_equals_R_factor_of_sigma_vt(kappa):
 
 
 def test_accumulation_order_R_is_Rtilde_times_R():
-    """R := Rt R (Alg. 2 line 9): the reversed product would break X = QR."""
+    """R := Rt R (the update of Alg. 2): the reversed product would break X = QR."""
     X = testmat(400, 9, 1e11, seed=5)
     Q, R, st, tr = oracle.scqr3(X)
     assert st == 0 and tr["passes"] >= 3
@@ -487,3 +487,19 @@ def test_option_arguments_checked():
     X = testmat(100, 4, 10.0, seed=9)
     assert oracle.scqr3(X, algorithm=1)[2] == oracle.E_ARG
     assert oracle.scqr3(X, algorithm=4)[2] == oracle.E_ARG
+
+
+@pytest.mark.parametrize("m,n", [(1000, 30), (20000, 64)])
+@pytest.mark.parametrize("kappa", [1e16, 1e18, 1e20])
+def test_alg2_beyond_one_over_u(m, n, kappa):
+    """Sec. 4 observes that Alg. 2 may work even for kappa(X) > 1/u (no
+    guarantee): shifted passes repeat until kappa(Q) allows CholeskyQR2. The
+    orthogonality and residual bounds of Thm. (maincholqr3) still hold, every
+    shifted pass precedes every plain one, and two plain passes end it."""
+    X = testmat(m, n, kappa, seed=77)
+    Q, R, st, tr = oracle.scqr3(X, normx2=1.0, algorithm=2, max_passes=8)
+    assert st == 0
+    k = tr["passes"]
+    assert k >= 4 and tr["shifted"] == [1] * (k - 2) + [0, 0]
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 6 * (m * n + n * (n + 1)) * U
+    assert np.linalg.norm(Q @ R - X) / np.linalg.norm(X, 2) <= 15 * n * n * U
