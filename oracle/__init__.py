@@ -73,6 +73,12 @@ def lib():
         L.orc_scqr3_ex.argtypes = [i64, i32, p, i64, i32, p, f64, f64, i32, f64, i32, f64, p, i64,
                                    p, ctypes.POINTER(_Trace)]
         L.orc_scqr3_ex.restype = i32
+        L.orc_gram_csr.argtypes = [i64, i32, p, i64, p, p, p, p, p]
+        L.orc_normb_csr.argtypes = [i64, p, p]
+        L.orc_normb_csr.restype = f64
+        L.orc_scqr3_csr.argtypes = [i64, i32, p, i64, p, p, p, f64, f64, i32, f64, i32, f64, p,
+                                    i64, p, ctypes.POINTER(_Trace)]
+        L.orc_scqr3_csr.restype = i32
         _lib = L
     return _lib
 
@@ -144,6 +150,29 @@ def trmm(Rt: np.ndarray, R: np.ndarray) -> np.ndarray:
     return out
 
 
+def _csr(csr):
+    row_ptr, col_idx, vals = csr
+    return (np.ascontiguousarray(row_ptr, dtype=np.int64), np.ascontiguousarray(col_idx, dtype=np.int32),
+            np.ascontiguousarray(vals, dtype=np.float64))
+
+
+def gram_csr(X: np.ndarray, csr):
+    """A = X^T (B X) for B given as (row_ptr, col_idx, vals); returns (A, ||X||_F^2)."""
+    X = _c(X)
+    m, n = X.shape
+    rp, ci, v = _csr(csr)
+    A = np.empty((n, n))
+    f = ctypes.c_double(0.0)
+    lib().orc_gram_csr(m, n, _ptr(X), n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(A), ctypes.byref(f))
+    return A, f.value
+
+
+def normb_csr(csr) -> float:
+    """Largest absolute row sum of the CSR matrix (>= ||B||_2 for symmetric B)."""
+    rp, _, v = _csr(csr)
+    return lib().orc_normb_csr(len(rp) - 1, _ptr(rp), _ptr(v))
+
+
 def normb_bound(Bblk: np.ndarray) -> float:
     Bblk = _c(Bblk)
     nb, bs, _ = Bblk.shape
@@ -152,7 +181,7 @@ def normb_bound(Bblk: np.ndarray) -> float:
 
 def scqr3(X: np.ndarray, Bblk: np.ndarray | None = None, normx2: float = 0.0,
           normb: float = 0.0, max_passes: int = 6, shift_scale: float = 0.0, algorithm: int = 3,
-          tol: float = 0.0):
+          tol: float = 0.0, csr=None):
     """Shifted CholeskyQR3 (Alg. 3 / Alg. 5 with the breakdown rule of Alg. 2).
 
     shift_scale = c > 0 first tries the smaller shift c u ||X||^2 of the
@@ -161,12 +190,22 @@ def scqr3(X: np.ndarray, Bblk: np.ndarray | None = None, normx2: float = 0.0,
     orthogonality stopping test (tol <= 0: 6{mn + n(n+1)} u, the bound of
     Thm. maincholqr3). Returns (Q, R, status, trace) where trace is a dict with
     the per-pass record (passes, shifted, unshifted_fail, s, norm2).
+    csr = (row_ptr, col_idx, vals) selects a sparse SPD B in CSR form instead
+    of the block-diagonal Bblk.
     """
     X = _c(X)
     m, n = X.shape
     Q = np.empty((m, n))
     R = np.empty((n, n))
     tr = _Trace()
+    if csr is not None:
+        rp, ci, v = _csr(csr)
+        if len(rp) != m + 1:
+            raise ValueError("row_ptr must have m + 1 entries")
+        st = lib().orc_scqr3_csr(m, n, _ptr(X), n, _ptr(rp), _ptr(ci), _ptr(v), normx2, normb,
+                                 max_passes, shift_scale, algorithm, tol, _ptr(Q), n, _ptr(R),
+                                 ctypes.byref(tr))
+        return Q, R, st, _trace_dict(tr)
     if Bblk is None:
         bs, bp = 0, None
     else:
@@ -174,10 +213,13 @@ def scqr3(X: np.ndarray, Bblk: np.ndarray | None = None, normx2: float = 0.0,
         bs, bp = Bblk.shape[1], _ptr(Bblk)
     st = lib().orc_scqr3_ex(m, n, _ptr(X), n, bs, bp, normx2, normb, max_passes, shift_scale,
                             algorithm, tol, _ptr(Q), n, _ptr(R), ctypes.byref(tr))
+    return Q, R, st, _trace_dict(tr)
+
+
+def _trace_dict(tr):
     k = tr.passes
-    trace = {"passes": k,
-             "shifted": list(tr.shifted[:k]),
-             "unshifted_fail": list(tr.unshifted_fail[:k]),
-             "s": list(tr.s[:k]),
-             "norm2": list(tr.norm2[:k])}
-    return Q, R, st, trace
+    return {"passes": k,
+            "shifted": list(tr.shifted[:k]),
+            "unshifted_fail": list(tr.unshifted_fail[:k]),
+            "s": list(tr.s[:k]),
+            "norm2": list(tr.norm2[:k])}

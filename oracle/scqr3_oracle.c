@@ -139,6 +139,56 @@ double orc_normb_bound(int64_t m, int bs, const double *Bblk) {
   return best;
 }
 
+void orc_gram_csr(int64_t m, int n, const double *X, int64_t ldx, const int64_t *row_ptr,
+                  const int32_t *col_idx, const double *vals, double *A, double *fro2) {
+  /* Y = B X with the sparse product of Sec. 7.2, then A = X^T Y. */
+  double *y = (double *)malloc(sizeof(double) * (size_t)n);
+  double f = 0.0;
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) A[j * n + k] = 0.0;
+  for (int64_t i = 0; i < m; ++i) {
+    for (int k = 0; k < n; ++k) y[k] = 0.0;
+    for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+      const double *xl = X + (int64_t)col_idx[p] * ldx;
+      for (int k = 0; k < n; ++k) y[k] = y[k] + vals[p] * xl[k];
+    }
+    const double *x = X + i * ldx;
+    for (int j = 0; j < n; ++j) {
+      f = f + x[j] * x[j];
+      for (int k = j; k < n; ++k) A[j * n + k] = A[j * n + k] + x[j] * y[k];
+    }
+  }
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < j; ++k) A[j * n + k] = A[k * n + j];
+  if (fro2) *fro2 = f;
+  free(y);
+}
+
+double orc_normb_csr(int64_t m, const int64_t *row_ptr, const double *vals) {
+  double best = 0.0;
+  for (int64_t i = 0; i < m; ++i) {
+    double r = 0.0;
+    for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) r = r + fabs(vals[p]);
+    if (r > best) best = r;
+  }
+  return best;
+}
+
+/* The inner product of one factorization: B = I, block-diagonal B or CSR B. */
+typedef struct {
+  int kind; /* 0: B = I; 1: block diagonal (bs, Bblk); 2: CSR */
+  int bs;
+  const double *Bblk;
+  const int64_t *row_ptr;
+  const int32_t *col_idx;
+  const double *vals;
+} orc_inner;
+
+static int orc_drive(int64_t m, int n, const double *X, int64_t ldx, const orc_inner *B,
+                     double normx2, double normb, int max_passes, double shift_scale,
+                     int algorithm, double tol, double *Q, int64_t ldq, double *R,
+                     orc_trace *trace);
+
 int orc_scqr3(int64_t m, int n, const double *X, int64_t ldx, int bs,
               const double *Bblk, double normx2, double normb, int max_passes,
               double *Q, int64_t ldq, double *R, orc_trace *trace) {
@@ -150,17 +200,37 @@ int orc_scqr3_ex(int64_t m, int n, const double *X, int64_t ldx, int bs,
                  const double *Bblk, double normx2, double normb, int max_passes,
                  double shift_scale, int algorithm, double tol, double *Q,
                  int64_t ldq, double *R, orc_trace *trace) {
+  if (bs > 0 && (m % bs) != 0) return ORC_E_ARG;
+  orc_inner B = {bs > 0 ? 1 : 0, bs, Bblk, NULL, NULL, NULL};
+  return orc_drive(m, n, X, ldx, &B, normx2, normb, max_passes, shift_scale, algorithm, tol, Q,
+                   ldq, R, trace);
+}
+
+int orc_scqr3_csr(int64_t m, int n, const double *X, int64_t ldx, const int64_t *row_ptr,
+                  const int32_t *col_idx, const double *vals, double normx2, double normb,
+                  int max_passes, double shift_scale, int algorithm, double tol, double *Q,
+                  int64_t ldq, double *R, orc_trace *trace) {
+  if (!row_ptr || !col_idx || !vals) return ORC_E_ARG;
+  orc_inner B = {2, 0, NULL, row_ptr, col_idx, vals};
+  return orc_drive(m, n, X, ldx, &B, normx2, normb, max_passes, shift_scale, algorithm, tol, Q,
+                   ldq, R, trace);
+}
+
+static int orc_drive(int64_t m, int n, const double *X, int64_t ldx, const orc_inner *B,
+                     double normx2, double normb, int max_passes, double shift_scale,
+                     int algorithm, double tol, double *Q, int64_t ldq, double *R,
+                     orc_trace *trace) {
   if (m < n || n < 1 || ldx < n || ldq < n || max_passes < 3 ||
-      max_passes > ORC_MAX_PASSES || (bs > 0 && (m % bs) != 0) ||
-      (algorithm != 2 && algorithm != 3))
+      max_passes > ORC_MAX_PASSES || (algorithm != 2 && algorithm != 3))
     return ORC_E_ARG;
   /* Alg. 2's printed tolerance sqrt(n) u lies below the rounding error of a
    * computed Gram matrix of orthonormal columns, so tol <= 0 selects the
    * orthogonality bound that Thm. (maincholqr3) proves for the final Q,
    * 6 {mn + n(n+1)} u. */
   if (!(tol > 0.0)) tol = 6.0 * ((double)m * (double)n + (double)n * (double)(n + 1)) * ORC_U;
-  const int oblique = bs > 0;
-  if (oblique && !(normb > 0.0)) normb = orc_normb_bound(m, bs, Bblk);
+  const int oblique = B->kind != 0;
+  if (B->kind == 1 && !(normb > 0.0)) normb = orc_normb_bound(m, B->bs, B->Bblk);
+  if (B->kind == 2 && !(normb > 0.0)) normb = orc_normb_csr(m, B->row_ptr, B->vals);
 
   double *A = (double *)malloc(sizeof(double) * (size_t)n * n);
   double *Rt = (double *)malloc(sizeof(double) * (size_t)n * n);
@@ -180,8 +250,10 @@ int orc_scqr3_ex(int64_t m, int n, const double *X, int64_t ldx, int bs,
     /* A := Q^T Q (or Q^T B Q); ||Q||^2 is estimated by ||Q||_F^2, which
      * for B = I is the trace of the computed Gram matrix (Sec. 4.1). */
     double nrm2 = 0.0;
-    if (oblique) {
-      orc_gram_oblique(m, n, Q, ldq, bs, Bblk, A, &nrm2);
+    if (B->kind == 1) {
+      orc_gram_oblique(m, n, Q, ldq, B->bs, B->Bblk, A, &nrm2);
+    } else if (B->kind == 2) {
+      orc_gram_csr(m, n, Q, ldq, B->row_ptr, B->col_idx, B->vals, A, &nrm2);
     } else {
       orc_gram(m, n, Q, ldq, A);
       for (int j = 0; j < n; ++j) nrm2 = nrm2 + A[j * n + j];

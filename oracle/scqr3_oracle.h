@@ -75,6 +75,18 @@ void orc_trmm(int n, const double *Rt, double *R);
  * block's Frobenius norm. */
 double orc_normb_bound(int64_t m, int bs, const double *Bblk);
 
+/* Oblique Gram A = X^T (B X) for a sparse symmetric B held in CSR form
+ * (Sec. 7.2 forms Y := B X with a sparse product, then X^T Y). Row i of Y is
+ * y_i = sum over the stored entries p = row_ptr[i] .. row_ptr[i+1]-1, in
+ * storage order, of vals[p] x_{col_idx[p]}; then the upper triangle of X^T Y
+ * by ascending rows, mirrored. Also sum_ij x_ij^2 in *fro2 (may be NULL). */
+void orc_gram_csr(int64_t m, int n, const double *X, int64_t ldx, const int64_t *row_ptr,
+                  const int32_t *col_idx, const double *vals, double *A, double *fro2);
+
+/* Upper bound of ||B||_2 for symmetric B in CSR form: the largest absolute
+ * row sum (||B||_2 = rho(B) <= ||B||_inf, Gershgorin). */
+double orc_normb_csr(int64_t m, const int64_t *row_ptr, const double *vals);
+
 /* Shifted CholeskyQR3 (Alg. 3; oblique: Alg. 5) with the breakdown rule of
  * Alg. 2: pass 1 is always shifted; a later pass whose plain Cholesky
  * breaks down is redone with the shift; the factorization ends after two
@@ -105,6 +117,13 @@ int orc_scqr3_ex(int64_t m, int n, const double *X, int64_t ldx, int bs,
                  const double *Bblk, double normx2, double normb, int max_passes,
                  double shift_scale, int algorithm, double tol, double *Q,
                  int64_t ldq, double *R, orc_trace *trace);
+
+/* orc_scqr3_ex with the oblique inner product of a sparse SPD B in CSR form
+ * (Alg. 5, Gram by orc_gram_csr; normb <= 0 selects orc_normb_csr). */
+int orc_scqr3_csr(int64_t m, int n, const double *X, int64_t ldx, const int64_t *row_ptr,
+                  const int32_t *col_idx, const double *vals, double normx2, double normb,
+                  int max_passes, double shift_scale, int algorithm, double tol, double *Q,
+                  int64_t ldq, double *R, orc_trace *trace);
 
 #ifdef __cplusplus
 }

@@ -10,6 +10,11 @@ Holds none of the factorization's arithmetic: it only draws matrices.
 * ``block_diag_spd``: B = blockdiag(G_j^T G_j + shift I) with seeded Gaussian
   G_j, the block-diagonal SPD inner product used for the oblique variant.
 * ``batched_shapes``: the uneven (m_i, n_i, kappa_i) mix of the batched form.
+* ``laplacian_csr`` / ``random_spd_csr``: sparse SPD B in CSR form for the
+  oblique variant with a sparse inner product (Sec. 7.2 uses SuiteSparse
+  matrices, which are not available here; these stand in for them): the
+  shifted finite-difference Laplacian of a 2-D or 3-D grid with an exact
+  kappa_2(B), and a symmetric random pattern made diagonally dominant.
 
 numpy versions serve sizes the CPU oracle can handle; the torch versions draw
 the same distributions on a CUDA device for the large cases.
@@ -127,3 +132,77 @@ def block_diag_spd_torch(m: int, bs: int, seed: int, shift: float = 0.1, device=
     B = torch.matmul(G.transpose(1, 2), G)
     B += shift * torch.eye(bs, device=device, dtype=torch.float64)
     return B.contiguous()
+
+
+def laplacian_csr(dims, kappa_b: float):
+    """B = L + sigma I, L the Dirichlet 5-point (2-D) or 7-point (3-D) Laplacian
+    on a grid of `dims` points in natural ordering, sigma chosen so that
+    kappa_2(B) = kappa_b exactly (sigma may be negative; B stays SPD).
+    Returns (row_ptr int64, col_idx int32, vals float64), columns ascending."""
+    dims = tuple(int(d) for d in dims)
+    m = int(np.prod(dims))
+    lam_lo = sum(2.0 - 2.0 * np.cos(np.pi / (d + 1)) for d in dims)
+    lam_hi = sum(2.0 - 2.0 * np.cos(d * np.pi / (d + 1)) for d in dims)
+    sigma = (lam_hi - kappa_b * lam_lo) / (kappa_b - 1.0)
+    strides = [int(np.prod(dims[a + 1:])) for a in range(len(dims))]
+    idx = np.arange(m, dtype=np.int64)
+    coord = [(idx // strides[a]) % dims[a] for a in range(len(dims))]
+    offs, masks = [], []
+    for a in range(len(dims)):  # -stride, largest stride first: ascending columns
+        offs.append(-strides[a])
+        masks.append(coord[a] > 0)
+    offs.append(0)
+    masks.append(np.ones(m, dtype=bool))
+    for a in reversed(range(len(dims))):
+        offs.append(strides[a])
+        masks.append(coord[a] < dims[a] - 1)
+    M = np.stack(masks, axis=1)
+    cols = idx[:, None] + np.asarray(offs, dtype=np.int64)[None, :]
+    vals = np.where(np.asarray(offs)[None, :] == 0, 2.0 * len(dims) + sigma, -1.0)
+    vals = np.broadcast_to(vals, M.shape)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(M.sum(axis=1), out=row_ptr[1:])
+    return row_ptr, cols[M].astype(np.int32), np.ascontiguousarray(vals[M], dtype=np.float64)
+
+
+def random_spd_csr(m: int, per_row: int, kappa_b: float, seed: int):
+    """Symmetric B with about 2*per_row off-diagonal entries per row at uniformly
+    random columns (values uniform in [-1, 1]) and diagonal
+    b_ii = sum_j |b_ij| + c, so that kappa_2(B) <= (2 max_i r_i + c) / c with
+    r_i the off-diagonal row sums; c is set from kappa_b. Long-range pattern:
+    the rows a sparse product gathers are scattered over the whole matrix."""
+    rng = np.random.default_rng(seed)
+    i = np.repeat(np.arange(m, dtype=np.int64), per_row)
+    j = rng.integers(0, m, size=i.size)
+    v = rng.uniform(-1.0, 1.0, size=i.size)
+    keep = i != j
+    i, j, v = i[keep], j[keep], v[keep]
+    r = np.concatenate([i, j])
+    c = np.concatenate([j, i])
+    v = np.concatenate([v, v])
+    key = r * m + c
+    order = np.argsort(key, kind="stable")
+    key, v = key[order], v[order]
+    ukey, start = np.unique(key, return_index=True)
+    v = np.add.reduceat(v, start)
+    r, c = ukey // m, ukey % m
+    rsum = np.zeros(m)
+    np.add.at(rsum, r, np.abs(v))
+    cdiag = 2.0 * rsum.max() / (kappa_b - 1.0)
+    r = np.concatenate([r, np.arange(m, dtype=np.int64)])
+    c = np.concatenate([c, np.arange(m, dtype=np.int64)])
+    v = np.concatenate([v, rsum + cdiag])
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(row_ptr, r + 1, 1)
+    np.cumsum(row_ptr, out=row_ptr)
+    return row_ptr, c.astype(np.int32), v
+
+
+def csr_to_dense(csr, m: int) -> np.ndarray:
+    row_ptr, col_idx, vals = csr
+    B = np.zeros((m, m))
+    rows = np.repeat(np.arange(m), np.diff(row_ptr))
+    np.add.at(B, (rows, col_idx.astype(np.int64)), vals)
+    return B

@@ -503,3 +503,96 @@ def test_alg2_beyond_one_over_u(m, n, kappa):
     assert k >= 4 and tr["shifted"] == [1] * (k - 2) + [0, 0]
     assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 6 * (m * n + n * (n + 1)) * U
     assert np.linalg.norm(Q @ R - X) / np.linalg.norm(X, 2) <= 15 * n * n * U
+
+
+# --------------------------------------------------------------------------- sparse B in CSR form (Sec. 7.2)
+
+def _dense_to_csr(B):
+    m = B.shape[0]
+    rows, cols = np.nonzero(B)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    return np.cumsum(row_ptr), cols.astype(np.int32), B[rows, cols].astype(np.float64)
+
+
+def test_gram_csr_exact_on_integers():
+    """A = X^T (B X) on small integers is exact in FP64: compare with int64."""
+    rng = np.random.default_rng(61)
+    m, n = 40, 7
+    Bi = rng.integers(-3, 4, size=(m, m)) * (rng.random((m, m)) < 0.15)
+    Bi = Bi + Bi.T + np.diag(rng.integers(1, 9, size=m))
+    Xi = rng.integers(-4, 5, size=(m, n))
+    A, f = oracle.gram_csr(Xi.astype(float), _dense_to_csr(Bi.astype(float)))
+    want = Xi.T @ (Bi @ Xi)
+    assert np.array_equal(np.triu(A), np.triu(want).astype(float))
+    assert np.array_equal(A, A.T)
+    assert f == float((Xi * Xi).sum())
+
+
+def test_normb_csr_is_max_abs_row_sum_and_bounds_norm():
+    from paper_1809_11085_gb300.testmat import csr_to_dense, random_spd_csr
+
+    csr = random_spd_csr(500, 3, 1e3, seed=62)
+    B = csr_to_dense(csr, 500)
+    nb = oracle.normb_csr(csr)
+    assert nb == pytest.approx(np.abs(B).sum(axis=1).max(), rel=1e-14)
+    assert np.linalg.eigvalsh(B).max() <= nb
+
+
+def test_csr_block_diagonal_matches_block_path():
+    """A block-diagonal B stored as CSR (same entry order) is the same
+    arithmetic as the block-diagonal form: bitwise equal results."""
+    m, n, bs = 256, 12, 8
+    Bblk = block_diag_spd(m, bs, seed=63)
+    B = np.zeros((m, m))
+    for k in range(m // bs):
+        B[k * bs:(k + 1) * bs, k * bs:(k + 1) * bs] = Bblk[k]
+    X = testmat(m, n, 1e8, seed=64)
+    nb = 3.7
+    Q1, R1, st1, tr1 = oracle.scqr3(X, Bblk, normb=nb)
+    Q2, R2, st2, tr2 = oracle.scqr3(X, normb=nb, csr=_dense_to_csr(B))
+    assert st1 == st2 == 0
+    assert np.array_equal(Q1, Q2) and np.array_equal(R1, R2) and tr1 == tr2
+
+
+@pytest.mark.parametrize("dims,kappa_b", [((18, 20), 1e3), ((6, 7, 8), 1e2)])
+def test_csr_laplacian_reduces_to_standard(dims, kappa_b):
+    """B = L L^T (dense Cholesky of the sparse Laplacian, numpy): Q_B = L^{-T} Qt
+    and R_B = Rt with Qt Rt = QR(L^T X); the shift is Eq. (finds2B) with the
+    max absolute row sum for ||B||_2."""
+    from paper_1809_11085_gb300.testmat import csr_to_dense, laplacian_csr
+
+    csr = laplacian_csr(dims, kappa_b)
+    m = int(np.prod(dims))
+    n = 10
+    B = csr_to_dense(csr, m)
+    X = testmat(m, n, 1e6, seed=65)
+    Q, R, st, tr = oracle.scqr3(X, csr=csr)
+    assert st == 0
+    L = np.linalg.cholesky(B)
+    Qt, Rt = signfix_qr(L.T @ X)
+    assert np.linalg.norm(R - Rt) / np.linalg.norm(Rt) < 1e-8
+    QB = np.linalg.solve(L.T, Qt)
+    assert np.linalg.norm(Q - QB) / np.linalg.norm(QB) < 1e-8
+    assert np.linalg.norm(Q.T @ B @ Q - np.eye(n), 2) < 1e-13
+    assert tr["s"][0] == pytest.approx(
+        oracle.shift_oblique(m, n, float((X * X).sum()), float(np.abs(B).sum(axis=1).max())), rel=1e-12)
+
+
+def test_csr_random_pattern_bounds():
+    """Thm. (Bsta): ||Q^T B Q - I||_F <= 8[m sqrt(mn) u + n(n+1) u] kappa(B) and
+    ||QR - X||_F / ||X||_2 <= 16 n^2 u kappa(B)^{3/2} (here ||X||_2 = 1; the
+    theorem's condition 80 kappa(B)(m sqrt(mn) u + n(n+1) u) <= 1 holds)."""
+    from paper_1809_11085_gb300.testmat import csr_to_dense, random_spd_csr
+
+    m, n = 2000, 16
+    csr = random_spd_csr(m, 3, 1e3, seed=66)
+    B = csr_to_dense(csr, m)
+    ev = np.linalg.eigvalsh(B)
+    kb = ev.max() / ev.min()
+    X = testmat(m, n, 1e10, seed=67)
+    Q, R, st, tr = oracle.scqr3(X, normx2=1.0, csr=csr)
+    assert st == 0 and tr["shifted"][0] == 1
+    assert np.linalg.norm(Q.T @ B @ Q - np.eye(n)) <= 8 * (m * np.sqrt(m * n) * U + n * (n + 1) * U) * kb
+    assert 80 * kb * (m * np.sqrt(m * n) * U + n * (n + 1) * U) <= 1
+    assert np.linalg.norm(Q @ R - X) <= 16 * n * n * U * kb ** 1.5
