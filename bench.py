@@ -507,6 +507,35 @@ def extra_legs(torch, dev, stream, args):
     del X, B, Q, ws, BQ
     free()
 
+    # oblique inner product, sparse B in CSR form: shifted 2-D Laplacian on a
+    # 2048 x 2048 grid (kappa(B) = 1e3), same X as the block-diagonal leg
+    from paper_1809_11085_gb300.testmat import laplacian_csr
+
+    mm, nn = 4194304, 128
+    X, _, _ = testmat_torch(mm, nn, 1e10, seed=1300, device=dev)
+    Bc = scqr3.CsrB.from_arrays(laplacian_csr((2048, 2048), 1e3), device=dev)
+    Q = torch.empty_like(X)
+    ws = scqr3.Workspace(mm, nn, Bc, device=dev)
+    ms = _time(torch, stream, lambda: scqr3.factor(X, Bc, Q=Q, workspace=ws, read_info=False))
+    inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
+    scqr3.timing_begin()
+    scqr3.factor(X, Bc, Q=Q, workspace=ws, read_info=False)
+    recs, _ = scqr3.timing_end()
+    gram_ms = [r[2] for r in recs if r[0] == scqr3.KERNEL_GRAM]
+    gram_ms = gram_ms[:inf.passes]  # launches after the last needed Gram return at once
+    gram_flops = mm * nn * (nn + 1) + 2 * Bc.nnz * nn  # Q^T Y (upper triangle) + Y = B Q
+    Bt = torch.sparse_csr_tensor(Bc.row_ptr, Bc.col_idx.to(torch.int64), Bc.vals, size=(mm, mm))
+    legs["oblique_csr"] = {
+        "workload": "FP64 sCQR3 in the B inner product, X 4194304 x 128 (kappa 1e10), B sparse CSR: "
+                    "shifted 5-point Laplacian, 2048 x 2048 grid, kappa(B) 1e3",
+        "ms": round(ms, 2), "rows_per_s": mm / (ms * 1e-3), "passes": inf.passes, "status": inf.status,
+        "orth_B": _orth(torch, Q, Bt @ Q), "nnz": Bc.nnz,
+        "tflops": (inf.passes * (mm * nn * (nn + 1) + 2 * Bc.nnz * nn + mm * nn * nn)) / (ms * 1e-3) / 1e12,
+        "csr_gram_ms": [round(t, 2) for t in gram_ms],
+        "csr_gram_frac_fp64_peak": [gram_flops / (t * 1e-3) / 1e12 / FP64_PEAK_DERIVED_TFLOPS for t in gram_ms]}
+    del X, Bc, Bt, Q, ws
+    free()
+
     # backward pass at the headline size
     mm, nn = 16777216, 64
     X, _, _ = testmat_torch(mm, nn, 1e10, seed=1500, device=dev)

@@ -52,6 +52,10 @@ extern "C" {
 #define SCQR3_E_WORKSPACE (-104)  /* workspace too small or misaligned     */
 #define SCQR3_E_B_NOT_SPD (-105)  /* a diagonal block of B is not SPD      */
 #define SCQR3_E_UNSUPPORTED (-106)/* size not supported by this build      */
+#define SCQR3_E_B_INVALID (-108)  /* CSR form of B malformed: row_ptr not
+                                     non-decreasing within [0, nnz], a column
+                                     index outside [0, m), or a row without a
+                                     positive diagonal entry                */
 #define SCQR3_E_SCRATCH_LIMIT (-107) /* scqr3_factor_noalloc: the problem needs
                                         more scratch than its fixed array   */
 
@@ -66,13 +70,23 @@ extern "C" {
  * uses FP64 throughout, Sec. 6); expected orthogonality ~1e-14. */
 #define SCQR3_PREC_MIXED 1
 
-/* Oblique inner product (x, y)_B = x^T B y of Sec. 5, for block-diagonal
- * SPD B = blockdiag(B_1, ..., B_{m/bs}). */
+/* Oblique inner product (x, y)_B = x^T B y of Sec. 5, for SPD B given
+ * either block-diagonal, B = blockdiag(B_1, ..., B_{m/bs}) (bs > 0), or as a
+ * general sparse matrix in CSR form (bs = 0; Sec. 7.2 uses sparse B and
+ * forms B Q by a sparse product). The CSR form must be symmetric (the
+ * library uses its rows as given and does not check symmetry), with int64
+ * row offsets and int32 column indices, m < 2^31; n <= 128, FP64 only. */
 typedef struct {
-  int bs;               /* block size, one of 1, 2, 4, 8, 16; m % bs == 0  */
+  int bs;               /* block size, one of 1, 2, 4, 8, 16, m % bs == 0;
+                           0 selects the CSR fields below                   */
   const double *blocks; /* device: (m/bs) blocks of bs*bs row-major FP64    */
-  double norm2;         /* ||B||_2 if > 0; otherwise the bound
-                           max_j ||B_j||_F is computed on the device        */
+  double norm2;         /* ||B||_2 if > 0; otherwise an upper bound is
+                           computed on the device: max_j ||B_j||_F (blocks),
+                           the largest absolute row sum (CSR)               */
+  const int64_t *row_ptr; /* CSR: device, m + 1 offsets, row_ptr[0] = 0     */
+  const int32_t *col_idx; /* CSR: device, nnz column indices                */
+  const double *vals;     /* CSR: device, nnz values                        */
+  int64_t nnz;            /* CSR: entries in col_idx / vals                 */
 } scqr3_B;
 
 typedef struct {

@@ -110,7 +110,7 @@ __device__ __forceinline__ void pass_segment(const double* src, int64_t lds, dou
   if (pass >= 0) {
     if (!st->run_trsm[pass]) return;
     do_trsm = true;
-    do_gram = st->gram_after[pass] != 0;
+    do_gram = st->gram_after[pass] != 0 && !P.csr;  // CSR B: Gram by csr_gram_kernel
   }
 
   if (do_trsm) {
@@ -292,7 +292,7 @@ __device__ __forceinline__ double shift_value(const Params& P, double nrm2, doub
   const double dm = (double)P.m, dn = (double)P.n;
   const double nn1 = __dmul_rn(dn, (double)(P.n + 1));
   double t;
-  if (P.bs > 0) {
+  if (is_oblique(P)) {
     t = __dmul_rn(__dmul_rn(2.0, dm), sqrt(__dmul_rn(dm, dn)));
   } else {
     t = __dmul_rn(dm, dn);
@@ -300,7 +300,7 @@ __device__ __forceinline__ double shift_value(const Params& P, double nrm2, doub
   double s = __dmul_rn(11.0, __dadd_rn(t, nn1));
   s = __dmul_rn(s, u);
   s = __dmul_rn(s, nrm2);
-  if (P.bs > 0) s = __dmul_rn(s, normb);
+  if (is_oblique(P)) s = __dmul_rn(s, normb);
   return s;
 }
 
@@ -308,7 +308,7 @@ __device__ __forceinline__ double shift_value(const Params& P, double nrm2, doub
 __device__ __forceinline__ double small_shift_value(const Params& P, double nrm2, double normb) {
   const double u = 1.1102230246251565e-16;
   double s = __dmul_rn(__dmul_rn(P.shift_scale, u), nrm2);
-  if (P.bs > 0) s = __dmul_rn(s, normb);
+  if (is_oblique(P)) s = __dmul_rn(s, normb);
   return s;
 }
 
@@ -390,13 +390,13 @@ __device__ __forceinline__ void chol_body(const Params& P, int pass, const doubl
     // ||Q||^2 estimate: trace of the Gram matrix (B = I), else the sum of
     // squares accumulated in the same pass (Sec. 4.1: ||.||_F for ||.||_2).
     double nrm2 = 0.0;
-    if (P.bs > 0) {
+    if (is_oblique(P)) {
       nrm2 = gram[E];
     } else {
       for (int j = 0; j < n; ++j) nrm2 = nrm2 + S[pk_idx(NP, j, j)];
     }
     if (pass == 0 && P.norm_x2 > 0.0) nrm2 = P.norm_x2;
-    if (pass == 0 && P.bs > 0)
+    if (pass == 0 && is_oblique(P))
       st->normb = P.normb_in > 0.0 ? P.normb_in : st->normb_bits_max;
     nrm_sh = nrm2;
     // Alg. 3 shifts pass 1 unconditionally; Alg. 2 tries the plain Cholesky first

@@ -41,6 +41,12 @@ void launch_df_finish(int grid, cudaStream_t s, double* Q, int64_t ldq, int64_t 
 void launch_df_pass(int np, int grid, cudaStream_t s, const double* src, int64_t lds, double* dst,
                     int64_t ldd, const Params& P, int pass, const double* rk, double* partials,
                     int part_stride, DevState* st);
+cudaError_t csr_setup(int per_sm[4]);
+int csr_rows_per_panel(int np);
+int csr_groups(int np);
+void launch_csr_check(int grid, cudaStream_t s, int64_t m, const scqr3_B* B, DevState* st);
+void launch_csr_gram(int np, int grid, cudaStream_t s, const double* src, int64_t lds, const Params& P,
+                     int pass, const scqr3_B* B, double* partials, int part_stride, const DevState* st);
 
 namespace {
 
@@ -63,6 +69,7 @@ struct DevGeo {
   int trsm256_per_sm = 0, gram256_per_sm = 0;
   int ctas_per_sm[5] = {0, 0, 0, 0, 0};
   int df_ctas_per_sm[5] = {0, 0, 0, 0, 0};
+  int csr_ctas_per_sm[4] = {0, 0, 0, 0};
   PassGeom geo[5];
 };
 constexpr int kMaxDevices = 64;
@@ -96,6 +103,10 @@ cudaError_t device_geo(int np, int* grid_max, PassGeom* geo) {
       if (e != cudaSuccess) return e;
       if (d.df_ctas_per_sm[np_slot(s)] < 1) return cudaErrorInvalidConfiguration;
     }
+    e = csr_setup(d.csr_ctas_per_sm);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < 4; ++k)
+      if (d.csr_ctas_per_sm[k] < 1) return cudaErrorInvalidConfiguration;
     d.ready = true;
   }
   if (np == 256) {
@@ -117,6 +128,12 @@ int trsm256_grid(int64_t m) {
   return (int)(np < g ? (np < 1 ? 1 : np) : g);
 }
 
+int csr_grid_max(int np) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return g_geo[dev].sms * g_geo[dev].csr_ctas_per_sm[np_slot(np)];
+}
+
 int df_grid_max(int np) {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -132,9 +149,13 @@ int sm_count() {
 int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
   if (n < 1) return -3;
   if (m < n) return -2;
-  if (B && (B->bs != 1 && B->bs != 2 && B->bs != 4 && B->bs != 8 && B->bs != 16)) return -5;
-  if (B && (m % B->bs) != 0) return -5;
-  if (B && !B->blocks) return -5;
+  if (B && (B->bs != 0 && B->bs != 1 && B->bs != 2 && B->bs != 4 && B->bs != 8 && B->bs != 16))
+    return -5;
+  if (B && B->bs > 0 && ((m % B->bs) != 0 || !B->blocks)) return -5;
+  // CSR form: arrays present, a diagonal entry per row possible, int32 columns
+  if (B && B->bs == 0 && (!B->row_ptr || !B->col_idx || !B->vals || B->nnz < m || m > INT32_MAX))
+    return -5;
+  if (B && B->bs == 0 && n > 128) return SCQR3_E_UNSUPPORTED;
   if (opts && opts->max_passes != 0 && (opts->max_passes < 3 || opts->max_passes > SCQR3_MAX_PASSES))
     return -12;
   if (opts && opts->precision != SCQR3_PREC_FP64 && opts->precision != SCQR3_PREC_MIXED) return -12;
@@ -171,7 +192,16 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, Layout* L, int* 
   const int E = pk_size(np);
   L->part_stride = E + 1;
   L->n_partials = mixed ? slotsdf : slots64;
-  const int slots_alloc = slots64 > slotsdf ? slots64 : slotsdf;
+  int slots_alloc = slots64 > slotsdf ? slots64 : slotsdf;
+  L->csr_grid = 0;
+  if (B && B->bs == 0 && np <= 128) {
+    const int64_t np_csr = (m + csr_rows_per_panel(np) - 1) / csr_rows_per_panel(np);
+    const int csr_max = csr_grid_max(np);
+    L->csr_grid = (int)(np_csr < csr_max ? np_csr : csr_max);
+    if (L->csr_grid < 1) L->csr_grid = 1;
+    L->n_partials = L->csr_grid * csr_groups(np);
+    if (L->n_partials > slots_alloc) slots_alloc = L->n_partials;
+  }
   size_t off = 0;
   L->state = off;
   off = align256(off + sizeof(DevState));
@@ -184,7 +214,7 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, Layout* L, int* 
   L->chol = off;  // Cholesky work buffers in global memory (n > 128)
   if (np == 256) off = align256(off + sizeof(double) * 2 * (size_t)E);
   L->lt = off;
-  if (B) {
+  if (B && B->bs > 0) {
     const int64_t nblk = m / B->bs;
     off = align256(off + sizeof(double) * (size_t)nblk * (B->bs * (B->bs + 1) / 2));
   }
@@ -293,7 +323,8 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   double* gram = (double*)(ws + L.gram);
   double* rstack = (double*)(ws + L.rstack);
   double* racc = (double*)(ws + L.racc);
-  double* lt = B ? (double*)(ws + L.lt) : nullptr;
+  const bool csr = B && B->bs == 0;
+  double* lt = (B && B->bs > 0) ? (double*)(ws + L.lt) : nullptr;
   double* partials = (double*)(ws + L.partials);
 
   Params P;
@@ -304,13 +335,18 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   P.bs = B ? B->bs : 0;
   P.norm_x2 = opts ? opts->norm_x2 : 0.0;
   P.normb_in = B ? B->norm2 : 0.0;
+  P.csr = csr ? 1 : 0;
   set_options(&P, opts);
 
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return SCQR3_E_CUDA;
   if (cudaMemsetAsync(info, 0, sizeof(scqr3_info), s) != cudaSuccess) return SCQR3_E_CUDA;
-  if (B) {
+  if (B && B->bs > 0) {
     tick(s, SCQR3_KERNEL_BFACTOR, 0);
     launch_bfactor(s, B->bs, B->blocks, m / B->bs, lt, st, sm_count());
+  }
+  if (csr) {
+    tick(s, SCQR3_KERNEL_BFACTOR, 0);
+    launch_csr_check(sm_count() * 4, s, m, B, st);
   }
 
   if (P.np == 256) {
@@ -346,7 +382,9 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
 
   // Pass 1 of Alg. 3: A = X^T X (or X^T B X).
   tick(s, SCQR3_KERNEL_GRAM, 0);
-  if (mixed)
+  if (csr)
+    launch_csr_gram(P.np, L.csr_grid, s, X, ldx, P, -1, B, partials, L.part_stride, st);
+  else if (mixed)
     launch_df_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, partials, L.part_stride, st);
   else
     launch_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, lt, partials, L.part_stride, st);
@@ -366,6 +404,10 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
       launch_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, lt, partials,
                   L.part_stride, st);
     if (k + 1 < P.max_passes) {
+      if (csr) {
+        tick(s, SCQR3_KERNEL_GRAM, k + 1);
+        launch_csr_gram(P.np, L.csr_grid, s, Q, ldq, P, k, B, partials, L.part_stride, st);
+      }
       tick(s, SCQR3_KERNEL_REDUCE, k + 1);
       launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, k);
       tick(s, SCQR3_KERNEL_CHOL, k + 1);

@@ -41,7 +41,11 @@ struct Params {
   double shift_scale;  // opts.shift_scale (<= 0: Eq. (finds2)/(finds2B) only)
   int algorithm;       // 2 (Alg. 2) or 3 (Alg. 3)
   double tol;          // Alg. 2 stopping tolerance (resolved on the host, > 0)
+  int csr;             // 1: B in CSR form (pass kernel solves only; csr_gram forms Q^T B Q)
 };
+
+// The factorization uses an oblique inner product (block-diagonal or CSR B).
+__host__ __device__ inline bool is_oblique(const Params& P) { return P.bs > 0 || P.csr != 0; }
 
 // Params fields set from the options (shared by the single and batched paths).
 void set_options(Params* P, const scqr3_opts* opts);
@@ -50,6 +54,7 @@ void set_options(Params* P, const scqr3_opts* opts);
 struct Layout {
   size_t state, gram, rstack, racc, chol, lt, partials, total;
   int n_partials;    // partial Gram slots used by this call (grid CTAs x groups)
+  int csr_grid;      // CTAs of csr_gram_kernel (CSR form only)
   int part_stride;   // doubles per partial slot: pk_size(np) + 1 (||.||_F^2)
 };
 

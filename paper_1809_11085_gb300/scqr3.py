@@ -17,6 +17,7 @@ MAX_N = 128
 OK = 0
 E_NONFINITE = -100
 E_MAXPASS = -101
+E_B_INVALID = -108
 E_CUDA = -103
 E_WORKSPACE = -104
 E_B_NOT_SPD = -105
@@ -33,7 +34,44 @@ class ScqrError(RuntimeError):
 
 
 class _B(ctypes.Structure):
-    _fields_ = [("bs", ctypes.c_int), ("blocks", ctypes.c_void_p), ("norm2", ctypes.c_double)]
+    _fields_ = [("bs", ctypes.c_int), ("blocks", ctypes.c_void_p), ("norm2", ctypes.c_double),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("nnz", ctypes.c_int64)]
+
+
+class CsrB:
+    """A sparse symmetric positive definite B in CSR form on the device, for the
+    oblique inner product (Sec. 5; Sec. 7.2 forms B Q by a sparse product).
+
+    row_ptr: int64 (m + 1,), col_idx: int32 (nnz,), vals: float64 (nnz,), all
+    contiguous CUDA tensors. norm2 > 0 gives ||B||_2; otherwise the library
+    uses the largest absolute row sum.
+    """
+
+    def __init__(self, row_ptr, col_idx, vals, norm2: float = 0.0):
+        import torch
+
+        for t, dt, name in ((row_ptr, torch.int64, "row_ptr"), (col_idx, torch.int32, "col_idx"),
+                            (vals, torch.float64, "vals")):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.dim() == 1
+                    and t.is_contiguous()):
+                raise TypeError("%s must be a contiguous 1-D %s CUDA tensor" % (name, dt))
+        if col_idx.numel() != vals.numel():
+            raise ValueError("col_idx and vals must have the same length")
+        self.row_ptr, self.col_idx, self.vals = row_ptr, col_idx, vals
+        self.m = row_ptr.numel() - 1
+        self.nnz = vals.numel()
+        self.norm2 = float(norm2)
+
+    @classmethod
+    def from_arrays(cls, csr, device="cuda", norm2: float = 0.0):
+        """From host (row_ptr, col_idx, vals) arrays (e.g. numpy)."""
+        import torch
+
+        rp, ci, v = csr
+        return cls(torch.as_tensor(rp, dtype=torch.int64).to(device).contiguous(),
+                   torch.as_tensor(ci, dtype=torch.int32).to(device).contiguous(),
+                   torch.as_tensor(v, dtype=torch.float64).to(device).contiguous(), norm2)
 
 
 class _Opts(ctypes.Structure):
@@ -121,9 +159,14 @@ def _b_struct(B, normb):
         return None, None
     import torch
 
+    if isinstance(B, CsrB):
+        b = _B(0, None, float(normb or B.norm2), ctypes.c_void_p(B.row_ptr.data_ptr()),
+               ctypes.c_void_p(B.col_idx.data_ptr()), ctypes.c_void_p(B.vals.data_ptr()), int(B.nnz))
+        return b, ctypes.byref(b)
+
     if not (isinstance(B, torch.Tensor) and B.is_cuda and B.dtype == torch.float64 and B.dim() == 3
             and B.shape[1] == B.shape[2] and B.is_contiguous()):
-        raise TypeError("B must be a contiguous (m/bs, bs, bs) float64 CUDA tensor")
+        raise TypeError("B must be a CsrB or a contiguous (m/bs, bs, bs) float64 CUDA tensor")
     b = _B(int(B.shape[1]), ctypes.c_void_p(B.data_ptr()), float(normb))
     return b, ctypes.byref(b)
 

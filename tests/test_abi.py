@@ -60,6 +60,14 @@ def test_argument_errors_are_reported_on_the_host(lib):
     # m not a multiple of bs
     b = scqr3._B(8, ctypes.c_void_p(8), 0.0)
     assert lib.scqr3_workspace_bytes(30, 5, ctypes.byref(b), None, ctypes.byref(out)) == -5
+    # CSR form (bs = 0): missing arrays, too few entries for a diagonal per row, n > 128
+    b = scqr3._B(0, None, 0.0, None, None, None, 0)
+    assert lib.scqr3_workspace_bytes(30, 5, ctypes.byref(b), None, ctypes.byref(out)) == -5
+    b = scqr3._B(0, None, 0.0, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), 29)
+    assert lib.scqr3_workspace_bytes(30, 5, ctypes.byref(b), None, ctypes.byref(out)) == -5
+    b = scqr3._B(0, None, 0.0, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), 3000)
+    assert lib.scqr3_workspace_bytes(1000, 200, ctypes.byref(b), None, ctypes.byref(out)) == \
+        scqr3.E_UNSUPPORTED
     # bad max_passes
     o = scqr3._Opts(2, 0, 0.0)
     assert lib.scqr3_workspace_bytes(30, 5, None, ctypes.byref(o), ctypes.byref(out)) == -12
