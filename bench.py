@@ -38,8 +38,8 @@ METRIC = "sCQR3 rows/s & % roofline at mÃ—n; mixed/batched vs FP64 at â€–Qáµ€Qâˆ
 FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
 # DRAM bytes per row of a fused solve+Gram launch of pass_kernel<64>, from the ncu capture
 # summarised in profiles/pass_kernel_fp64_1048576x64_full.md; valid only for that kernel source.
-PROFILED_KERNEL_SHA = "97a248845d02384d"
-PROFILED_BYTES_PER_ROW = 992.4
+PROFILED_KERNEL_SHA = "f9f2d688afe16ef4"
+PROFILED_BYTES_PER_ROW = 991.7
 
 
 def parse():
@@ -57,8 +57,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--legs", default="all", choices=["all", "main"],
-                    help="main: only the headline workload; all: also the other configurations")
+    ap.add_argument("--legs", default="all", choices=["all", "main", "csr"],
+                    help="main: only the headline workload; all: also the other configurations; "
+                         "csr: the headline plus the sparse-B leg alone")
+    ap.add_argument("--csr-grid", type=int, default=2048,
+                    help="side of the 2-D grid whose Laplacian is B in the sparse-B leg (m = side^2)")
     return ap.parse_args()
 
 
@@ -384,6 +387,8 @@ def run_gpu(args, rank, world, local_rank):
     legs = {}
     if args.legs == "all":
         legs = extra_legs(torch, dev, stream, args)
+    elif args.legs == "csr":
+        legs = {"oblique_csr": csr_leg(torch, dev, stream, args.csr_grid)}
 
     fl = flops_of(m, n, passes)
     out = {
@@ -439,6 +444,36 @@ def _orth(torch, Q, BQ=None):
     G = Q.T @ (Q if BQ is None else BQ)
     G -= torch.eye(n, dtype=torch.float64, device=Q.device)
     return torch.linalg.matrix_norm(G, 2).item()
+
+
+def csr_leg(torch, dev, stream, side):
+    """Oblique inner product with a sparse B in CSR form: the shifted 2-D
+    Laplacian on a side x side grid (kappa(B) = 1e3), X of side^2 x 128."""
+    from paper_1809_11085_gb300 import scqr3
+    from paper_1809_11085_gb300.testmat import laplacian_csr, testmat_torch
+
+    mm, nn = side * side, 128
+    X, _, _ = testmat_torch(mm, nn, 1e10, seed=1300, device=dev)
+    Bc = scqr3.CsrB.from_arrays(laplacian_csr((side, side), 1e3), device=dev)
+    Q = torch.empty_like(X)
+    ws = scqr3.Workspace(mm, nn, Bc, device=dev)
+    ms = _time(torch, stream, lambda: scqr3.factor(X, Bc, Q=Q, workspace=ws, read_info=False))
+    inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
+    scqr3.timing_begin()
+    scqr3.factor(X, Bc, Q=Q, workspace=ws, read_info=False)
+    recs, _ = scqr3.timing_end()
+    gram_ms = [r[2] for r in recs if r[0] == scqr3.KERNEL_GRAM]
+    gram_ms = gram_ms[:inf.passes]  # launches after the last needed Gram return at once
+    gram_flops = mm * nn * (nn + 1) + 2 * Bc.nnz * nn  # Q^T Y (upper triangle) + Y = B Q
+    Bt = torch.sparse_csr_tensor(Bc.row_ptr, Bc.col_idx.to(torch.int64), Bc.vals, size=(mm, mm))
+    return {
+        "workload": "FP64 sCQR3 in the B inner product, X %d x 128 (kappa 1e10), B sparse CSR: "
+                    "shifted 5-point Laplacian, %d x %d grid, kappa(B) 1e3" % (mm, side, side),
+        "ms": round(ms, 2), "rows_per_s": mm / (ms * 1e-3), "passes": inf.passes, "status": inf.status,
+        "orth_B": _orth(torch, Q, Bt @ Q), "nnz": Bc.nnz,
+        "tflops": (inf.passes * (mm * nn * (nn + 1) + 2 * Bc.nnz * nn + mm * nn * nn)) / (ms * 1e-3) / 1e12,
+        "csr_gram_ms": [round(t, 2) for t in gram_ms],
+        "csr_gram_frac_fp64_peak": [gram_flops / (t * 1e-3) / 1e12 / FP64_PEAK_DERIVED_TFLOPS for t in gram_ms]}
 
 
 def extra_legs(torch, dev, stream, args):
@@ -507,33 +542,7 @@ def extra_legs(torch, dev, stream, args):
     del X, B, Q, ws, BQ
     free()
 
-    # oblique inner product, sparse B in CSR form: shifted 2-D Laplacian on a
-    # 2048 x 2048 grid (kappa(B) = 1e3), same X as the block-diagonal leg
-    from paper_1809_11085_gb300.testmat import laplacian_csr
-
-    mm, nn = 4194304, 128
-    X, _, _ = testmat_torch(mm, nn, 1e10, seed=1300, device=dev)
-    Bc = scqr3.CsrB.from_arrays(laplacian_csr((2048, 2048), 1e3), device=dev)
-    Q = torch.empty_like(X)
-    ws = scqr3.Workspace(mm, nn, Bc, device=dev)
-    ms = _time(torch, stream, lambda: scqr3.factor(X, Bc, Q=Q, workspace=ws, read_info=False))
-    inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
-    scqr3.timing_begin()
-    scqr3.factor(X, Bc, Q=Q, workspace=ws, read_info=False)
-    recs, _ = scqr3.timing_end()
-    gram_ms = [r[2] for r in recs if r[0] == scqr3.KERNEL_GRAM]
-    gram_ms = gram_ms[:inf.passes]  # launches after the last needed Gram return at once
-    gram_flops = mm * nn * (nn + 1) + 2 * Bc.nnz * nn  # Q^T Y (upper triangle) + Y = B Q
-    Bt = torch.sparse_csr_tensor(Bc.row_ptr, Bc.col_idx.to(torch.int64), Bc.vals, size=(mm, mm))
-    legs["oblique_csr"] = {
-        "workload": "FP64 sCQR3 in the B inner product, X 4194304 x 128 (kappa 1e10), B sparse CSR: "
-                    "shifted 5-point Laplacian, 2048 x 2048 grid, kappa(B) 1e3",
-        "ms": round(ms, 2), "rows_per_s": mm / (ms * 1e-3), "passes": inf.passes, "status": inf.status,
-        "orth_B": _orth(torch, Q, Bt @ Q), "nnz": Bc.nnz,
-        "tflops": (inf.passes * (mm * nn * (nn + 1) + 2 * Bc.nnz * nn + mm * nn * nn)) / (ms * 1e-3) / 1e12,
-        "csr_gram_ms": [round(t, 2) for t in gram_ms],
-        "csr_gram_frac_fp64_peak": [gram_flops / (t * 1e-3) / 1e12 / FP64_PEAK_DERIVED_TFLOPS for t in gram_ms]}
-    del X, Bc, Bt, Q, ws
+    legs["oblique_csr"] = csr_leg(torch, dev, stream, args.csr_grid)
     free()
 
     # backward pass at the headline size
