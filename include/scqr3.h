@@ -169,6 +169,41 @@ int scqr3_factor(const double *X, int64_t m, int n, int64_t ldx,
                  const scqr3_opts *opts, scqr3_info *info, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Host-buffer form: the same factorization with X, Q, R and info in host
+ * memory. Not in the paper; it exists so that a caller whose data lives on
+ * the host pays for the transfers only once, overlapped with the work:
+ *  - X goes to the device in row chunks on a second stream. With B = NULL,
+ *    each chunk's share of the first Gram matrix X^T X starts as soon as the
+ *    chunk has arrived; each chunk writes its own partial sums, so the
+ *    first Gram matrix is summed in a different order than by scqr3_factor
+ *    when m > 262,144 (same result up to rounding; bit for bit below that).
+ *  - After each Cholesky the host reads the device's pass flags (about
+ *    100 bytes), so it knows which solve is the last one. That solve runs in
+ *    row chunks, and each chunk of Q is copied back while the next is solved.
+ *
+ *  X, Q   host, m x n row-major, leading dimensions ldx, ldq >= n. Q may be
+ *         X (ldq == ldx). Pinned memory (cudaHostAlloc, cudaHostRegister)
+ *         lets the copies overlap the work; pageable memory also works.
+ *  R      host, n x n, as for scqr3_factor.
+ *  Qdev   device scratch of m x n doubles (leading dimension n) holding the
+ *         iterates; it is the caller's, like the workspace.
+ *  workspace  device, scqr3_host_workspace_bytes() bytes, 256-byte aligned.
+ *  info   host scqr3_info, filled before the call returns.
+ *
+ * The call is synchronous: it returns when Q, R and info are written (or
+ * with a negative code before any work was queued, or SCQR3_E_CUDA). It
+ * uses one internal copy stream per device, created by the first call, and
+ * calls on the same device run one at a time. Failure: Q receives the last
+ * completed iterate (X itself if pass 1 failed). Neither the batched form
+ * nor Rpass is offered here. */
+int scqr3_host_workspace_bytes(int64_t m, int n, const scqr3_B *B,
+                               const scqr3_opts *opts, size_t *bytes);
+int scqr3_factor_host(const double *X, int64_t m, int n, int64_t ldx,
+                      const scqr3_B *B, double *Q, int64_t ldq, double *R,
+                      double *Qdev, void *workspace, size_t workspace_bytes,
+                      const scqr3_opts *opts, scqr3_info *info, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batched form (FP64, B = I): many independent, uneven factorizations, each
  * exactly as scqr3_factor would compute it (Alg. 3 with the breakdown rule
  * of Alg. 2), in one fixed launch sequence. Not in the paper, whose

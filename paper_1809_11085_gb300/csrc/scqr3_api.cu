@@ -172,7 +172,17 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
 // Grid of the pass kernel and the workspace carve-up. The partial-slot area is
 // sized for the larger of the FP64 and mixed kernels' needs, so one workspace
 // serves either precision.
-int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, Layout* L, int* grid, PassGeom* geo) {
+// Host-buffer entry point: X arrives and Q leaves in row chunks of this size.
+constexpr int kHostChunks = 8;
+constexpr int64_t kHostMinChunkRows = 262144;
+int64_t host_chunk_rows(int64_t m) {
+  int64_t r = (m + kHostChunks - 1) / kHostChunks;
+  r = (r + 255) / 256 * 256;
+  return r < kHostMinChunkRows ? kHostMinChunkRows : r;
+}
+
+int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, int host_chunks, Layout* L, int* grid,
+                PassGeom* geo) {
   const int np = padded_n(n);
   int grid_max = 0;
   if (device_geo(np, &grid_max, geo) != cudaSuccess) return SCQR3_E_CUDA;
@@ -213,6 +223,31 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, Layout* L, int* 
   off = align256(off + sizeof(double) * E);
   L->chol = off;  // Cholesky work buffers in global memory (n > 128)
   if (np == 256) off = align256(off + sizeof(double) * 2 * (size_t)E);
+  if (host_chunks && !B) {
+    // the first Gram runs per chunk, each chunk into slots of its own
+    int first = 0;
+    const int64_t cr = host_chunk_rows(m);
+    for (int64_t r0 = 0; r0 < m; r0 += cr) {
+      const int64_t rows = (m - r0) < cr ? (m - r0) : cr;
+      if (np == 256) {
+        first += grid64;
+      } else if (mixed) {
+        const int64_t pn = (rows + df_rows_per_panel(np) - 1) / df_rows_per_panel(np);
+        first += (int)(pn < griddf ? pn : griddf) * df_groups(np);
+      } else {
+        const int64_t pn = (rows + geo->pr - 1) / geo->pr;
+        first += (int)(pn < grid64 ? pn : grid64) * geo->groups;
+      }
+    }
+    if (first > slots_alloc) slots_alloc = first;
+  }
+  L->rdev = L->infodev = 0;
+  if (host_chunks) {
+    L->rdev = off;
+    off = align256(off + sizeof(double) * (size_t)n * n);
+    L->infodev = off;
+    off = align256(off + sizeof(scqr3_info));
+  }
   L->lt = off;
   if (B && B->bs > 0) {
     const int64_t nblk = m / B->bs;
@@ -283,18 +318,175 @@ extern "C" int scqr3_workspace_bytes(int64_t m, int n, const scqr3_B* B, const s
   Layout L;
   int grid;
   PassGeom geo;
-  const int r = make_layout(m, n, B, opts && opts->precision == SCQR3_PREC_MIXED, &L, &grid, &geo);
+  const int r = make_layout(m, n, B, opts && opts->precision == SCQR3_PREC_MIXED, 0, &L, &grid, &geo);
   if (r != SCQR3_OK) return r;
   *bytes = L.total;
   return SCQR3_OK;
 }
 
-extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, const scqr3_B* B,
-                            double* Q, int64_t ldq, double* R, double* Rpass, void* workspace,
-                            size_t workspace_bytes, const scqr3_opts* opts, scqr3_info* info,
-                            void* stream) {
+extern "C" int scqr3_host_workspace_bytes(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts,
+                                          size_t* bytes) {
+  if (!bytes) return -5;
   const int a = check_args(m, n, B, opts);
   if (a != SCQR3_OK) return a;
+  Layout L;
+  int grid;
+  PassGeom geo;
+  const int r = make_layout(m, n, B, opts && opts->precision == SCQR3_PREC_MIXED, 1, &L, &grid, &geo);
+  if (r != SCQR3_OK) return r;
+  *bytes = L.total;
+  return SCQR3_OK;
+}
+
+namespace {
+
+// One factorization's launch context: sizes, options, workspace carve-up.
+struct Call {
+  Params P;
+  Layout L;
+  int grid = 0;  // pass kernel CTAs (FP64 or mixed)
+  PassGeom geo;
+  bool mixed = false, csr = false;
+  const scqr3_B* B = nullptr;
+  cudaStream_t s = nullptr;
+  DevState* st = nullptr;
+  double *gram = nullptr, *rstack = nullptr, *racc = nullptr, *lt = nullptr, *partials = nullptr;
+  double *S = nullptr, *Ra = nullptr;  // n = 256: Cholesky work buffers
+  double *R = nullptr, *Rpass = nullptr;
+  scqr3_info* info = nullptr;
+};
+
+// Carves the workspace, fills Params, and queues the state reset and the
+// preparation of B. Arguments were checked by the caller.
+int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void* workspace,
+               size_t workspace_bytes, int host_chunks, double* R, double* Rpass, scqr3_info* info,
+               cudaStream_t s, Call* c) {
+  if (((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
+  c->mixed = opts && opts->precision == SCQR3_PREC_MIXED;
+  const int r = make_layout(m, n, B, c->mixed, host_chunks, &c->L, &c->grid, &c->geo);
+  if (r != SCQR3_OK) return r;
+  if (workspace_bytes < c->L.total) return SCQR3_E_WORKSPACE;
+  char* ws = (char*)workspace;
+  c->B = B;
+  c->s = s;
+  c->csr = B && B->bs == 0;
+  c->st = (DevState*)(ws + c->L.state);
+  c->gram = (double*)(ws + c->L.gram);
+  c->rstack = (double*)(ws + c->L.rstack);
+  c->racc = (double*)(ws + c->L.racc);
+  c->lt = (B && B->bs > 0) ? (double*)(ws + c->L.lt) : nullptr;
+  c->partials = (double*)(ws + c->L.partials);
+  c->S = (double*)(ws + c->L.chol);
+  c->Ra = c->S + pk_size(256);
+  c->R = R;
+  c->Rpass = Rpass;
+  c->info = info;
+
+  Params& P = c->P;
+  P.m = m;
+  P.n = n;
+  P.np = padded_n(n);
+  P.max_passes = (opts && opts->max_passes) ? opts->max_passes : 6;
+  P.bs = B ? B->bs : 0;
+  P.norm_x2 = opts ? opts->norm_x2 : 0.0;
+  P.normb_in = B ? B->norm2 : 0.0;
+  P.csr = c->csr ? 1 : 0;
+  set_options(&P, opts);
+
+  if (cudaMemsetAsync(c->st, 0, sizeof(DevState), s) != cudaSuccess) return SCQR3_E_CUDA;
+  if (cudaMemsetAsync(info, 0, sizeof(scqr3_info), s) != cudaSuccess) return SCQR3_E_CUDA;
+  if (B && B->bs > 0) {
+    tick(s, SCQR3_KERNEL_BFACTOR, 0);
+    launch_bfactor(s, B->bs, B->blocks, m / B->bs, c->lt, c->st, sm_count());
+  }
+  if (c->csr) {
+    tick(s, SCQR3_KERNEL_BFACTOR, 0);
+    launch_csr_check(sm_count() * 4, s, m, B, c->st);
+  }
+  return SCQR3_OK;
+}
+
+// The first Gram matrix (of X) over rows [r0, r1), into the partial slots
+// from `slot0` on; returns the number of slots written. The whole range
+// (0, m) gives exactly the launch of the fixed sequence.
+int first_gram(Call& c, const double* X, int64_t ldx, int64_t r0, int64_t r1, int slot0) {
+  Params Pc = c.P;
+  Pc.m = r1 - r0;
+  const double* src = X + r0 * ldx;
+  double* part = c.partials + (int64_t)slot0 * c.L.part_stride;
+  tick(c.s, SCQR3_KERNEL_GRAM, 0);
+  if (c.P.np == 256) {
+    launch_gram256(c.grid, c.s, src, ldx, Pc, -1, part, c.L.part_stride, c.st);
+    return c.grid;
+  }
+  if (c.csr) {  // the whole matrix only: rows reach across any split
+    launch_csr_gram(c.P.np, c.L.csr_grid, c.s, src, ldx, c.P, -1, c.B, part, c.L.part_stride, c.st);
+    return c.L.n_partials;
+  }
+  if (c.mixed) {
+    const int64_t pn = (Pc.m + df_rows_per_panel(c.P.np) - 1) / df_rows_per_panel(c.P.np);
+    const int g = (int)(pn < c.grid ? (pn < 1 ? 1 : pn) : c.grid);
+    launch_df_pass(c.P.np, g, c.s, src, ldx, nullptr, 0, Pc, -1, nullptr, part, c.L.part_stride, c.st);
+    return g * df_groups(c.P.np);
+  }
+  const int64_t pn = (Pc.m + c.geo.pr - 1) / c.geo.pr;
+  const int g = (int)(pn < c.grid ? (pn < 1 ? 1 : pn) : c.grid);
+  launch_pass(c.P.np, g, c.s, src, ldx, nullptr, 0, Pc, -1, nullptr, c.lt, part, c.L.part_stride, c.st);
+  return g * c.geo.groups;
+}
+
+void launch_any_chol(Call& c, int pass) {
+  tick(c.s, SCQR3_KERNEL_CHOL, pass);
+  if (c.P.np == 256)
+    launch_chol256(c.s, c.P, pass, c.gram, c.rstack, c.racc, c.R, c.Rpass, c.st, c.info, c.S, c.Ra);
+  else
+    launch_chol(c.P.np, c.s, c.P, pass, c.gram, c.rstack, c.racc, c.R, c.Rpass, c.st, c.info);
+}
+
+// Pass k's solve Q := Q R_k^{-1} over rows [r0, r1) (src -> dst), with the
+// fused Gram when the device asks for it (FP64 and mixed forms, whole range
+// only: a range is used only for a final solve, which has no Gram).
+void solve_rows(Call& c, int k, const double* src, int64_t lds, double* dst, int64_t ldd, int64_t r0,
+                int64_t r1) {
+  Params Pc = c.P;
+  Pc.m = r1 - r0;
+  src += r0 * lds;
+  dst += r0 * ldd;
+  const double* rk = c.rstack + (size_t)k * pk_size(c.P.np);
+  if (c.P.np == 256) {
+    tick(c.s, SCQR3_KERNEL_TRSM, k);
+    launch_trsm256(trsm256_grid(Pc.m), c.s, src, lds, dst, ldd, Pc, k, rk, c.st);
+    return;
+  }
+  tick(c.s, SCQR3_KERNEL_PASS, k);
+  if (c.mixed) {
+    const int64_t pn = (Pc.m + df_rows_per_panel(c.P.np) - 1) / df_rows_per_panel(c.P.np);
+    const int g = (int)(pn < c.grid ? (pn < 1 ? 1 : pn) : c.grid);
+    launch_df_pass(c.P.np, g, c.s, src, lds, dst, ldd, Pc, k, rk, c.partials, c.L.part_stride, c.st);
+  } else {
+    const int64_t pn = (Pc.m + c.geo.pr - 1) / c.geo.pr;
+    const int g = (int)(pn < c.grid ? (pn < 1 ? 1 : pn) : c.grid);
+    launch_pass(c.P.np, g, c.s, src, lds, dst, ldd, Pc, k, rk, c.lt, c.partials, c.L.part_stride, c.st);
+  }
+}
+
+// After pass k: the separate Gram kernels (n = 256, CSR B), the fixed-order
+// sum and the Cholesky of pass k + 1.
+void after_pass(Call& c, int k, const double* Q, int64_t ldq) {
+  if (c.P.np == 256) {
+    tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
+    launch_gram256(c.grid, c.s, Q, ldq, c.P, k, c.partials, c.L.part_stride, c.st);
+  } else if (c.csr) {
+    tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
+    launch_csr_gram(c.P.np, c.L.csr_grid, c.s, Q, ldq, c.P, k, c.B, c.partials, c.L.part_stride, c.st);
+  }
+  tick(c.s, SCQR3_KERNEL_REDUCE, k + 1);
+  launch_reduce(c.s, c.partials, c.L.n_partials, c.L.part_stride, c.gram, c.st, k);
+  launch_any_chol(c, k + 1);
+}
+
+int check_factor_pointers(const double* X, int64_t m, int n, int64_t ldx, const double* Q, int64_t ldq,
+                          const double* R, const void* workspace, const void* info) {
   if (!X) return -1;
   if (ldx < n) return -4;
   if (!Q) return -6;
@@ -307,118 +499,176 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   const size_t qbytes = sizeof(double) * (size_t)((m - 1) * ldq + n);
   if ((const void*)Q != (const void*)X && overlaps(X, xbytes, Q, qbytes)) return -6;
   if ((const void*)Q == (const void*)X && ldq != ldx) return -7;
-  if (((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
+  return SCQR3_OK;
+}
 
-  const bool mixed = opts && opts->precision == SCQR3_PREC_MIXED;
-  Layout L;
-  int grid;
-  PassGeom geo;
-  const int r = make_layout(m, n, B, mixed, &L, &grid, &geo);
-  if (r != SCQR3_OK) return r;
-  if (workspace_bytes < L.total) return SCQR3_E_WORKSPACE;
+}  // namespace
 
+extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, const scqr3_B* B,
+                            double* Q, int64_t ldq, double* R, double* Rpass, void* workspace,
+                            size_t workspace_bytes, const scqr3_opts* opts, scqr3_info* info,
+                            void* stream) {
+  int a = check_args(m, n, B, opts);
+  if (a != SCQR3_OK) return a;
+  a = check_factor_pointers(X, m, n, ldx, Q, ldq, R, workspace, info);
+  if (a != SCQR3_OK) return a;
+  Call c;
+  a = begin_call(m, n, B, opts, workspace, workspace_bytes, 0, R, Rpass, info, (cudaStream_t)stream, &c);
+  if (a != SCQR3_OK) return a;
+
+  // Pass 1 of Alg. 3: A = X^T X (or X^T B X), then the fixed sequence of
+  // passes whose launches the device skips once they are not needed.
+  const int slots = first_gram(c, X, ldx, 0, m, 0);
+  tick(c.s, SCQR3_KERNEL_REDUCE, 0);
+  launch_reduce(c.s, c.partials, slots, c.L.part_stride, c.gram, c.st, -1);
+  launch_any_chol(c, 0);
+  for (int k = 0; k < c.P.max_passes; ++k) {
+    solve_rows(c, k, k == 0 ? X : Q, k == 0 ? ldx : ldq, Q, ldq, 0, m);
+    if (k + 1 < c.P.max_passes) after_pass(c, k, Q, ldq);
+  }
+  if (c.mixed) {
+    tick(c.s, SCQR3_KERNEL_FINISH, -1);
+    launch_df_finish(sm_count() * 4, c.s, Q, ldq, m, n, c.P.max_passes, c.st);
+  }
+  tick(c.s, -1, -1);
+  if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
+  return SCQR3_OK;
+}
+
+namespace {
+// A copy stream, chunk events and a pinned staging slot for the pass flags,
+// per device; a call holds the device's lock while it runs.
+struct HostRes {
+  bool ready = false;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t entry = nullptr;
+  cudaEvent_t up[kHostChunks], down[kHostChunks];
+  DevState* flags = nullptr;  // pinned host memory
+  std::mutex mu;
+};
+HostRes g_host[kMaxDevices];
+
+int host_res(HostRes** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SCQR3_E_CUDA;
+  HostRes& h = g_host[dev];
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!h.ready) {
+    if (cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking) != cudaSuccess) return SCQR3_E_CUDA;
+    if (cudaEventCreateWithFlags(&h.entry, cudaEventDisableTiming) != cudaSuccess) return SCQR3_E_CUDA;
+    for (int i = 0; i < kHostChunks; ++i) {
+      if (cudaEventCreateWithFlags(&h.up[i], cudaEventDisableTiming) != cudaSuccess) return SCQR3_E_CUDA;
+      if (cudaEventCreateWithFlags(&h.down[i], cudaEventDisableTiming) != cudaSuccess) return SCQR3_E_CUDA;
+    }
+    if (cudaMallocHost((void**)&h.flags, sizeof(DevState)) != cudaSuccess) return SCQR3_E_CUDA;
+    h.ready = true;
+  }
+  *out = &h;
+  return SCQR3_OK;
+}
+}  // namespace
+
+extern "C" int scqr3_factor_host(const double* X, int64_t m, int n, int64_t ldx, const scqr3_B* B,
+                                 double* Q, int64_t ldq, double* R, double* Qdev, void* workspace,
+                                 size_t workspace_bytes, const scqr3_opts* opts, scqr3_info* info,
+                                 void* stream) {
+  int a = check_args(m, n, B, opts);
+  if (a != SCQR3_OK) return a;
+  a = check_factor_pointers(X, m, n, ldx, Q, ldq, R, workspace, info);
+  if (a != SCQR3_OK) return a;
+  if (!Qdev) return -9;
+  HostRes* h = nullptr;
+  a = host_res(&h);
+  if (a != SCQR3_OK) return a;
+  std::lock_guard<std::mutex> lk(h->mu);
   cudaStream_t s = (cudaStream_t)stream;
-  char* ws = (char*)workspace;
-  DevState* st = (DevState*)(ws + L.state);
-  double* gram = (double*)(ws + L.gram);
-  double* rstack = (double*)(ws + L.rstack);
-  double* racc = (double*)(ws + L.racc);
-  const bool csr = B && B->bs == 0;
-  double* lt = (B && B->bs > 0) ? (double*)(ws + L.lt) : nullptr;
-  double* partials = (double*)(ws + L.partials);
-
-  Params P;
-  P.m = m;
-  P.n = n;
-  P.np = padded_n(n);
-  P.max_passes = (opts && opts->max_passes) ? opts->max_passes : 6;
-  P.bs = B ? B->bs : 0;
-  P.norm_x2 = opts ? opts->norm_x2 : 0.0;
-  P.normb_in = B ? B->norm2 : 0.0;
-  P.csr = csr ? 1 : 0;
-  set_options(&P, opts);
-
-  if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return SCQR3_E_CUDA;
-  if (cudaMemsetAsync(info, 0, sizeof(scqr3_info), s) != cudaSuccess) return SCQR3_E_CUDA;
-  if (B && B->bs > 0) {
-    tick(s, SCQR3_KERNEL_BFACTOR, 0);
-    launch_bfactor(s, B->bs, B->blocks, m / B->bs, lt, st, sm_count());
+  Call c;
+  {
+    // R and info live in the workspace until the end of the call
+    Layout L;
+    int grid;
+    PassGeom geo;
+    a = make_layout(m, n, B, opts && opts->precision == SCQR3_PREC_MIXED, 1, &L, &grid, &geo);
+    if (a != SCQR3_OK) return a;
+    if (workspace_bytes < L.total || ((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
+    char* ws = (char*)workspace;
+    a = begin_call(m, n, B, opts, workspace, workspace_bytes, 1, (double*)(ws + L.rdev), nullptr,
+                   (scqr3_info*)(ws + L.infodev), s, &c);
+    if (a != SCQR3_OK) return a;
   }
-  if (csr) {
-    tick(s, SCQR3_KERNEL_BFACTOR, 0);
-    launch_csr_check(sm_count() * 4, s, m, B, st);
-  }
+  const size_t row_bytes = sizeof(double) * (size_t)n;
+  const int64_t cr = host_chunk_rows(m);
+  const int nchunks = (int)((m + cr - 1) / cr);
 
-  if (P.np == 256) {
-    // Same sequence with the substitution and the Gram in separate kernels.
-    const int E256 = pk_size(256);
-    double* S = (double*)(ws + L.chol);
-    double* Ra = S + E256;
-    const int tg = trsm256_grid(m);
-    tick(s, SCQR3_KERNEL_GRAM, 0);
-    launch_gram256(grid, s, X, ldx, P, -1, partials, L.part_stride, st);
-    tick(s, SCQR3_KERNEL_REDUCE, 0);
-    launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, -1);
-    tick(s, SCQR3_KERNEL_CHOL, 0);
-    launch_chol256(s, P, 0, gram, rstack, racc, R, Rpass, st, info, S, Ra);
-    for (int k = 0; k < P.max_passes; ++k) {
-      const double* src = (k == 0) ? X : Q;
-      const int64_t lds = (k == 0) ? ldx : ldq;
-      tick(s, SCQR3_KERNEL_TRSM, k);
-      launch_trsm256(tg, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E256, st);
-      if (k + 1 < P.max_passes) {
-        tick(s, SCQR3_KERNEL_GRAM, k + 1);
-        launch_gram256(grid, s, Q, ldq, P, k, partials, L.part_stride, st);
-        tick(s, SCQR3_KERNEL_REDUCE, k + 1);
-        launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, k);
-        tick(s, SCQR3_KERNEL_CHOL, k + 1);
-        launch_chol256(s, P, k + 1, gram, rstack, racc, R, Rpass, st, info, S, Ra);
-      }
+  // X -> Qdev in chunks on the copy stream (after the caller's earlier work on
+  // `stream`); with B = I each chunk's share of the first Gram starts as soon
+  // as it has arrived.
+  if (cudaEventRecord(h->entry, s) != cudaSuccess) return SCQR3_E_CUDA;
+  if (cudaStreamWaitEvent(h->copy, h->entry, 0) != cudaSuccess) return SCQR3_E_CUDA;
+  int slots = 0;
+  for (int ci = 0; ci < nchunks; ++ci) {
+    const int64_t r0 = ci * cr, r1 = (r0 + cr) < m ? (r0 + cr) : m;
+    if (cudaMemcpy2DAsync(Qdev + r0 * n, row_bytes, X + r0 * ldx, sizeof(double) * ldx, row_bytes,
+                          (size_t)(r1 - r0), cudaMemcpyHostToDevice, h->copy) != cudaSuccess)
+      return SCQR3_E_CUDA;
+    if (cudaEventRecord(h->up[ci], h->copy) != cudaSuccess) return SCQR3_E_CUDA;
+    if (!B) {
+      if (cudaStreamWaitEvent(s, h->up[ci], 0) != cudaSuccess) return SCQR3_E_CUDA;
+      slots += first_gram(c, Qdev, n, r0, r1, slots);
     }
-    tick(s, -1, -1);
-    if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
-    return SCQR3_OK;
   }
-
-  // Pass 1 of Alg. 3: A = X^T X (or X^T B X).
-  tick(s, SCQR3_KERNEL_GRAM, 0);
-  if (csr)
-    launch_csr_gram(P.np, L.csr_grid, s, X, ldx, P, -1, B, partials, L.part_stride, st);
-  else if (mixed)
-    launch_df_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, partials, L.part_stride, st);
-  else
-    launch_pass(P.np, grid, s, X, ldx, nullptr, 0, P, -1, nullptr, lt, partials, L.part_stride, st);
+  if (B) {
+    if (cudaStreamWaitEvent(s, h->up[nchunks - 1], 0) != cudaSuccess) return SCQR3_E_CUDA;
+    slots = first_gram(c, Qdev, n, 0, m, 0);
+  }
   tick(s, SCQR3_KERNEL_REDUCE, 0);
-  launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, -1);
-  tick(s, SCQR3_KERNEL_CHOL, 0);
-  launch_chol(P.np, s, P, 0, gram, rstack, racc, R, Rpass, st, info);
-  const int E = pk_size(P.np);
-  for (int k = 0; k < P.max_passes; ++k) {
-    const double* src = (k == 0) ? X : Q;
-    const int64_t lds = (k == 0) ? ldx : ldq;
-    tick(s, SCQR3_KERNEL_PASS, k);
-    if (mixed)
-      launch_df_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, partials,
-                     L.part_stride, st);
-    else
-      launch_pass(P.np, grid, s, src, lds, Q, ldq, P, k, rstack + (size_t)k * E, lt, partials,
-                  L.part_stride, st);
-    if (k + 1 < P.max_passes) {
-      if (csr) {
-        tick(s, SCQR3_KERNEL_GRAM, k + 1);
-        launch_csr_gram(P.np, L.csr_grid, s, Q, ldq, P, k, B, partials, L.part_stride, st);
-      }
-      tick(s, SCQR3_KERNEL_REDUCE, k + 1);
-      launch_reduce(s, partials, L.n_partials, L.part_stride, gram, st, k);
-      tick(s, SCQR3_KERNEL_CHOL, k + 1);
-      launch_chol(P.np, s, P, k + 1, gram, rstack, racc, R, Rpass, st, info);
+  launch_reduce(s, c.partials, slots, c.L.part_stride, c.gram, c.st, -1);
+  launch_any_chol(c, 0);
+
+  // Passes, driven from the host: after each Cholesky the device's flags say
+  // whether pass k solves and whether a Gram follows. The last solve runs in
+  // row chunks whose copies back to Q overlap the next chunk's solve.
+  bool copied = false;
+  for (int k = 0; k < c.P.max_passes; ++k) {
+    if (cudaMemcpyAsync(h->flags, c.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return SCQR3_E_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SCQR3_E_CUDA;
+    if (!h->flags->run_trsm[k]) break;
+    if (h->flags->gram_after[k]) {
+      solve_rows(c, k, Qdev, n, Qdev, n, 0, m);
+      if (k + 1 < c.P.max_passes) after_pass(c, k, Qdev, n);
+      continue;
     }
+    for (int ci = 0; ci < nchunks; ++ci) {
+      const int64_t r0 = ci * cr, r1 = (r0 + cr) < m ? (r0 + cr) : m;
+      solve_rows(c, k, Qdev, n, Qdev, n, r0, r1);
+      if (cudaEventRecord(h->down[ci], s) != cudaSuccess) return SCQR3_E_CUDA;
+      if (cudaStreamWaitEvent(h->copy, h->down[ci], 0) != cudaSuccess) return SCQR3_E_CUDA;
+      if (cudaMemcpy2DAsync(Q + r0 * ldq, sizeof(double) * ldq, Qdev + r0 * n, row_bytes, row_bytes,
+                            (size_t)(r1 - r0), cudaMemcpyDeviceToHost, h->copy) != cudaSuccess)
+        return SCQR3_E_CUDA;
+    }
+    copied = true;
+    break;
   }
-  if (mixed) {
-    tick(s, SCQR3_KERNEL_FINISH, -1);
-    launch_df_finish(sm_count() * 4, s, Q, ldq, m, n, P.max_passes, st);
+  if (!copied) {  // stopped by Alg. 2's test or a failure: Q as the device left it
+    if (c.mixed) {
+      tick(s, SCQR3_KERNEL_FINISH, -1);
+      launch_df_finish(sm_count() * 4, s, Qdev, n, m, n, c.P.max_passes, c.st);
+    }
+    if (cudaEventRecord(h->down[0], s) != cudaSuccess) return SCQR3_E_CUDA;
+    if (cudaStreamWaitEvent(h->copy, h->down[0], 0) != cudaSuccess) return SCQR3_E_CUDA;
+    if (cudaMemcpy2DAsync(Q, sizeof(double) * ldq, Qdev, row_bytes, row_bytes, (size_t)m,
+                          cudaMemcpyDeviceToHost, h->copy) != cudaSuccess)
+      return SCQR3_E_CUDA;
   }
   tick(s, -1, -1);
+  if (cudaMemcpyAsync(R, c.R, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return SCQR3_E_CUDA;
+  if (cudaMemcpyAsync(info, c.info, sizeof(scqr3_info), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return SCQR3_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SCQR3_E_CUDA;
+  if (cudaStreamSynchronize(h->copy) != cudaSuccess) return SCQR3_E_CUDA;
   if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
   return SCQR3_OK;
 }

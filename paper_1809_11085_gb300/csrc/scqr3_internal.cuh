@@ -53,6 +53,7 @@ void set_options(Params* P, const scqr3_opts* opts);
 // Workspace carve-up (byte offsets from the base, each 256-aligned).
 struct Layout {
   size_t state, gram, rstack, racc, chol, lt, partials, total;
+  size_t rdev, infodev;  // host-buffer entry point: R and info on the device
   int n_partials;    // partial Gram slots used by this call (grid CTAs x groups)
   int csr_grid;      // CTAs of csr_gram_kernel (CSR form only)
   int part_stride;   // doubles per partial slot: pk_size(np) + 1 (||.||_F^2)

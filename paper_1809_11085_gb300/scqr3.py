@@ -133,6 +133,12 @@ def lib():
         L.scqr3_factor.argtypes = [p, i64, i32, i64, ctypes.POINTER(_B), p, i64, p, p, p, sz,
                                    ctypes.POINTER(_Opts), p, p]
         L.scqr3_factor.restype = i32
+        L.scqr3_host_workspace_bytes.argtypes = [i64, i32, ctypes.POINTER(_B), ctypes.POINTER(_Opts),
+                                                 ctypes.POINTER(sz)]
+        L.scqr3_host_workspace_bytes.restype = i32
+        L.scqr3_factor_host.argtypes = [p, i64, i32, i64, ctypes.POINTER(_B), p, i64, p, p, p, sz,
+                                        ctypes.POINTER(_Opts), p, p]
+        L.scqr3_factor_host.restype = i32
         L.scqr3_backward_workspace_bytes.argtypes = [i64, i32, ctypes.POINTER(sz)]
         L.scqr3_backward_workspace_bytes.restype = i32
         L.scqr3_backward.argtypes = [p, i64, i32, i64, p, i32, p, i64, p, p, i64, p, sz, p]
@@ -249,6 +255,68 @@ def factor(X, B=None, *, max_passes: int = 0, norm_x2: float = 0.0, normb: float
         return Q, R, workspace.info
     info = Info.from_bytes(workspace.info.cpu().numpy().tobytes())
     return Q, R, info
+
+
+class HostWorkspace:
+    """Device scratch of scqr3_factor_host for repeated calls of one shape:
+    the workspace and the m x n device buffer of the iterates."""
+
+    def __init__(self, m, n, B=None, max_passes=0, precision=PREC_FP64, device=None):
+        import torch
+
+        _, bp = _b_struct(B, 0.0)
+        _, op = _opts(max_passes, 0.0, precision)
+        out = ctypes.c_size_t(0)
+        r = lib().scqr3_host_workspace_bytes(int(m), int(n), bp, op, ctypes.byref(out))
+        if r != OK:
+            raise ScqrError(r, "scqr3_host_workspace_bytes")
+        self.bytes = out.value
+        dev = device or "cuda"
+        self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=dev)
+        self.ptr = (self.buf.data_ptr() + 255) & ~255
+        self.Qdev = torch.empty((m, n), dtype=torch.float64, device=dev)
+
+
+def factor_host(X, B=None, *, Q=None, R=None, workspace: HostWorkspace | None = None, stream=None,
+                max_passes: int = 0, norm_x2: float = 0.0, normb: float = 0.0,
+                precision: int = PREC_FP64, shift_scale: float = 0.0, algorithm: int = ALG_SCQR3,
+                tol: float = 0.0):
+    """scqr3_factor_host: X, Q, R host (CPU float64 tensors, pinned for overlap).
+
+    Synchronous; returns (Q, R, info). Q may be X for an in-place factorization.
+    """
+    import torch
+
+    def host_mat(t, name, shape=None):
+        if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.dtype == torch.float64
+                and t.dim() == 2 and t.stride(1) == 1):
+            raise TypeError("%s must be a row-major 2-D float64 CPU tensor" % name)
+        if shape is not None and tuple(t.shape) != shape:
+            raise ValueError("%s must have shape %s" % (name, shape))
+
+    host_mat(X, "X")
+    m, n = X.shape
+    if Q is None:
+        Q = torch.empty((m, n), dtype=torch.float64, pin_memory=X.is_pinned())
+    host_mat(Q, "Q", (m, n))
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64)
+    host_mat(R, "R", (n, n))
+    if not R.is_contiguous():
+        raise TypeError("R must be contiguous")
+    if workspace is None:
+        workspace = HostWorkspace(m, n, B, max_passes, precision)
+    b, bp = _b_struct(B, normb)
+    o, op = _opts(max_passes, norm_x2, precision, shift_scale, algorithm, tol)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    buf = (ctypes.c_char * INFO_BYTES)()
+    r = lib().scqr3_factor_host(X.data_ptr(), m, n, X.stride(0), bp, Q.data_ptr(), Q.stride(0),
+                                R.data_ptr(), workspace.Qdev.data_ptr(), workspace.ptr, workspace.bytes, op,
+                                ctypes.addressof(buf), ctypes.c_void_p(stream))
+    if r != OK:
+        raise ScqrError(r, "scqr3_factor_host")
+    return Q, R, Info.from_bytes(bytes(buf))
 
 
 def timing_begin(capacity: int = 4096) -> None:
