@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--m", type=int, default=16777216)
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--kappa", type=float, default=1e10)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="arithmetic of the timed factorization (mixed: FP32 pairs + FP64)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "tc"],
+                    help="arithmetic of the timed factorization (mixed: FP32 pairs + FP64; tc: FP64 "
+                         "substitution with the Gram matrices on the BF16 tensor cores, exact digit split)")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -99,17 +100,19 @@ def flops_of(m, n, passes):
     return passes * m * (n * (n + 1) + n * n)
 
 
-def pass_kernel_flops(m, n, kernel, pass_idx, passes):
-    """Flops done by one pass_kernel launch (0 when the device skipped it)."""
+def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True):
+    """FP64 flops done by one pass_kernel launch (0 when the device skipped it).
+    gram_in_pass=False: the Gram matrices run on the tensor cores, the pass
+    kernel only solves."""
     from paper_1809_11085_gb300 import scqr3
 
     if kernel == scqr3.KERNEL_GRAM:
-        return m * n * (n + 1)
+        return m * n * (n + 1) if gram_in_pass else 0
     if kernel == scqr3.KERNEL_PASS:
         if pass_idx >= passes:
             return 0
         f = m * n * n
-        if pass_idx < passes - 1:
+        if pass_idx < passes - 1 and gram_in_pass:
             f += m * n * (n + 1)
         return f
     return 0
@@ -266,7 +269,7 @@ def run_gpu(args, rank, world, local_rank):
     ws = scqr3.Workspace(m, n, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    prec = scqr3.PREC_MIXED if args.precision == "mixed" else scqr3.PREC_FP64
+    prec = {"fp64": scqr3.PREC_FP64, "mixed": scqr3.PREC_MIXED, "tc": scqr3.PREC_TC}[args.precision]
     for _ in range(args.warmup):
         scqr3.factor(X, Q=Q, workspace=ws, read_info=False, precision=prec)
     torch.cuda.synchronize(dev)
@@ -309,7 +312,7 @@ def run_gpu(args, rank, world, local_rank):
     for kernel, p, t in recs:
         name = scqr3.KERNEL_NAMES.get(kernel, str(kernel))
         share[name] = share.get(name, 0.0) + t
-        f = pass_kernel_flops(m, n, kernel, p, passes)
+        f = pass_kernel_flops(m, n, kernel, p, passes, gram_in_pass=prec != scqr3.PREC_TC)
         if f > 0:
             kflops += f
             kms += t

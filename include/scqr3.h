@@ -49,6 +49,7 @@ extern "C" {
                                      CholeskyQR passes followed the last
                                      shifted one; Q, R are still X = QR   */
 #define SCQR3_E_CUDA (-103)       /* a CUDA launch failed                  */
+#define SCQR3_E_TIMEOUT (-102) /* a wait inside a kernel passed its iteration limit */
 #define SCQR3_E_WORKSPACE (-104)  /* workspace too small or misaligned     */
 #define SCQR3_E_B_NOT_SPD (-105)  /* a diagonal block of B is not SPD      */
 #define SCQR3_E_UNSUPPORTED (-106)/* size not supported by this build      */
@@ -69,6 +70,15 @@ extern "C" {
  * Inputs must lie within the float exponent range. Not in the paper (which
  * uses FP64 throughout, Sec. 6); expected orthogonality ~1e-14. */
 #define SCQR3_PREC_MIXED 1
+/* FP64 substitution; the Gram matrices on the BF16 tensor cores (tcgen05)
+ * through an exact fixed-point split: each column is scaled by a power of two
+ * above its largest entry and cut into eight 7-bit digits, every digit
+ * product is exact, sums of 256 rows are exact in the FP32 accumulator, and
+ * the digit-pair sums are combined in FP64. The Gram error is below about
+ * m 2^-55 sigma_j sigma_k, within the norm-wise bound that the shift of
+ * Eq. (finds2) covers, so results match the FP64 form to rounding. Not in
+ * the paper. n <= 64 and B = NULL. */
+#define SCQR3_PREC_TC 2
 
 /* Oblique inner product (x, y)_B = x^T B y of Sec. 5, for SPD B given
  * either block-diagonal, B = blockdiag(B_1, ..., B_{m/bs}) (bs > 0), or as a

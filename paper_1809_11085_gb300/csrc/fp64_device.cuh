@@ -110,7 +110,7 @@ __device__ __forceinline__ void pass_segment(const double* src, int64_t lds, dou
   if (pass >= 0) {
     if (!st->run_trsm[pass]) return;
     do_trsm = true;
-    do_gram = st->gram_after[pass] != 0 && !P.csr;  // CSR B: Gram by csr_gram_kernel
+    do_gram = st->gram_after[pass] != 0 && !P.solve_only;  // else the Gram has its own kernel
   }
 
   if (do_trsm) {

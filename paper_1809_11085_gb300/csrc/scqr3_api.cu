@@ -47,6 +47,10 @@ int csr_groups(int np);
 void launch_csr_check(int grid, cudaStream_t s, int64_t m, const scqr3_B* B, DevState* st);
 void launch_csr_gram(int np, int grid, cudaStream_t s, const double* src, int64_t lds, const Params& P,
                      int pass, const scqr3_B* B, double* partials, int part_stride, const DevState* st);
+cudaError_t tc_setup();
+int tc_groups(int64_t m);
+void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
+                    unsigned long long* colmax, double* partials, int part_stride, DevState* st);
 
 namespace {
 
@@ -105,6 +109,8 @@ cudaError_t device_geo(int np, int* grid_max, PassGeom* geo) {
     }
     e = csr_setup(d.csr_ctas_per_sm);
     if (e != cudaSuccess) return e;
+    e = tc_setup();
+    if (e != cudaSuccess) return e;
     for (int k = 0; k < 4; ++k)
       if (d.csr_ctas_per_sm[k] < 1) return cudaErrorInvalidConfiguration;
     d.ready = true;
@@ -158,7 +164,10 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
   if (B && B->bs == 0 && n > 128) return SCQR3_E_UNSUPPORTED;
   if (opts && opts->max_passes != 0 && (opts->max_passes < 3 || opts->max_passes > SCQR3_MAX_PASSES))
     return -12;
-  if (opts && opts->precision != SCQR3_PREC_FP64 && opts->precision != SCQR3_PREC_MIXED) return -12;
+  if (opts && opts->precision != SCQR3_PREC_FP64 && opts->precision != SCQR3_PREC_MIXED &&
+      opts->precision != SCQR3_PREC_TC)
+    return -12;
+  if (opts && opts->precision == SCQR3_PREC_TC && (B || n > 64)) return SCQR3_E_UNSUPPORTED;
   if (opts && opts->precision == SCQR3_PREC_MIXED && B) return -5;  // mixed form: B = I only
   if (opts && opts->algorithm != 0 && opts->algorithm != SCQR3_ALG_SCQR3 &&
       opts->algorithm != SCQR3_ALG_ADAPTIVE)
@@ -170,8 +179,8 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
 }
 
 // Grid of the pass kernel and the workspace carve-up. The partial-slot area is
-// sized for the larger of the FP64 and mixed kernels' needs, so one workspace
-// serves either precision.
+// sized for the largest of the FP64, mixed and tensor-core kernels' needs, so
+// one workspace serves every precision.
 // Host-buffer entry point: X arrives and Q leaves in row chunks of this size.
 constexpr int kHostChunks = 8;
 constexpr int64_t kHostMinChunkRows = 262144;
@@ -181,9 +190,10 @@ int64_t host_chunk_rows(int64_t m) {
   return r < kHostMinChunkRows ? kHostMinChunkRows : r;
 }
 
-int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, int host_chunks, Layout* L, int* grid,
-                PassGeom* geo) {
-  const int np = padded_n(n);
+int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunks, Layout* L, int* grid,
+                    PassGeom* geo) {
+  const bool mixed = prec == SCQR3_PREC_MIXED, tcg = prec == SCQR3_PREC_TC;
+  const int np = tcg ? 64 : padded_n(n);  // the tensor-core Gram works on 64 columns
   int grid_max = 0;
   if (device_geo(np, &grid_max, geo) != cudaSuccess) return SCQR3_E_CUDA;
   const int64_t npanels = (m + geo->pr - 1) / geo->pr;
@@ -212,6 +222,15 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, int host_chunks,
     L->n_partials = L->csr_grid * csr_groups(np);
     if (L->n_partials > slots_alloc) slots_alloc = L->n_partials;
   }
+  const int sms = sm_count();
+  // the tensor-core Gram's slots and column scales are always reserved, so
+  // one workspace serves every precision of a shape
+  {
+    const int g = tc_groups(m);
+    L->tc_grid = g < sms ? (g < 1 ? 1 : g) : sms;
+    if (L->tc_grid > slots_alloc) slots_alloc = L->tc_grid;
+    if (tcg) L->n_partials = L->tc_grid;
+  }
   size_t off = 0;
   L->state = off;
   off = align256(off + sizeof(DevState));
@@ -224,21 +243,24 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, int host_chunks,
   L->chol = off;  // Cholesky work buffers in global memory (n > 128)
   if (np == 256) off = align256(off + sizeof(double) * 2 * (size_t)E);
   if (host_chunks && !B) {
-    // the first Gram runs per chunk, each chunk into slots of its own
-    int first = 0;
+    // the first Gram runs per chunk, each chunk into slots of its own (sized
+    // for every precision, like the rest of the workspace)
+    int f64 = 0, fdf = 0, ftc = 0;
     const int64_t cr = host_chunk_rows(m);
     for (int64_t r0 = 0; r0 < m; r0 += cr) {
       const int64_t rows = (m - r0) < cr ? (m - r0) : cr;
+      const int g = tc_groups(rows);
+      ftc += g < sms ? (g < 1 ? 1 : g) : sms;
       if (np == 256) {
-        first += grid64;
-      } else if (mixed) {
-        const int64_t pn = (rows + df_rows_per_panel(np) - 1) / df_rows_per_panel(np);
-        first += (int)(pn < griddf ? pn : griddf) * df_groups(np);
+        f64 += grid64;
       } else {
+        const int64_t pdf = (rows + df_rows_per_panel(np) - 1) / df_rows_per_panel(np);
+        fdf += (int)(pdf < griddf ? pdf : griddf) * df_groups(np);
         const int64_t pn = (rows + geo->pr - 1) / geo->pr;
-        first += (int)(pn < grid64 ? pn : grid64) * geo->groups;
+        f64 += (int)(pn < grid64 ? pn : grid64) * geo->groups;
       }
     }
+    const int first = f64 > fdf ? (f64 > ftc ? f64 : ftc) : (fdf > ftc ? fdf : ftc);
     if (first > slots_alloc) slots_alloc = first;
   }
   L->rdev = L->infodev = 0;
@@ -248,6 +270,8 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, int host_chunks,
     L->infodev = off;
     off = align256(off + sizeof(scqr3_info));
   }
+  L->colmax = off;
+  off = align256(off + sizeof(unsigned long long) * 64);
   L->lt = off;
   if (B && B->bs > 0) {
     const int64_t nblk = m / B->bs;
@@ -256,6 +280,23 @@ int make_layout(int64_t m, int n, const scqr3_B* B, bool mixed, int host_chunks,
   L->partials = off;
   off = align256(off + sizeof(double) * (size_t)slots_alloc * L->part_stride);
   L->total = off;
+  return SCQR3_OK;
+}
+
+// The layout for `prec`, with a total size that fits every precision the
+// shape supports, so that one workspace serves them all.
+int make_layout(int64_t m, int n, const scqr3_B* B, int prec, int host_chunks, Layout* L, int* grid,
+                PassGeom* geo) {
+  const int r = make_layout_one(m, n, B, prec, host_chunks, L, grid, geo);
+  if (r != SCQR3_OK) return r;
+  for (int p : {SCQR3_PREC_FP64, SCQR3_PREC_TC}) {
+    if (p == prec || (p == SCQR3_PREC_TC && (B || n > 64))) continue;
+    Layout L2;
+    int g2;
+    PassGeom geo2;
+    if (make_layout_one(m, n, B, p, host_chunks, &L2, &g2, &geo2) == SCQR3_OK && L2.total > L->total)
+      L->total = L2.total;
+  }
   return SCQR3_OK;
 }
 
@@ -318,7 +359,7 @@ extern "C" int scqr3_workspace_bytes(int64_t m, int n, const scqr3_B* B, const s
   Layout L;
   int grid;
   PassGeom geo;
-  const int r = make_layout(m, n, B, opts && opts->precision == SCQR3_PREC_MIXED, 0, &L, &grid, &geo);
+  const int r = make_layout(m, n, B, opts ? opts->precision : SCQR3_PREC_FP64, 0, &L, &grid, &geo);
   if (r != SCQR3_OK) return r;
   *bytes = L.total;
   return SCQR3_OK;
@@ -332,7 +373,7 @@ extern "C" int scqr3_host_workspace_bytes(int64_t m, int n, const scqr3_B* B, co
   Layout L;
   int grid;
   PassGeom geo;
-  const int r = make_layout(m, n, B, opts && opts->precision == SCQR3_PREC_MIXED, 1, &L, &grid, &geo);
+  const int r = make_layout(m, n, B, opts ? opts->precision : SCQR3_PREC_FP64, 1, &L, &grid, &geo);
   if (r != SCQR3_OK) return r;
   *bytes = L.total;
   return SCQR3_OK;
@@ -346,12 +387,13 @@ struct Call {
   Layout L;
   int grid = 0;  // pass kernel CTAs (FP64 or mixed)
   PassGeom geo;
-  bool mixed = false, csr = false;
+  bool mixed = false, csr = false, tc = false;
   const scqr3_B* B = nullptr;
   cudaStream_t s = nullptr;
   DevState* st = nullptr;
   double *gram = nullptr, *rstack = nullptr, *racc = nullptr, *lt = nullptr, *partials = nullptr;
   double *S = nullptr, *Ra = nullptr;  // n = 256: Cholesky work buffers
+  unsigned long long* colmax = nullptr;  // tensor-core Gram: column scales
   double *R = nullptr, *Rpass = nullptr;
   scqr3_info* info = nullptr;
 };
@@ -363,7 +405,9 @@ int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void*
                cudaStream_t s, Call* c) {
   if (((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
   c->mixed = opts && opts->precision == SCQR3_PREC_MIXED;
-  const int r = make_layout(m, n, B, c->mixed, host_chunks, &c->L, &c->grid, &c->geo);
+  c->tc = opts && opts->precision == SCQR3_PREC_TC;
+  const int r = make_layout(m, n, B, opts ? opts->precision : SCQR3_PREC_FP64, host_chunks, &c->L, &c->grid,
+                            &c->geo);
   if (r != SCQR3_OK) return r;
   if (workspace_bytes < c->L.total) return SCQR3_E_WORKSPACE;
   char* ws = (char*)workspace;
@@ -377,6 +421,7 @@ int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void*
   c->lt = (B && B->bs > 0) ? (double*)(ws + c->L.lt) : nullptr;
   c->partials = (double*)(ws + c->L.partials);
   c->S = (double*)(ws + c->L.chol);
+  c->colmax = (unsigned long long*)(ws + c->L.colmax);
   c->Ra = c->S + pk_size(256);
   c->R = R;
   c->Rpass = Rpass;
@@ -385,12 +430,14 @@ int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void*
   Params& P = c->P;
   P.m = m;
   P.n = n;
-  P.np = padded_n(n);
+  P.np = c->tc ? 64 : padded_n(n);
   P.max_passes = (opts && opts->max_passes) ? opts->max_passes : 6;
   P.bs = B ? B->bs : 0;
   P.norm_x2 = opts ? opts->norm_x2 : 0.0;
   P.normb_in = B ? B->norm2 : 0.0;
   P.csr = c->csr ? 1 : 0;
+  P.tc = c->tc ? 1 : 0;
+  P.solve_only = (c->csr || c->tc) ? 1 : 0;
   set_options(&P, opts);
 
   if (cudaMemsetAsync(c->st, 0, sizeof(DevState), s) != cudaSuccess) return SCQR3_E_CUDA;
@@ -418,6 +465,12 @@ int first_gram(Call& c, const double* X, int64_t ldx, int64_t r0, int64_t r1, in
   if (c.P.np == 256) {
     launch_gram256(c.grid, c.s, src, ldx, Pc, -1, part, c.L.part_stride, c.st);
     return c.grid;
+  }
+  if (c.tc) {
+    const int g0 = tc_groups(Pc.m);
+    const int g = g0 < sm_count() ? (g0 < 1 ? 1 : g0) : sm_count();
+    launch_tc_gram(g, sm_count(), c.s, src, ldx, Pc, -1, c.colmax, part, c.L.part_stride, c.st);
+    return g;
   }
   if (c.csr) {  // the whole matrix only: rows reach across any split
     launch_csr_gram(c.P.np, c.L.csr_grid, c.s, src, ldx, c.P, -1, c.B, part, c.L.part_stride, c.st);
@@ -476,6 +529,9 @@ void after_pass(Call& c, int k, const double* Q, int64_t ldq) {
   if (c.P.np == 256) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     launch_gram256(c.grid, c.s, Q, ldq, c.P, k, c.partials, c.L.part_stride, c.st);
+  } else if (c.tc) {
+    tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
+    launch_tc_gram(c.L.tc_grid, sm_count(), c.s, Q, ldq, c.P, k, c.colmax, c.partials, c.L.part_stride, c.st);
   } else if (c.csr) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     launch_csr_gram(c.P.np, c.L.csr_grid, c.s, Q, ldq, c.P, k, c.B, c.partials, c.L.part_stride, c.st);
@@ -588,7 +644,7 @@ extern "C" int scqr3_factor_host(const double* X, int64_t m, int n, int64_t ldx,
     Layout L;
     int grid;
     PassGeom geo;
-    a = make_layout(m, n, B, opts && opts->precision == SCQR3_PREC_MIXED, 1, &L, &grid, &geo);
+    a = make_layout(m, n, B, opts ? opts->precision : SCQR3_PREC_FP64, 1, &L, &grid, &geo);
     if (a != SCQR3_OK) return a;
     if (workspace_bytes < L.total || ((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
     char* ws = (char*)workspace;

@@ -41,7 +41,9 @@ struct Params {
   double shift_scale;  // opts.shift_scale (<= 0: Eq. (finds2)/(finds2B) only)
   int algorithm;       // 2 (Alg. 2) or 3 (Alg. 3)
   double tol;          // Alg. 2 stopping tolerance (resolved on the host, > 0)
-  int csr;             // 1: B in CSR form (pass kernel solves only; csr_gram forms Q^T B Q)
+  int csr;             // 1: B in CSR form (csr_gram_kernel forms Q^T B Q)
+  int tc;              // 1: Gram matrices on the tensor cores (tc_gram_kernel)
+  int solve_only;      // 1: the pass kernel only solves; a separate kernel forms the Gram
 };
 
 // The factorization uses an oblique inner product (block-diagonal or CSR B).
@@ -56,6 +58,8 @@ struct Layout {
   size_t rdev, infodev;  // host-buffer entry point: R and info on the device
   int n_partials;    // partial Gram slots used by this call (grid CTAs x groups)
   int csr_grid;      // CTAs of csr_gram_kernel (CSR form only)
+  int tc_grid;       // CTAs of tc_gram_kernel (tensor-core Gram only)
+  size_t colmax;     // tensor-core Gram: per-column max |q_ij| (64 words)
   int part_stride;   // doubles per partial slot: pk_size(np) + 1 (||.||_F^2)
 };
 

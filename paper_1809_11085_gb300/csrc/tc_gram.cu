@@ -1,0 +1,419 @@
+// tc_gram.cu -- the Gram matrix A = Q^T Q on the BF16 tensor cores (tcgen05),
+// accurate to FP64 level, for n <= 64.
+//
+// The FP64 pipe of this GPU issues 2 DFMA per clock per SM, so the Gram matrix
+// of a tall-skinny matrix costs as much as the substitution. The tensor cores
+// multiply BF16 exactly into FP32, which allows an exact fixed-point split:
+//
+//  * every column j gets a scale sigma_j = 2^E_j > max_i |q_ij| (colmax_kernel);
+//  * |q_ij| / sigma_j * 2^56 is truncated to an integer F < 2^56 and cut into
+//    eight 7-bit digits a_0 .. a_7 (a_0 most significant), each carrying the
+//    sign of q_ij, so q_ij = sigma_j * sum_s a_s 2^(-7(s+1)) up to less than
+//    sigma_j 2^-56; every digit is exactly a BF16 number;
+//  * a product of two digits is below 2^14 and the tensor core accumulates
+//    it exactly in FP32 as long as a sum stays below 2^24: 256 rows of up to
+//    four digit pairs (4 * 256 * 127^2 < 2^24);
+//  * D_d = sum over digit pairs (s, t) with s + t = d, d = 0 .. 7, is read back
+//    from tensor memory every 256 rows. The digit sums are exact integers, so
+//    U = D_0 2^21 + D_1 2^14 + D_2 2^7 + D_3 and T = D_4 2^21 + ... + D_7
+//    (both below 2^46) are formed exactly in int64 and only 2^-35 U + 2^-63 T
+//    is accumulated in FP64 (the FP64 pipe is the scarce one). Pairs with
+//    s + t > 7 (below 2^-56 relative) are dropped.
+//
+// The result differs from q_j^T q_k by at most about m 2^-55 sigma_j sigma_k:
+// the norm-wise bound of the Gram error that the shift of Eq. (finds2)
+// covers (gamma_m n ||Q||^2), so the factorization keeps its guarantees.
+//
+// Layout: both operands are the digit planes of a 64-row chunk, K-major (the
+// chunk rows are the K dimension), no swizzle: core matrices of 8 columns x 8
+// rows (16 bytes per column), the 8 row groups of a column block contiguous
+// (128 bytes apart), column blocks 1024 bytes apart. A plane is 8 KB; planes
+// are stored in the order 0, 4, 1, 5, 2, 6, 3, 7 so that the A operand of one
+// MMA (M = 128) covers digit s in its rows 0..63 and digit s + 4 in rows
+// 64..127: one instruction computes the pairs (s, t) and (s + 4, t). Tile e
+// of tensor memory (columns 64e .. 64e+63) accumulates, for s = 0 .. min(3, e)
+// and t = e - s, the pairs (s, t) in lanes 0..63 (d = e) and (s + 4, t) in
+// lanes 64..127 (d = e + 4). Eight tiles use all 512 columns.
+//
+// One CTA of 256 threads per SM. Two 64 KB digit-plane stages: the threads cut
+// chunk c + 1 while the tensor core works on chunk c. When the rows are
+// contiguous (ld = n, m n even, 16-byte aligned), thread 0 brings chunk c + 2
+// into one of two 32 KB FP64 staging buffers with an asynchronous bulk copy
+// (cp.async.bulk, completion counted in bytes on an mbarrier), so the global
+// loads leave the critical path; otherwise the threads load the rows directly. Thread 0 issues the MMAs
+// (descriptors are a base plus compile-time offsets) and commits them to the
+// stage's mbarrier. For the read-back, warp w serves the tensor-memory lane
+// quadrant w % 4 and the 32 columns 32 (w / 4) ..; a warp whose rows all lie
+// below its columns (strict lower triangle) skips it. Every wait has an
+// iteration limit; past it the kernel records SCQR3_E_TIMEOUT, skips the rest
+// and frees its tensor memory.
+#include "fp64_device.cuh"
+
+namespace scqr3 {
+
+namespace tc {
+
+constexpr int NP = 64;              // padded n
+constexpr int KC = 64;              // rows per chunk (MMA K extent)
+constexpr int CHUNKS = 4;           // chunks per read-back group (256 rows)
+constexpr int PLANE = 8192;         // bytes per digit plane
+constexpr int STAGE = 8 * PLANE;    // 64 KB
+constexpr int THREADS = 256;
+constexpr uint32_t LBO = 128;       // K-direction core-matrix stride
+constexpr uint32_t SBO = 1024;      // column-block stride
+constexpr int XSTAGE = KC * NP * 8;  // FP64 rows of one chunk, staged by a bulk copy
+constexpr size_t SMEM = 2 * (size_t)STAGE + 2 * (size_t)XSTAGE + 1024;  // + alignment slack
+constexpr long long WAIT_LIMIT = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+               :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ uint64_t desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+// byte offset of digit plane s within a stage
+__host__ __device__ constexpr uint32_t plane_off(int s) { return s < 4 ? s * 2 * PLANE : (s - 4) * 2 * PLANE + PLANE; }
+
+// The MMAs of one chunk: tile e, digit s (and s + 4), digit t = e - s, K step kk.
+// The start-address field of a descriptor is its low 14 bits (address / 16);
+// the operands of a stage lie within 64 KB of its base, so offsets are added
+// to the base descriptor without carrying out of the field.
+template <int E, int S, int KK>
+__device__ __forceinline__ void issue_one(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
+  constexpr int T = E - S;
+  constexpr uint64_t aoff = (plane_off(S) + KK * 2 * LBO) >> 4;
+  constexpr uint64_t boff = (plane_off(T) + KK * 2 * LBO) >> 4;
+  const uint32_t accum = (!first_chunk || S > 0 || KK > 0) ? 1u : 0u;
+  mma(tmem + 64 * E, dbase + aoff, dbase + boff, idesc, accum);
+}
+template <int E, int S>
+__device__ __forceinline__ void issue_s(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
+  issue_one<E, S, 0>(dbase, tmem, idesc, first_chunk);
+  issue_one<E, S, 1>(dbase, tmem, idesc, first_chunk);
+  issue_one<E, S, 2>(dbase, tmem, idesc, first_chunk);
+  issue_one<E, S, 3>(dbase, tmem, idesc, first_chunk);
+  if constexpr (S < 3 && S < E) issue_s<E, S + 1>(dbase, tmem, idesc, first_chunk);
+}
+template <int E>
+__device__ __forceinline__ void issue_e(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
+  issue_s<E, 0>(dbase, tmem, idesc, first_chunk);
+  if constexpr (E < 7) issue_e<E + 1>(dbase, tmem, idesc, first_chunk);
+}
+
+// Bounded wait for the completion of the phase with parity `parity`.
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+               : "r"(taddr) : "memory");
+}
+
+// |x| / 2^E * 2^56 truncated to an integer (< 2^56 when |x| < 2^E).
+__device__ __forceinline__ unsigned long long fixed56(double x, int E) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  int ex = (int)((bits >> 52) & 0x7FF);
+  unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+  if (ex) mant |= 1ull << 52; else ex = 1;
+  const int sh = ex - 1019 - E;  // F = mant * 2^sh
+  return sh >= 0 ? (sh <= 3 ? (mant << sh) : (1ull << 56) - 1) : (sh > -64 ? (mant >> -sh) : 0ull);
+}
+
+// BF16 bit pattern of seven-bit digit s of F, with the sign bit `sign`.
+__device__ __forceinline__ uint32_t digit_bf16(unsigned long long F, int s, uint32_t sign) {
+  const uint32_t a = (uint32_t)((F >> (49 - 7 * s)) & 127u);
+  return (__float_as_uint((float)a) >> 16) | sign;
+}
+
+}  // namespace tc
+
+// Column scales: colmax[j] = max_i |q_ij| (as the bit pattern of a double;
+// +inf if a non-finite entry is seen) over rows [0, m) of src.
+__global__ void __launch_bounds__(256)
+colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int pass,
+              unsigned long long* __restrict__ colmax, const DevState* __restrict__ st) {
+  if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
+  __shared__ double red[256];
+  const int tid = threadIdx.x;
+  const int j = tid % 64, r0 = tid / 64;
+  double mx = 0.0;
+  bool bad = false;
+  if (j < n) {
+    for (int64_t i = (int64_t)blockIdx.x * 4 + r0; i < m; i += (int64_t)gridDim.x * 4) {
+      const double v = src[i * lds + j];
+      if (!isfinite(v)) bad = true;
+      mx = fmax(mx, fabs(v));
+    }
+  }
+  red[tid] = bad ? INFINITY : mx;
+  __syncthreads();
+  if (tid < 64 && j < n) {
+    double b = fmax(fmax(red[tid], red[tid + 64]), fmax(red[tid + 128], red[tid + 192]));
+    if (red[tid] == INFINITY || red[tid + 64] == INFINITY || red[tid + 128] == INFINITY || red[tid + 192] == INFINITY)
+      b = INFINITY;
+    atomicMax(&colmax[j], (unsigned long long)__double_as_longlong(b));  // non-negative doubles order as bits
+  }
+}
+
+__global__ void __launch_bounds__(tc::THREADS, 1)
+tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
+               const unsigned long long* __restrict__ colmax, double* __restrict__ partials, int part_stride,
+               DevState* __restrict__ st, int bulk) {
+  using namespace tc;
+  if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
+  extern __shared__ uint8_t dsm[];
+  uint8_t* stages = (uint8_t*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t bar[2];   // MMAs of the stage's chunk done
+  __shared__ __align__(8) uint64_t full[2];  // staged rows of the buffer's chunk arrived
+  __shared__ uint32_t tslot;
+  __shared__ int Esh[NP];
+  __shared__ double sig[NP];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = P.n;
+  const int64_t m = P.m;
+  double* part = partials + (int64_t)blockIdx.x * part_stride;
+
+  int bad = 0;
+  if (tid < NP) {
+    int E = -1000;
+    double sg = 0.0;
+    if (tid < n) {
+      const double cm = __longlong_as_double((long long)colmax[tid]);
+      if (!isfinite(cm)) {
+        bad = 1;  // non-finite input: the Gram matrix is NaN
+      } else if (cm > 0.0) {
+        const int ex = (int)((colmax[tid] >> 52) & 0x7FF);
+        E = (ex ? ex : 1) - 1023 + 1;  // cm < 2^E
+        sg = ldexp(1.0, E);
+      }
+    }
+    Esh[tid] = E;
+    sig[tid] = sg;
+  }
+  if (__syncthreads_or(bad)) {
+    for (int e = tid; e < part_stride; e += THREADS) part[e] = NAN;
+    return;
+  }
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&bar[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full[i])), "r"(1));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+  const uint32_t sbase = smem_u32(stages);
+  // D F32, A and B BF16, both K-major, N = 64, M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+  // read-back: lane quadrant qd = warp % 4 (row 32 qd + lane of the tiles;
+  // rows 0..63 hold d = e, rows 64..127 d = e + 4), columns 32 h .. 32 h + 31
+  const int qd = warp & 3, h = warp >> 2;
+  const int row = 32 * qd + lane;
+  const int jr = row & 63;
+  const bool upper = row < 64;
+  const bool rb_skip = h == 0 && (qd & 1) == 1;  // rows 32..63 x columns 0..31: below the diagonal
+  double acc[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+
+  // This CTA's chunks in order: ordinal k is chunk k % CHUNKS of its group
+  // blockIdx.x + (k / CHUNKS) gridDim.x; the sequence ends at the first
+  // chunk past m (only the last group can be partial).
+  uint8_t* xst = stages + 2 * STAGE;  // two FP64 staging buffers
+  auto row0_of = [&](uint32_t k) -> int64_t {
+    const int64_t g = blockIdx.x + (int64_t)(k / CHUNKS) * gridDim.x;
+    const int64_t r0 = (g * CHUNKS + (k % CHUNKS)) * KC;
+    return r0 < m ? r0 : -1;
+  };
+  // thread 0: bulk copy of chunk k's rows into staging buffer k % 2
+  uint32_t issued = 0;  // thread 0: chunks whose copy was issued
+  auto stage_in = [&](uint32_t k) {
+    const int64_t r0 = row0_of(k);
+    if (r0 < 0) return;
+    issued = k + 1;
+    const int rows = (int)((m - r0) < KC ? (m - r0) : KC);
+    const uint32_t bytes = (uint32_t)rows * (uint32_t)n * 8u;
+    const uint32_t fb = smem_u32(&full[k & 1]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(xst + (k & 1) * XSTAGE)), "l"(src + r0 * lds), "r"(bytes), "r"(fb) : "memory");
+  };
+  if (bulk && tid == 0) {
+    stage_in(0);
+    stage_in(1);
+  }
+
+  uint32_t chunk = 0;    // chunks committed by this CTA
+  uint32_t staged = 0;   // staging waits done
+  bool ok = true;
+  for (;; ++chunk) {
+    const int64_t row0 = row0_of(chunk);
+    if (row0 < 0) break;
+    const int q = (int)(chunk % CHUNKS);
+    const int rows = (int)((m - row0) < KC ? (m - row0) : KC);
+    const int stg = chunk & 1;
+    // the stage's previous chunk must be consumed and this chunk's rows staged;
+    // the decision is the CTA's
+    bool w = chunk < 2 || wait_parity(smem_u32(&bar[stg]), ((chunk - 2) >> 1) & 1);
+    if (bulk) w = wait_parity(smem_u32(&full[stg]), (chunk >> 1) & 1) && w;
+    if (!__syncthreads_and(w)) {
+      ok = false;
+      break;
+    }
+    staged = chunk + 1;
+    uint8_t* sb = stages + stg * STAGE;
+    const double* xs = (const double*)(xst + stg * XSTAGE);
+    // cut the chunk: unit (j, ig) = 8 consecutive rows of column j
+    for (int u = tid; u < NP * (KC / 8); u += THREADS) {
+      const int j = u % NP, ig = u / NP;
+      const int E = Esh[j];
+      unsigned long long F[8];
+      uint32_t sg[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = ig * 8 + r;
+        double x = 0.0;
+        if (j < n && i < rows) x = bulk ? xs[i * n + j] : src[(row0 + i) * lds + j];
+        F[r] = tc::fixed56(x, E);
+        sg[r] = (uint32_t)(((unsigned long long)__double_as_longlong(x) >> 48) & 0x8000u);
+      }
+      uint8_t* dst = sb + (j >> 3) * SBO + ig * LBO + (j & 7) * 16;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        uint4 w4;
+        w4.x = tc::digit_bf16(F[0], s, sg[0]) | (tc::digit_bf16(F[1], s, sg[1]) << 16);
+        w4.y = tc::digit_bf16(F[2], s, sg[2]) | (tc::digit_bf16(F[3], s, sg[3]) << 16);
+        w4.z = tc::digit_bf16(F[4], s, sg[4]) | (tc::digit_bf16(F[5], s, sg[5]) << 16);
+        w4.w = tc::digit_bf16(F[6], s, sg[6]) | (tc::digit_bf16(F[7], s, sg[7]) << 16);
+        *(uint4*)(dst + plane_off(s)) = w4;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      if (bulk) stage_in(chunk + 2);  // buffer stg is consumed
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      tc::issue_e<0>(desc(sbase + stg * STAGE), tmem, idesc, q == 0);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&bar[stg])) : "memory");
+    }
+    if (q != CHUNKS - 1 && row0_of(chunk + 1) >= 0) continue;
+    // end of a group: all its MMAs (the last commit covers every earlier one)
+    if (!__syncthreads_and(wait_parity(smem_u32(&bar[stg]), (chunk >> 1) & 1))) {
+      ok = false;
+      ++chunk;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!rb_skip) {
+      const uint32_t tq = tmem + ((uint32_t)(32 * qd) << 16) + 32 * h;
+#pragma unroll
+      for (int c = 0; c < 32; c += 16) {
+        // U from tiles 0..3 and T from tiles 4..7 (upper rows); the lower rows
+        // hold d = e + 4: T from tiles 0..3 (tiles 4..7 would be d >= 8)
+        long long U[16], T[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) U[k] = T[k] = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          if (!upper && e >= 4) break;
+          uint32_t v[16];
+          tc::ld16(tq + 64 * e + c, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int d = upper ? e : e + 4;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const long long dv = (long long)__float2int_rn(__uint_as_float(v[k]));
+            if (d < 4) U[k] = U[k] * 128 + dv;
+            else T[k] = T[k] * 128 + dv;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          if (32 * h + c + k < jr) continue;
+          acc[c + k] = fma(0x1p-35, (double)U[k], acc[c + k]);
+          acc[c + k] = fma(0x1p-63, (double)T[k], acc[c + k]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // tensor memory is read before the next group overwrites it
+  }
+  if (!ok) {
+    atomicCAS(&st->status, SCQR3_OK, SCQR3_E_TIMEOUT);
+    // let the MMAs and copies already issued finish (bounded) before the memory goes away
+    if (chunk > 0) wait_parity(smem_u32(&bar[(chunk - 1) & 1]), ((chunk - 1) >> 1) & 1);
+    if (bulk && tid == 0)
+      for (uint32_t k = staged; k < issued; ++k) wait_parity(smem_u32(&full[k & 1]), (k >> 1) & 1);
+  }
+
+  // rows 64..127 hold the d + 4 share of the same entries: add them to rows 0..63
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  double* xch = (double*)stages;  // 64 x 64 doubles (32 KB) of stage 0
+  if (!upper) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) xch[jr * NP + 32 * h + k] = acc[k];
+  }
+  __syncthreads();
+  if (upper && !rb_skip) {
+    const double sj = sig[jr];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const int col = 32 * h + k;
+      if (col >= jr) part[pk_idx(NP, jr, col)] = (acc[k] + xch[jr * NP + col]) * sj * sig[col];
+    }
+  }
+  if (tid == 0) part[pk_size(NP)] = 0.0;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+}
+
+// ---- host side ----------------------------------------------------------------------------
+
+cudaError_t tc_setup() {
+  return cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+}
+
+int tc_groups(int64_t m) { return (int)((m + tc::KC * tc::CHUNKS - 1) / (tc::KC * tc::CHUNKS)); }
+
+// Column scales then the tensor-core Gram of rows [0, P.m) of src into `grid` slots.
+void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
+                    unsigned long long* colmax, double* partials, int part_stride, DevState* st) {
+  if (P.np != tc::NP || part_stride != pk_size(tc::NP) + 1) return;  // the slots hold the 64-column layout
+  cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * tc::NP, s);
+  const int64_t want = (P.m + 3) / 4;
+  const int cg = (int)(want < (int64_t)sms * 8 ? (want < 1 ? 1 : want) : (int64_t)sms * 8);
+  colmax_kernel<<<cg, 256, 0, s>>>(src, lds, P.m, P.n, pass, colmax, st);
+  // bulk copies need contiguous rows, 16-byte aligned, and chunk sizes that are
+  // multiples of 16 bytes (m n even)
+  const int bulk = (lds == P.n && ((uintptr_t)src & 15) == 0 && ((P.m * P.n) & 1) == 0) ? 1 : 0;
+  tc_gram_kernel<<<grid, tc::THREADS, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials, part_stride, st, bulk);
+}
+
+}  // namespace scqr3

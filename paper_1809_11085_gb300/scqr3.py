@@ -18,6 +18,7 @@ OK = 0
 E_NONFINITE = -100
 E_MAXPASS = -101
 E_B_INVALID = -108
+E_TIMEOUT = -102
 E_CUDA = -103
 E_WORKSPACE = -104
 E_B_NOT_SPD = -105
@@ -179,6 +180,7 @@ def _b_struct(B, normb):
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_TC = 2  # FP64 substitution, Gram matrices on the BF16 tensor cores (exact digit split)
 ALG_ADAPTIVE = 2  # Alg. 2: shift only on breakdown, stop on the orthogonality test
 ALG_SCQR3 = 3     # Alg. 3: shifted pass, then CholeskyQR2
 

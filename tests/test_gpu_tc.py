@@ -1,0 +1,128 @@
+"""GPU parity of precision=SCQR3_PREC_TC: FP64 substitution with the Gram
+matrices on the BF16 tensor cores through the exact seven-bit digit split.
+
+The split represents each entry to 2^-56 of its column's scale and every digit
+product and 256-row sum is exact, so the Gram matrix is accurate to about
+m 2^-55 sigma_j sigma_k: the same order as an FP64 Gram matrix. The tests
+therefore use the FP64 parity tolerances against the oracle:
+||Q^T Q - I||_2 <= 1e-13, ||X - QR||_F / ||X||_F <= 1e-13, and R within
+1e-12 (kappa <= 1e8) or 100 n kappa u.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1809_11085_gb300 import scqr3  # noqa: E402
+from paper_1809_11085_gb300.testmat import testmat  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+TC = scqr3.PREC_TC
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1809_11085_gb300 import build
+
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def run(Xh, **kw):
+    Q, R, info = scqr3.factor(torch.from_numpy(Xh).cuda(), precision=TC, **kw)
+    torch.cuda.synchronize()
+    return Q.cpu().numpy(), R.cpu().numpy(), info
+
+
+def check(Xh, kappa, **kw):
+    Qg, Rg, info = run(Xh, **kw)
+    Qo, Ro, st, tr = oracle.scqr3(Xh, normx2=kw.get("norm_x2", 0.0), algorithm=kw.get("algorithm", 3))
+    assert st == 0 and info.status == 0, (st, info)
+    n = Xh.shape[1]
+    assert np.array_equal(np.tril(Rg, -1), np.zeros((n, n)))
+    assert (np.diag(Rg) > 0).all()
+    assert np.linalg.norm(Qg.T @ Qg - np.eye(n), 2) <= 1e-13
+    assert np.linalg.norm(Xh - Qg @ Rg) / np.linalg.norm(Xh) <= 1e-13
+    dR = np.linalg.norm(Rg - Ro) / np.linalg.norm(Ro)
+    assert dR <= (1e-12 if kappa <= 1e8 else 100 * n * kappa * U), dR
+    return info, tr
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 16, 31, 32, 33, 63, 64])
+@pytest.mark.parametrize("m_kind", ["square", "small", "ragged", "tall"])
+def test_shape_sweep(n, m_kind):
+    m = {"square": n, "small": 300, "ragged": 20011, "tall": 100003}[m_kind]
+    if m < n:
+        m = n
+    Xh = testmat(m, n, 1e6, seed=6000 + n + m)
+    check(Xh, 1e6)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e8, 1e12, 1e15])
+def test_conditioning(kappa):
+    """The pass structure follows the oracle's where the decisions are not
+    marginal (kappa 1e2, 1e8: three passes; 1e15: a second shifted pass)."""
+    Xh = testmat(50000, 64, kappa, seed=6100)
+    info, tr = check(Xh, kappa, norm_x2=1.0)
+    if kappa in (1e2, 1e8):
+        assert info.passes == tr["passes"] == 3
+
+
+def test_badly_scaled_columns_and_rows():
+    """Column scales from 2^-300 to 2^300 and rows spanning 1e-30 .. 1: each
+    column has its own power-of-two scale, and the fixed-point error is
+    relative to it, which is what the norm-wise Gram bound needs."""
+    rng = np.random.default_rng(6200)
+    m, n = 30000, 40
+    Xh = testmat(m, n, 1e4, seed=6201)
+    Xh *= np.exp2(rng.integers(-300, 300, size=n))[None, :]
+    Xh[rng.random(m) < 0.3] *= 1e-30
+    Qg, Rg, info = run(Xh)
+    assert info.status == 0
+    Qd, Rd, idv = scqr3.factor(torch.from_numpy(Xh).cuda())
+    Rd = Rd.cpu().numpy()
+    assert info.passes == idv.passes
+    # column scaling commutes with QR: compare R column-scaled
+    scale = np.abs(np.diag(Rd))
+    assert np.linalg.norm((Rg - Rd) / scale[None, :]) < 1e-10
+    assert np.linalg.norm(Qg.T @ Qg - np.eye(n), 2) < 1e-13
+
+
+def test_matches_fp64_form_at_scale():
+    m, n = 1_000_000, 64
+    from paper_1809_11085_gb300.testmat import testmat_torch
+
+    X, _, _ = testmat_torch(m, n, 1e8, seed=6300)
+    Qt, Rt, it = scqr3.factor(X, precision=TC)
+    Qd, Rd, idv = scqr3.factor(X)
+    torch.cuda.synchronize()
+    assert it.status == 0 and it.passes == idv.passes
+    assert (torch.linalg.matrix_norm(Rt - Rd) / torch.linalg.matrix_norm(Rd)).item() < 1e-12
+    eye = torch.eye(n, dtype=torch.float64, device="cuda")
+    assert torch.linalg.matrix_norm(Qt.T @ Qt - eye, 2).item() < 1e-13
+    assert (torch.linalg.matrix_norm(X - Qt @ Rt) / torch.linalg.matrix_norm(X)).item() < 1e-13
+
+
+def test_deterministic_host_form_and_alg2():
+    Xh = testmat(200000, 64, 1e10, seed=6400)
+    Q1, R1, i1 = run(Xh)
+    Q2, R2, i2 = run(Xh)
+    assert np.array_equal(Q1, Q2) and np.array_equal(R1, R2)
+    X = torch.empty(Xh.shape, dtype=torch.float64, pin_memory=True)
+    X.copy_(torch.from_numpy(Xh))
+    Qh, Rh, ih = scqr3.factor_host(X, precision=TC)  # one chunk: the same launches
+    assert ih.status == 0
+    assert np.array_equal(Qh.numpy(), Q1) and np.array_equal(Rh.numpy(), R1)
+    check(testmat(100000, 48, 1e5, seed=6401), 1e5, algorithm=scqr3.ALG_ADAPTIVE)
+
+
+def test_non_finite_and_rejections():
+    Xh = testmat(5000, 16, 1e4, seed=6500)
+    Xh[77, 3] = np.inf
+    _, _, info = run(Xh)
+    assert info.status == scqr3.E_NONFINITE
+    with pytest.raises(scqr3.ScqrError):
+        scqr3.factor(torch.zeros((1000, 65), dtype=torch.float64, device="cuda"), precision=TC)
