@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--m", type=int, default=16777216)
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--kappa", type=float, default=1e10)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "tc"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "tc", "mixed_tc"],
                     help="arithmetic of the timed factorization (mixed: FP32 pairs + FP64; tc: FP64 "
                          "substitution with the Gram matrices on the BF16 tensor cores, exact digit split)")
     ap.add_argument("--no-sweep", action="store_true")
@@ -269,7 +269,8 @@ def run_gpu(args, rank, world, local_rank):
     ws = scqr3.Workspace(m, n, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    prec = {"fp64": scqr3.PREC_FP64, "mixed": scqr3.PREC_MIXED, "tc": scqr3.PREC_TC}[args.precision]
+    prec = {"fp64": scqr3.PREC_FP64, "mixed": scqr3.PREC_MIXED, "tc": scqr3.PREC_TC,
+            "mixed_tc": scqr3.PREC_MIXED_TC}[args.precision]
     for _ in range(args.warmup):
         scqr3.factor(X, Q=Q, workspace=ws, read_info=False, precision=prec)
     torch.cuda.synchronize(dev)
@@ -312,7 +313,8 @@ def run_gpu(args, rank, world, local_rank):
     for kernel, p, t in recs:
         name = scqr3.KERNEL_NAMES.get(kernel, str(kernel))
         share[name] = share.get(name, 0.0) + t
-        f = pass_kernel_flops(m, n, kernel, p, passes, gram_in_pass=prec != scqr3.PREC_TC)
+        f = pass_kernel_flops(m, n, kernel, p, passes,
+                              gram_in_pass=prec not in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC))
         if f > 0:
             kflops += f
             kms += t

@@ -79,6 +79,10 @@ extern "C" {
  * Eq. (finds2) covers, so results match the FP64 form to rounding. Not in
  * the paper. n <= 64 and B = NULL. */
 #define SCQR3_PREC_TC 2
+/* The mixed form's substitution (FP32 pairs) with the Gram matrices of
+ * SCQR3_PREC_TC; the iterates are kept in FP64 between passes. n <= 64 and
+ * B = NULL. Not in the paper. */
+#define SCQR3_PREC_MIXED_TC 3
 
 /* Oblique inner product (x, y)_B = x^T B y of Sec. 5, for SPD B given
  * either block-diagonal, B = blockdiag(B_1, ..., B_{m/bs}) (bs > 0), or as a

@@ -104,9 +104,9 @@ df_pass_kernel(const double* src, int64_t lds, double* dst, int64_t ldd, Params 
   if (pass >= 0) {
     if (!st->run_trsm[pass]) return;
     do_trsm = true;
-    do_gram = st->gram_after[pass] != 0;
+    do_gram = st->gram_after[pass] != 0 && !P.solve_only;
   }
-  const bool src_fp64 = pass <= 0;
+  const bool src_fp64 = pass <= 0 || P.solve_only;  // solve-only: FP64 iterates between passes
   const bool dst_fp64 = !do_gram;
   const float2* srcf = reinterpret_cast<const float2*>(src);
   float2* dstf = reinterpret_cast<float2*>(dst);
@@ -272,9 +272,9 @@ df2_pass_kernel(const double* src, int64_t lds, double* dst, int64_t ldd, Params
   if (pass >= 0) {
     if (!st->run_trsm[pass]) return;
     do_trsm = true;
-    do_gram = st->gram_after[pass] != 0;
+    do_gram = st->gram_after[pass] != 0 && !P.solve_only;
   }
-  const bool src_fp64 = pass <= 0;
+  const bool src_fp64 = pass <= 0 || P.solve_only;  // solve-only: FP64 iterates between passes
   const bool dst_fp64 = !do_gram;
   const float2* srcf = reinterpret_cast<const float2*>(src);
   float2* dstf = reinterpret_cast<float2*>(dst);
@@ -443,9 +443,9 @@ dfp_pass_kernel(const double* src, int64_t lds, double* dst, int64_t ldd, Params
   if (pass >= 0) {
     if (!st->run_trsm[pass]) return;
     do_trsm = true;
-    do_gram = st->gram_after[pass] != 0;
+    do_gram = st->gram_after[pass] != 0 && !P.solve_only;
   }
-  const bool src_fp64 = pass <= 0;
+  const bool src_fp64 = pass <= 0 || P.solve_only;  // solve-only: FP64 iterates between passes
   const bool dst_fp64 = !do_gram;
   const float2* srcf = reinterpret_cast<const float2*>(src);
   float2* dstf = reinterpret_cast<float2*>(dst);

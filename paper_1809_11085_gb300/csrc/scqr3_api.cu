@@ -165,9 +165,12 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
   if (opts && opts->max_passes != 0 && (opts->max_passes < 3 || opts->max_passes > SCQR3_MAX_PASSES))
     return -12;
   if (opts && opts->precision != SCQR3_PREC_FP64 && opts->precision != SCQR3_PREC_MIXED &&
-      opts->precision != SCQR3_PREC_TC)
+      opts->precision != SCQR3_PREC_TC && opts->precision != SCQR3_PREC_MIXED_TC)
     return -12;
-  if (opts && opts->precision == SCQR3_PREC_TC && (B || n > 64)) return SCQR3_E_UNSUPPORTED;
+  const bool tcp = opts && (opts->precision == SCQR3_PREC_TC || opts->precision == SCQR3_PREC_MIXED_TC);
+  // tensor-core Gram: n <= 64, B = I, and at most 2^31 rows (its exact int64
+  // digit-sum accumulators)
+  if (tcp && (B || n > 64 || m > ((int64_t)1 << 31))) return SCQR3_E_UNSUPPORTED;
   if (opts && opts->precision == SCQR3_PREC_MIXED && B) return -5;  // mixed form: B = I only
   if (opts && opts->algorithm != 0 && opts->algorithm != SCQR3_ALG_SCQR3 &&
       opts->algorithm != SCQR3_ALG_ADAPTIVE)
@@ -192,7 +195,8 @@ int64_t host_chunk_rows(int64_t m) {
 
 int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunks, Layout* L, int* grid,
                     PassGeom* geo) {
-  const bool mixed = prec == SCQR3_PREC_MIXED, tcg = prec == SCQR3_PREC_TC;
+  const bool mixed = prec == SCQR3_PREC_MIXED || prec == SCQR3_PREC_MIXED_TC;
+  const bool tcg = prec == SCQR3_PREC_TC || prec == SCQR3_PREC_MIXED_TC;
   const int np = tcg ? 64 : padded_n(n);  // the tensor-core Gram works on 64 columns
   int grid_max = 0;
   if (device_geo(np, &grid_max, geo) != cudaSuccess) return SCQR3_E_CUDA;
@@ -289,8 +293,8 @@ int make_layout(int64_t m, int n, const scqr3_B* B, int prec, int host_chunks, L
                 PassGeom* geo) {
   const int r = make_layout_one(m, n, B, prec, host_chunks, L, grid, geo);
   if (r != SCQR3_OK) return r;
-  for (int p : {SCQR3_PREC_FP64, SCQR3_PREC_TC}) {
-    if (p == prec || (p == SCQR3_PREC_TC && (B || n > 64))) continue;
+  for (int p : {SCQR3_PREC_FP64, SCQR3_PREC_TC, SCQR3_PREC_MIXED_TC}) {
+    if (p == prec || (p != SCQR3_PREC_FP64 && (B || n > 64))) continue;
     Layout L2;
     int g2;
     PassGeom geo2;
@@ -404,8 +408,8 @@ int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void*
                size_t workspace_bytes, int host_chunks, double* R, double* Rpass, scqr3_info* info,
                cudaStream_t s, Call* c) {
   if (((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
-  c->mixed = opts && opts->precision == SCQR3_PREC_MIXED;
-  c->tc = opts && opts->precision == SCQR3_PREC_TC;
+  c->mixed = opts && (opts->precision == SCQR3_PREC_MIXED || opts->precision == SCQR3_PREC_MIXED_TC);
+  c->tc = opts && (opts->precision == SCQR3_PREC_TC || opts->precision == SCQR3_PREC_MIXED_TC);
   const int r = make_layout(m, n, B, opts ? opts->precision : SCQR3_PREC_FP64, host_chunks, &c->L, &c->grid,
                             &c->geo);
   if (r != SCQR3_OK) return r;
@@ -582,7 +586,7 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
     solve_rows(c, k, k == 0 ? X : Q, k == 0 ? ldx : ldq, Q, ldq, 0, m);
     if (k + 1 < c.P.max_passes) after_pass(c, k, Q, ldq);
   }
-  if (c.mixed) {
+  if (c.mixed && !c.P.solve_only) {  // float pairs may remain only when the solves fuse the Gram
     tick(c.s, SCQR3_KERNEL_FINISH, -1);
     launch_df_finish(sm_count() * 4, c.s, Q, ldq, m, n, c.P.max_passes, c.st);
   }
@@ -708,7 +712,7 @@ extern "C" int scqr3_factor_host(const double* X, int64_t m, int n, int64_t ldx,
     break;
   }
   if (!copied) {  // stopped by Alg. 2's test or a failure: Q as the device left it
-    if (c.mixed) {
+    if (c.mixed && !c.P.solve_only) {
       tick(s, SCQR3_KERNEL_FINISH, -1);
       launch_df_finish(sm_count() * 4, s, Qdev, n, m, n, c.P.max_passes, c.st);
     }

@@ -16,9 +16,11 @@
 //  * D_d = sum over digit pairs (s, t) with s + t = d, d = 0 .. 7, is read back
 //    from tensor memory every 256 rows. The digit sums are exact integers, so
 //    U = D_0 2^21 + D_1 2^14 + D_2 2^7 + D_3 and T = D_4 2^21 + ... + D_7
-//    (both below 2^46) are formed exactly in int64 and only 2^-35 U + 2^-63 T
-//    is accumulated in FP64 (the FP64 pipe is the scarce one). Pairs with
-//    s + t > 7 (below 2^-56 relative) are dropped.
+//    (each below 2^45.1 per 256 rows) are accumulated exactly in int64 over
+//    all of a CTA's rows (at most 2^31 rows in all, so below 2^63), and only
+//    the final 2^-35 U + 2^-63 T is formed in FP64: the FP64 pipe, the scarce
+//    one, does no work per row. Pairs with s + t > 7 (below 2^-56 relative)
+//    are dropped.
 //
 // The result differs from q_j^T q_k by at most about m 2^-55 sigma_j sigma_k:
 // the norm-wise bound of the Gram error that the shift of Eq. (finds2)
@@ -35,7 +37,7 @@
 // and t = e - s, the pairs (s, t) in lanes 0..63 (d = e) and (s + 4, t) in
 // lanes 64..127 (d = e + 4). Eight tiles use all 512 columns.
 //
-// One CTA of 256 threads per SM. Two 64 KB digit-plane stages: the threads cut
+// One CTA of 256 + 32 threads per SM. Two 64 KB digit-plane stages: the threads cut
 // chunk c + 1 while the tensor core works on chunk c. When the rows are
 // contiguous (ld = n, m n even, 16-byte aligned), thread 0 brings chunk c + 2
 // into one of two 32 KB FP64 staging buffers with an asynchronous bulk copy
@@ -58,7 +60,7 @@ constexpr int KC = 64;              // rows per chunk (MMA K extent)
 constexpr int CHUNKS = 4;           // chunks per read-back group (256 rows)
 constexpr int PLANE = 8192;         // bytes per digit plane
 constexpr int STAGE = 8 * PLANE;    // 64 KB
-constexpr int THREADS = 256;
+constexpr int THREADS = 256;   // slicer and read-back threads (the producer warp comes on top)
 constexpr uint32_t LBO = 128;       // K-direction core-matrix stride
 constexpr uint32_t SBO = 1024;      // column-block stride
 constexpr int XSTAGE = KC * NP * 8;  // FP64 rows of one chunk, staged by a bulk copy
@@ -134,10 +136,20 @@ __device__ __forceinline__ unsigned long long fixed56(double x, int E) {
   return sh >= 0 ? (sh <= 3 ? (mant << sh) : (1ull << 56) - 1) : (sh > -64 ? (mant >> -sh) : 0ull);
 }
 
-// BF16 bit pattern of seven-bit digit s of F, with the sign bit `sign`.
+__device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr) : "memory");
+}
+
+// BF16 bit pattern of seven-bit digit s of F, with the sign bit `sign`. The
+// integer becomes a float exactly as (2^23 + a) - 2^23 (one full-rate FP32 add
+// instead of a quarter-rate conversion); a < 128 has at most 7 significant
+// bits, so its BF16 pattern is the top half of the float's.
 __device__ __forceinline__ uint32_t digit_bf16(unsigned long long F, int s, uint32_t sign) {
   const uint32_t a = (uint32_t)((F >> (49 - 7 * s)) & 127u);
-  return (__float_as_uint((float)a) >> 16) | sign;
+  const float f = __fsub_rn(__uint_as_float(0x4B000000u | a), 8388608.0f);
+  return (__float_as_uint(f) >> 16) | sign;
 }
 
 }  // namespace tc
@@ -170,7 +182,7 @@ colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int
   }
 }
 
-__global__ void __launch_bounds__(tc::THREADS, 1)
+__global__ void __launch_bounds__(tc::THREADS + 32, 1)
 tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
                const unsigned long long* __restrict__ colmax, double* __restrict__ partials, int part_stride,
                DevState* __restrict__ st, int bulk) {
@@ -178,12 +190,17 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
   extern __shared__ uint8_t dsm[];
   uint8_t* stages = (uint8_t*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bar[2];   // MMAs of the stage's chunk done
-  __shared__ __align__(8) uint64_t full[2];  // staged rows of the buffer's chunk arrived
+  uint8_t* xst = stages + 2 * STAGE;           // two FP64 staging buffers
+  __shared__ __align__(8) uint64_t bar[2];     // MMAs of the stage's chunk done (tcgen05.commit)
+  __shared__ __align__(8) uint64_t full[2];    // staged rows of the buffer's chunk arrived (bytes)
+  __shared__ __align__(8) uint64_t pfull[2];   // digit planes of the stage written (256 arrivals)
+  __shared__ __align__(8) uint64_t tfree;      // tensor memory read back (256 arrivals)
   __shared__ uint32_t tslot;
   __shared__ int Esh[NP];
   __shared__ double sig[NP];
+  __shared__ volatile int err_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool producer = warp == THREADS / 32;  // warp 8: copies and MMAs (lane 0)
   const int n = P.n;
   const int64_t m = P.m;
   double* part = partials + (int64_t)blockIdx.x * part_stride;
@@ -206,15 +223,18 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
     sig[tid] = sg;
   }
   if (__syncthreads_or(bad)) {
-    for (int e = tid; e < part_stride; e += THREADS) part[e] = NAN;
+    for (int e = tid; e < part_stride; e += blockDim.x) part[e] = NAN;
     return;
   }
 
   if (tid == 0) {
+    err_sh = 0;
     for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&bar[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&pfull[i])), "r"(THREADS));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&tfree)), "r"(THREADS));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -229,163 +249,171 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   // D F32, A and B BF16, both K-major, N = 64, M = 128
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-  // read-back: lane quadrant qd = warp % 4 (row 32 qd + lane of the tiles;
-  // rows 0..63 hold d = e, rows 64..127 d = e + 4), columns 32 h .. 32 h + 31
-  const int qd = warp & 3, h = warp >> 2;
-  const int row = 32 * qd + lane;
-  const int jr = row & 63;
-  const bool upper = row < 64;
-  const bool rb_skip = h == 0 && (qd & 1) == 1;  // rows 32..63 x columns 0..31: below the diagonal
-  double acc[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) acc[k] = 0.0;
-
   // This CTA's chunks in order: ordinal k is chunk k % CHUNKS of its group
-  // blockIdx.x + (k / CHUNKS) gridDim.x; the sequence ends at the first
-  // chunk past m (only the last group can be partial).
-  uint8_t* xst = stages + 2 * STAGE;  // two FP64 staging buffers
+  // blockIdx.x + (k / CHUNKS) gridDim.x; the sequence ends at the first chunk
+  // past m (only the last group can be partial).
   auto row0_of = [&](uint32_t k) -> int64_t {
     const int64_t g = blockIdx.x + (int64_t)(k / CHUNKS) * gridDim.x;
     const int64_t r0 = (g * CHUNKS + (k % CHUNKS)) * KC;
     return r0 < m ? r0 : -1;
   };
-  // thread 0: bulk copy of chunk k's rows into staging buffer k % 2
-  uint32_t issued = 0;  // thread 0: chunks whose copy was issued
-  auto stage_in = [&](uint32_t k) {
-    const int64_t r0 = row0_of(k);
-    if (r0 < 0) return;
-    issued = k + 1;
-    const int rows = (int)((m - r0) < KC ? (m - r0) : KC);
-    const uint32_t bytes = (uint32_t)rows * (uint32_t)n * 8u;
-    const uint32_t fb = smem_u32(&full[k & 1]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(smem_u32(xst + (k & 1) * XSTAGE)), "l"(src + r0 * lds), "r"(bytes), "r"(fb) : "memory");
-  };
-  if (bulk && tid == 0) {
-    stage_in(0);
-    stage_in(1);
-  }
+  auto group_end = [&](uint32_t k) { return (k % CHUNKS) == CHUNKS - 1 || row0_of(k + 1) < 0; };
 
-  uint32_t chunk = 0;    // chunks committed by this CTA
-  uint32_t staged = 0;   // staging waits done
-  bool ok = true;
-  for (;; ++chunk) {
-    const int64_t row0 = row0_of(chunk);
-    if (row0 < 0) break;
-    const int q = (int)(chunk % CHUNKS);
-    const int rows = (int)((m - row0) < KC ? (m - row0) : KC);
-    const int stg = chunk & 1;
-    // the stage's previous chunk must be consumed and this chunk's rows staged;
-    // the decision is the CTA's
-    bool w = chunk < 2 || wait_parity(smem_u32(&bar[stg]), ((chunk - 2) >> 1) & 1);
-    if (bulk) w = wait_parity(smem_u32(&full[stg]), (chunk >> 1) & 1) && w;
-    if (!__syncthreads_and(w)) {
-      ok = false;
-      break;
-    }
-    staged = chunk + 1;
-    uint8_t* sb = stages + stg * STAGE;
-    const double* xs = (const double*)(xst + stg * XSTAGE);
-    // cut the chunk: unit (j, ig) = 8 consecutive rows of column j
-    for (int u = tid; u < NP * (KC / 8); u += THREADS) {
-      const int j = u % NP, ig = u / NP;
-      const int E = Esh[j];
-      unsigned long long F[8];
-      uint32_t sg[8];
+  // read-back of the slicer warps: lane quadrant qd = warp % 4 (row 32 qd +
+  // lane of the tiles; rows 0..63 hold d = e, rows 64..127 d = e + 4),
+  // columns 32 h .. 32 h + 31; rows 32..63 x columns 0..31 lie below the diagonal
+  constexpr int CW = 32;
+  const int qd = warp & 3, h = (warp >> 2) & 1;
+  const int row = 32 * qd + lane;
+  const int jr = row & 63;
+  const bool upper = row < 64;
+  const bool rb_skip = (qd & 1) == 1 && h == 0;
+  // exact digit-sum accumulators of this thread's 32 entries: U (d = 0..3)
+  // and T (d = 4..7)
+  long long U[CW], T[CW];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int i = ig * 8 + r;
-        double x = 0.0;
-        if (j < n && i < rows) x = bulk ? xs[i * n + j] : src[(row0 + i) * lds + j];
-        F[r] = tc::fixed56(x, E);
-        sg[r] = (uint32_t)(((unsigned long long)__double_as_longlong(x) >> 48) & 0x8000u);
+  for (int k = 0; k < CW; ++k) U[k] = T[k] = 0;
+
+  uint32_t issued = 0;     // producer: chunks whose rows were requested
+  uint32_t committed = 0;  // producer: chunks whose MMAs were committed
+  if (producer) {
+    if (lane == 0) {
+      auto stage_in = [&](uint32_t k) {
+        const int64_t r0 = row0_of(k);
+        if (r0 < 0) return;
+        issued = k + 1;
+        const int rows = (int)((m - r0) < KC ? (m - r0) : KC);
+        const uint32_t bytes = (uint32_t)rows * (uint32_t)n * 8u;
+        const uint32_t fb = smem_u32(&full[k & 1]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(smem_u32(xst + (k & 1) * XSTAGE)), "l"(src + r0 * lds), "r"(bytes), "r"(fb) : "memory");
+      };
+      if (bulk) {
+        stage_in(0);
+        stage_in(1);
       }
-      uint8_t* dst = sb + (j >> 3) * SBO + ig * LBO + (j & 7) * 16;
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        uint4 w4;
-        w4.x = tc::digit_bf16(F[0], s, sg[0]) | (tc::digit_bf16(F[1], s, sg[1]) << 16);
-        w4.y = tc::digit_bf16(F[2], s, sg[2]) | (tc::digit_bf16(F[3], s, sg[3]) << 16);
-        w4.z = tc::digit_bf16(F[4], s, sg[4]) | (tc::digit_bf16(F[5], s, sg[5]) << 16);
-        w4.w = tc::digit_bf16(F[6], s, sg[6]) | (tc::digit_bf16(F[7], s, sg[7]) << 16);
-        *(uint4*)(dst + plane_off(s)) = w4;
+      for (uint32_t k = 0; row0_of(k) >= 0; ++k) {
+        const int stg = k & 1;
+        const uint32_t q = k % CHUNKS, gi = k / CHUNKS;
+        bool okw = wait_parity(smem_u32(&pfull[stg]), (k >> 1) & 1);  // planes written, staging consumed
+        if (okw && bulk) stage_in(k + 2);
+        if (okw && q == 0 && gi > 0) okw = wait_parity(smem_u32(&tfree), (gi - 1) & 1);  // tiles read back
+        if (!okw || err_sh) {
+          err_sh = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        tc::issue_e<0>(desc(sbase + stg * STAGE), tmem, idesc, q == 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_u32(&bar[stg])) : "memory");
+        committed = k + 1;
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      if (bulk) stage_in(chunk + 2);  // buffer stg is consumed
+  } else {
+    for (uint32_t chunk = 0;; ++chunk) {
+      const int64_t row0 = row0_of(chunk);
+      if (row0 < 0 || err_sh) break;
+      const int rows = (int)((m - row0) < KC ? (m - row0) : KC);
+      const int stg = chunk & 1;
+      bool w = chunk < 2 || wait_parity(smem_u32(&bar[stg]), ((chunk - 2) >> 1) & 1);  // planes free
+      if (w && bulk) w = wait_parity(smem_u32(&full[stg]), (chunk >> 1) & 1);            // rows staged
+      if (!w) {
+        err_sh = 1;
+        break;
+      }
+      uint8_t* sb = stages + stg * STAGE;
+      const double* xs = (const double*)(xst + stg * XSTAGE);
+      // cut the chunk: unit (j, ig) = 8 consecutive rows of column j
+      for (int u = tid; u < NP * (KC / 8); u += THREADS) {
+        const int j = u % NP, ig = u / NP;
+        const int E = Esh[j];
+        unsigned long long F[8];
+        uint32_t sg[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int i = ig * 8 + r;
+          double x = 0.0;
+          if (j < n && i < rows) x = bulk ? xs[i * n + j] : src[(row0 + i) * lds + j];
+          F[r] = tc::fixed56(x, E);
+          sg[r] = (uint32_t)(((unsigned long long)__double_as_longlong(x) >> 48) & 0x8000u);
+        }
+        uint8_t* dst = sb + (j >> 3) * SBO + ig * LBO + (j & 7) * 16;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          uint4 w4;
+          w4.x = tc::digit_bf16(F[0], s, sg[0]) | (tc::digit_bf16(F[1], s, sg[1]) << 16);
+          w4.y = tc::digit_bf16(F[2], s, sg[2]) | (tc::digit_bf16(F[3], s, sg[3]) << 16);
+          w4.z = tc::digit_bf16(F[4], s, sg[4]) | (tc::digit_bf16(F[5], s, sg[5]) << 16);
+          w4.w = tc::digit_bf16(F[6], s, sg[6]) | (tc::digit_bf16(F[7], s, sg[7]) << 16);
+          *(uint4*)(dst + plane_off(s)) = w4;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[stg])) : "memory");
+      if (!group_end(chunk)) continue;
+      // end of a group: all its MMAs (the last commit covers every earlier one)
+      if (!wait_parity(smem_u32(&bar[stg]), (chunk >> 1) & 1)) {
+        err_sh = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      tc::issue_e<0>(desc(sbase + stg * STAGE), tmem, idesc, q == 0);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&bar[stg])) : "memory");
-    }
-    if (q != CHUNKS - 1 && row0_of(chunk + 1) >= 0) continue;
-    // end of a group: all its MMAs (the last commit covers every earlier one)
-    if (!__syncthreads_and(wait_parity(smem_u32(&bar[stg]), (chunk >> 1) & 1))) {
-      ok = false;
-      ++chunk;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!rb_skip) {
-      const uint32_t tq = tmem + ((uint32_t)(32 * qd) << 16) + 32 * h;
+      if (!rb_skip) {
+        const uint32_t tq = tmem + ((uint32_t)(32 * qd) << 16) + CW * h;
 #pragma unroll
-      for (int c = 0; c < 32; c += 16) {
-        // U from tiles 0..3 and T from tiles 4..7 (upper rows); the lower rows
-        // hold d = e + 4: T from tiles 0..3 (tiles 4..7 would be d >= 8)
-        long long U[16], T[16];
+        for (int c = 0; c < CW; c += 8) {
+          // upper rows: U from tiles 0..3, T from tiles 4..7; lower rows hold
+          // d = e + 4: T from tiles 0..3 (tiles 4..7 would be d >= 8).
+          // D_d enters with weight 2^(7 (3 - d)) (U) or 2^(7 (7 - d)) (T).
 #pragma unroll
-        for (int k = 0; k < 16; ++k) U[k] = T[k] = 0;
+          for (int e = 0; e < 8; ++e) {
+            if (!upper && e >= 4) break;
+            uint32_t v[8];
+            tc::ld8(tq + 64 * e + c, v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int d = upper ? e : e + 4;
+            const int sh = d < 4 ? 7 * (3 - d) : 7 * (7 - d);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          if (!upper && e >= 4) break;
-          uint32_t v[16];
-          tc::ld16(tq + 64 * e + c, v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const int d = upper ? e : e + 4;
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const long long dv = (long long)__float2int_rn(__uint_as_float(v[k]));
-            if (d < 4) U[k] = U[k] * 128 + dv;
-            else T[k] = T[k] * 128 + dv;
+            for (int k = 0; k < 8; ++k) {
+              const long long dv = (long long)__float2int_rn(__uint_as_float(v[k])) << sh;
+              if (d < 4) U[c + k] += dv;
+              else T[c + k] += dv;
+            }
           }
         }
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          if (32 * h + c + k < jr) continue;
-          acc[c + k] = fma(0x1p-35, (double)U[k], acc[c + k]);
-          acc[c + k] = fma(0x1p-63, (double)T[k], acc[c + k]);
-        }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&tfree)) : "memory");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // tensor memory is read before the next group overwrites it
   }
-  if (!ok) {
+  __syncthreads();
+  if (err_sh) {
     atomicCAS(&st->status, SCQR3_OK, SCQR3_E_TIMEOUT);
     // let the MMAs and copies already issued finish (bounded) before the memory goes away
-    if (chunk > 0) wait_parity(smem_u32(&bar[(chunk - 1) & 1]), ((chunk - 1) >> 1) & 1);
-    if (bulk && tid == 0)
-      for (uint32_t k = staged; k < issued; ++k) wait_parity(smem_u32(&full[k & 1]), (k >> 1) & 1);
+    if (producer && lane == 0) {
+      if (committed > 0) wait_parity(smem_u32(&bar[(committed - 1) & 1]), ((committed - 1) >> 1) & 1);
+      for (uint32_t k = committed; k < issued; ++k) wait_parity(smem_u32(&full[k & 1]), (k >> 1) & 1);
+    }
   }
 
   // rows 64..127 hold the d + 4 share of the same entries: add them to rows 0..63
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  double* xch = (double*)stages;  // 64 x 64 doubles (32 KB) of stage 0
-  if (!upper) {
+  long long* xch = (long long*)stages;  // 64 x 64 int64 (32 KB) of stage 0
+  if (!producer && !upper) {
 #pragma unroll
-    for (int k = 0; k < 32; ++k) xch[jr * NP + 32 * h + k] = acc[k];
+    for (int k = 0; k < CW; ++k) xch[jr * NP + CW * h + k] = T[k];
   }
   __syncthreads();
-  if (upper && !rb_skip) {
+  if (!producer && upper && !rb_skip) {
     const double sj = sig[jr];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const int col = 32 * h + k;
-      if (col >= jr) part[pk_idx(NP, jr, col)] = (acc[k] + xch[jr * NP + col]) * sj * sig[col];
+    for (int k = 0; k < CW; ++k) {
+      const int col = CW * h + k;
+      if (col >= jr) {
+        const double a = fma(0x1p-35, (double)U[k], 0x1p-63 * (double)(T[k] + xch[jr * NP + col]));
+        part[pk_idx(NP, jr, col)] = a * sj * sig[col];
+      }
     }
   }
   if (tid == 0) part[pk_size(NP)] = 0.0;
@@ -413,7 +441,8 @@ void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_
   // bulk copies need contiguous rows, 16-byte aligned, and chunk sizes that are
   // multiples of 16 bytes (m n even)
   const int bulk = (lds == P.n && ((uintptr_t)src & 15) == 0 && ((P.m * P.n) & 1) == 0) ? 1 : 0;
-  tc_gram_kernel<<<grid, tc::THREADS, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials, part_stride, st, bulk);
+  tc_gram_kernel<<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials, part_stride, st,
+                                                          bulk);
 }
 
 }  // namespace scqr3

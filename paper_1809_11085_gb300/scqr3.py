@@ -181,6 +181,7 @@ def _b_struct(B, normb):
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_TC = 2  # FP64 substitution, Gram matrices on the BF16 tensor cores (exact digit split)
+PREC_MIXED_TC = 3  # the mixed form's substitution with the tensor-core Gram matrices
 ALG_ADAPTIVE = 2  # Alg. 2: shift only on breakdown, stop on the orthogonality test
 ALG_SCQR3 = 3     # Alg. 3: shifted pass, then CholeskyQR2
 

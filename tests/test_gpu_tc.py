@@ -126,3 +126,50 @@ def test_non_finite_and_rejections():
     assert info.status == scqr3.E_NONFINITE
     with pytest.raises(scqr3.ScqrError):
         scqr3.factor(torch.zeros((1000, 65), dtype=torch.float64, device="cuda"), precision=TC)
+
+
+# ------------------------------------------------------------------------------- mixed substitution + TC Gram
+
+UDF = 2.0 ** -48
+
+
+@pytest.mark.parametrize("n", [1, 7, 16, 33, 64])
+@pytest.mark.parametrize("kappa", [1e4, 1e10, 1e15])
+def test_mixed_tc_against_oracle(n, kappa):
+    """PREC_MIXED_TC: the mixed form's FP32-pair substitution (unit roundoff
+    about 2^-48) with the tensor-core Gram matrices; the tolerances are the
+    mixed form's (orthogonality 1e-13, residual 64 n 2^-48, R to 100 n kappa 2^-48)."""
+    m = 30011
+    Xh = testmat(m, n, kappa, seed=6600 + n + int(np.log10(kappa)))
+    Q, R, info = scqr3.factor(torch.from_numpy(Xh).cuda(), precision=scqr3.PREC_MIXED_TC)
+    torch.cuda.synchronize()
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    _, Ro, st, tr = oracle.scqr3(Xh)
+    assert st == 0 and info.status == 0, info
+    assert np.linalg.norm(Q.T @ Q - np.eye(n), 2) <= 1e-13
+    assert np.linalg.norm(Xh - Q @ R) / np.linalg.norm(Xh) <= 64 * max(n, 8) * UDF
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= max(1e-12, 100 * n * kappa * UDF)
+    assert np.array_equal(np.tril(R, -1), np.zeros((n, n))) and (np.diag(R) > 0).all()
+
+
+def test_mixed_tc_alg2_host_and_scale():
+    from paper_1809_11085_gb300.testmat import testmat_torch
+
+    X, _, _ = testmat_torch(1_000_000, 64, 1e10, seed=6700)
+    Q, R, info = scqr3.factor(X, precision=scqr3.PREC_MIXED_TC)
+    Qd, Rd, _ = scqr3.factor(X)
+    torch.cuda.synchronize()
+    assert info.status == 0 and info.passes == 3
+    eye = torch.eye(64, dtype=torch.float64, device="cuda")
+    assert torch.linalg.matrix_norm(Q.T @ Q - eye, 2).item() < 1e-13
+    assert (torch.linalg.matrix_norm(X - Q @ R) / torch.linalg.matrix_norm(X)).item() < 64 * 64 * UDF
+    Xh = testmat(100000, 48, 1e5, seed=6701)
+    Qa, Ra, ia = scqr3.factor(torch.from_numpy(Xh).cuda(), precision=scqr3.PREC_MIXED_TC,
+                              algorithm=scqr3.ALG_ADAPTIVE)
+    torch.cuda.synchronize()
+    assert ia.status == 0 and ia.passes == 2
+    Xp = torch.empty(Xh.shape, dtype=torch.float64, pin_memory=True)
+    Xp.copy_(torch.from_numpy(Xh))
+    Qh, Rh, ih = scqr3.factor_host(Xp, precision=scqr3.PREC_MIXED_TC, algorithm=scqr3.ALG_ADAPTIVE)
+    assert ih.status == 0
+    assert np.array_equal(Qh.numpy(), Qa.cpu().numpy()) and np.array_equal(Rh.numpy(), Ra.cpu().numpy())
