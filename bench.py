@@ -51,14 +51,15 @@ def parse():
     ap.add_argument("--m", type=int, default=16777216)
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--kappa", type=float, default=1e10)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "tc", "mixed_tc"],
-                    help="arithmetic of the timed factorization (mixed: FP32 pairs + FP64; tc: FP64 "
-                         "substitution with the Gram matrices on the BF16 tensor cores, exact digit split)")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "tc", "mixed_tc"],
+                    help="arithmetic of the timed factorization (fp64: FP64 DFMA throughout; tc: FP64 "
+                         "substitution with FP64-accurate Gram matrices from exact digit products on the "
+                         "BF16 tensor cores; mixed: FP32 pairs + FP64; auto: tc for n <= 64, else fp64)")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--legs", default="all", choices=["all", "main", "csr"],
+    ap.add_argument("--legs", default="all", choices=["all", "main", "csr", "none"],
                     help="main: only the headline workload; all: also the other configurations; "
                          "csr: the headline plus the sparse-B leg alone")
     ap.add_argument("--csr-grid", type=int, default=2048,
@@ -98,6 +99,26 @@ def flops_of(m, n, passes):
     each pass is one Gram (n(n+1) flops per row: n(n+1)/2 FMAs) and one
     substitution (n^2 flops per row: n(n-1)/2 FMAs and n multiplications)."""
     return passes * m * (n * (n + 1) + n * n)
+
+
+def tc_gram_roofline(m, n, ms_list):
+    """Tensor-pipe figures of the tensor-core Gram launches: the MMAs it issues
+    per 64-row chunk (104 of M=128, N=64, K=16: 2*128*64*16 flops each) against
+    the measured sustained BF16 peak (the kernel runs inside a long step)."""
+    if not ms_list:
+        return None
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    chunks = (m + 63) // 64
+    issued = chunks * 104 * 2 * 128 * 64 * 16
+    useful = m * 36 * n * n * 2  # the 36 digit pairs with s + t <= 7 of every row's outer product
+    t = statistics.median(ms_list) * 1e-3
+    return {"bound": "tensor", "kernel": "tc_gram_kernel (+ colmax_kernel in the timing)",
+            "achieved": issued / t / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": issued / t / 1e12 / peak,
+            "useful_digit_tflops": useful / t / 1e12, "ms_per_gram": statistics.median(ms_list),
+            "peak_note": "measured sustained bf16 (MEASURED_PEAKS.json)" if peaks else "fallback",
+            "traffic": None}
 
 
 def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True):
@@ -269,8 +290,9 @@ def run_gpu(args, rank, world, local_rank):
     ws = scqr3.Workspace(m, n, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    pname = args.precision if args.precision != "auto" else ("tc" if n <= 64 else "fp64")
     prec = {"fp64": scqr3.PREC_FP64, "mixed": scqr3.PREC_MIXED, "tc": scqr3.PREC_TC,
-            "mixed_tc": scqr3.PREC_MIXED_TC}[args.precision]
+            "mixed_tc": scqr3.PREC_MIXED_TC}[pname]
     for _ in range(args.warmup):
         scqr3.factor(X, Q=Q, workspace=ws, read_info=False, precision=prec)
     torch.cuda.synchronize(dev)
@@ -310,8 +332,14 @@ def run_gpu(args, rank, world, local_rank):
     # dominant kernel: pass_kernel launches that did work
     kflops, kms, kl = 0.0, 0.0, 0
     share = {}
+    tc_gram_ms = []
+    tc_path = prec in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC)
     for kernel, p, t in recs:
         name = scqr3.KERNEL_NAMES.get(kernel, str(kernel))
+        if tc_path and kernel == scqr3.KERNEL_GRAM:
+            name = "tc_gram_kernel (+ colmax_kernel)"
+            if p <= passes - 1:
+                tc_gram_ms.append(t)
         share[name] = share.get(name, 0.0) + t
         f = pass_kernel_flops(m, n, kernel, p, passes,
                               gram_in_pass=prec not in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC))
@@ -328,6 +356,24 @@ def run_gpu(args, rank, world, local_rank):
         return
 
     dgemm = dgemm_tflops(torch, dev)
+
+    # the other forms on the same X, one step each (after a warm-up)
+    forms = {}
+    if args.legs != "none":
+        Rref = R.clone()
+        for fname, fp in (("fp64", scqr3.PREC_FP64), ("tc", scqr3.PREC_TC), ("mixed", scqr3.PREC_MIXED),
+                          ("mixed_tc", scqr3.PREC_MIXED_TC)):
+            if fp == prec or (n > 64 and fp in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC)):
+                continue
+            fms = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, workspace=ws, read_info=False, precision=fp),
+                        reps=2)
+            _, Rf, finf = scqr3.factor(X, Q=Q, workspace=ws, precision=fp)
+            forms[fname] = {"ms": round(fms, 2), "rows_per_s": m / (fms * 1e-3), "passes": finf.passes,
+                            "orth": _orth(torch, Q),
+                            "resid": (torch.linalg.matrix_norm(X - Q @ Rf) / torch.linalg.matrix_norm(X)).item(),
+                            "dR_vs_headline": (torch.linalg.matrix_norm(Rf - Rref) /
+                                               torch.linalg.matrix_norm(Rref)).item()}
+        # restore the headline's Q for nothing else: the e2e leg has its own buffers
 
     # e2e: pinned host X -> device, factorization, Q and R -> pinned host, every step
     e2e = None
@@ -372,11 +418,11 @@ def run_gpu(args, rank, world, local_rank):
             sig = repeated_small_sigma(n, 8, 1e-14, 1e7) if kk == "repeated" else None
             Xs, _, _ = testmat_torch(m, n, 0.0 if sig is not None else kk, seed=1150 + len(sweep),
                                      device=dev, sigma=sig)
-            scqr3.factor(Xs, Q=Q, workspace=ws, read_info=False)
+            scqr3.factor(Xs, Q=Q, workspace=ws, read_info=False, precision=prec)
             torch.cuda.synchronize(dev)
             g0, g1 = torch.cuda.Event(True), torch.cuda.Event(True)
             g0.record(stream)
-            _, Rs, inf = scqr3.factor(Xs, Q=Q, workspace=ws, read_info=False)
+            _, Rs, inf = scqr3.factor(Xs, Q=Q, workspace=ws, read_info=False, precision=prec)
             g1.record(stream)
             torch.cuda.synchronize(dev)
             inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
@@ -406,18 +452,28 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "sCQR3 FP64, X = U diag(sigma) V^T, %d x %d, kappa=%g" % (m, n, kappa),
+        "dtype_note": {"fp64": "FP64 throughout",
+                       "tc": "FP64 substitution, Cholesky and accumulation; Gram digit products exact "
+                             "(7-bit integers in BF16, sums below 2^24 in FP32, folded in int64)",
+                       "mixed": "FP32 pairs for Gram and substitution, FP64 shift/Cholesky/accumulation",
+                       "mixed_tc": "FP32-pair substitution, exact tensor-core Gram"}[pname],
+        "config": {"workload": "sCQR3, X = U diag(sigma) V^T, %d x %d, kappa=%g, precision=%s" % (m, n, kappa, pname),
                    "m": m, "n": n, "kappa": kappa, "passes": passes, "shifted": info.shifted,
                    "l2": "inputs (%.1f GB) larger than the 129 MB L2; no flush" % (m * n * 8 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "alu", "kernel": "pass_kernel<64> (FP64 DFMA)",
+        "roofline": {"bound": "alu",
+                     "kernel": "pass_kernel<64> (FP64 DFMA%s)" % (", substitution only" if tc_path else ""),
                      "achieved": achieved, "peak": FP64_PEAK_DERIVED_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_DERIVED_TFLOPS) if achieved else None,
-                     "traffic": profiled_traffic(m, n), "traffic_note":
-                         "DRAM bytes of one fused solve+Gram launch (ncu, scaled by rows)",
+                     "traffic": None if tc_path else profiled_traffic(m, n), "traffic_note":
+                         "DRAM bytes of one fused solve+Gram launch (ncu, scaled by rows); null for the "
+                         "substitution-only launches of the tensor-core forms",
                      "launches_timed": kl,
                      "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; cuBLAS DGEMM measured beside it",
                      "cublas_dgemm_tflops": dgemm},
+        "precision": pname,
+        "roofline_tc_gram": tc_gram_roofline(m, n, tc_gram_ms) if tc_path else None,
+        "forms": forms,
         "path_tflops": fl / (ms * 1e-3) / 1e12,
         "gflops_6mn2": 6 * m * n * n / (ms * 1e-3) / 1e9,
         "kernel_share": {k: round(v / tot, 4) for k, v in share.items()},
