@@ -51,6 +51,8 @@
 // and frees its tensor memory.
 #include "fp64_device.cuh"
 
+#include <cuda_bf16.h>
+
 namespace scqr3 {
 
 namespace tc {
@@ -142,43 +144,69 @@ __device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr) : "memory");
 }
 
-// BF16 bit pattern of seven-bit digit s of F, with the sign bit `sign`. The
-// integer becomes a float exactly as (2^23 + a) - 2^23 (one full-rate FP32 add
-// instead of a quarter-rate conversion); a < 128 has at most 7 significant
-// bits, so its BF16 pattern is the top half of the float's.
-__device__ __forceinline__ uint32_t digit_bf16(unsigned long long F, int s, uint32_t sign) {
-  const uint32_t a = (uint32_t)((F >> (49 - 7 * s)) & 127u);
-  const float f = __fsub_rn(__uint_as_float(0x4B000000u | a), 8388608.0f);
-  return (__float_as_uint(f) >> 16) | sign;
+// Digit s of two entries (rows r and r + 1 of a column) as a BF16 pair with
+// their signs (bits 15 and 31 of `signs`). The digits a, b < 128 are placed
+// side by side and ORed into the BF16 pattern of 128 (0x4300): that is the
+// exact BF16 value 128 + a, since BF16 resolves units between 128 and 256;
+// one exact BF16x2 subtraction of 128 leaves a and b.
+template <int S>
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long F0, unsigned long long F1, uint32_t signs) {
+  const uint32_t lo = (uint32_t)(F0 >> (49 - 7 * S)), hi = (uint32_t)(F1 >> (49 - 7 * S));
+  uint32_t w = (__byte_perm(lo, hi, 0x5410) & 0x007F007Fu) | 0x43004300u;
+  __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&w);
+  v = __hsub2(v, __floats2bfloat162_rn(128.0f, 128.0f));
+  return *reinterpret_cast<uint32_t*>(&v) | signs;
+}
+
+template <int S>
+__device__ __forceinline__ void store_plane(uint8_t* dst, const unsigned long long (&F)[8], const uint32_t (&sp)[4]) {
+  uint4 w4;
+  w4.x = digit_pair<S>(F[0], F[1], sp[0]);
+  w4.y = digit_pair<S>(F[2], F[3], sp[1]);
+  w4.z = digit_pair<S>(F[4], F[5], sp[2]);
+  w4.w = digit_pair<S>(F[6], F[7], sp[3]);
+  *(uint4*)(dst + plane_off(S)) = w4;
 }
 
 }  // namespace tc
 
-// Column scales: colmax[j] = max_i |q_ij| (as the bit pattern of a double;
-// +inf if a non-finite entry is seen) over rows [0, m) of src.
+// Column scales: colmax[j] = max_i |q_ij| as the bit pattern of a double (the
+// patterns of non-negative doubles order like the numbers; an Inf or NaN
+// entry, exponent field all ones, orders above every finite one, so
+// colmax[j] is then non-finite) over rows [0, m) of src. Integer operations
+// only: the FP64 pipe is the slow one.
 __global__ void __launch_bounds__(256)
 colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int pass,
               unsigned long long* __restrict__ colmax, const DevState* __restrict__ st) {
   if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
-  __shared__ double red[256];
+  __shared__ unsigned long long red[256];
   const int tid = threadIdx.x;
   const int j = tid % 64, r0 = tid / 64;
-  double mx = 0.0;
-  bool bad = false;
+  const unsigned long long* s64 = reinterpret_cast<const unsigned long long*>(src);
+  constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+  unsigned long long mx = 0;
   if (j < n) {
-    for (int64_t i = (int64_t)blockIdx.x * 4 + r0; i < m; i += (int64_t)gridDim.x * 4) {
-      const double v = src[i * lds + j];
-      if (!isfinite(v)) bad = true;
-      mx = fmax(mx, fabs(v));
+    // 8 rows per thread in flight: the scan is bound by memory latency otherwise
+    const int64_t step = (int64_t)gridDim.x * 4;
+    int64_t i = (int64_t)blockIdx.x * 4 + r0;
+    for (; i + 7 * step < m; i += 8 * step) {
+      unsigned long long v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = s64[(i + u * step) * lds + j];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) mx = mx > (v[u] & ABS) ? mx : (v[u] & ABS);
+    }
+    for (; i < m; i += step) {
+      const unsigned long long v = s64[i * lds + j] & ABS;
+      mx = mx > v ? mx : v;
     }
   }
-  red[tid] = bad ? INFINITY : mx;
+  red[tid] = mx;
   __syncthreads();
   if (tid < 64 && j < n) {
-    double b = fmax(fmax(red[tid], red[tid + 64]), fmax(red[tid + 128], red[tid + 192]));
-    if (red[tid] == INFINITY || red[tid + 64] == INFINITY || red[tid + 128] == INFINITY || red[tid + 192] == INFINITY)
-      b = INFINITY;
-    atomicMax(&colmax[j], (unsigned long long)__double_as_longlong(b));  // non-negative doubles order as bits
+    unsigned long long b = red[tid];
+    for (int q = 1; q < 4; ++q) b = b > red[tid + 64 * q] ? b : red[tid + 64 * q];
+    atomicMax(&colmax[j], b);
   }
 }
 
@@ -329,25 +357,25 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
         const int j = u % NP, ig = u / NP;
         const int E = Esh[j];
         unsigned long long F[8];
-        uint32_t sg[8];
+        uint32_t sp[4] = {0u, 0u, 0u, 0u};  // sign bits of rows 2p (bit 15) and 2p + 1 (bit 31)
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           const int i = ig * 8 + r;
           double x = 0.0;
           if (j < n && i < rows) x = bulk ? xs[i * n + j] : src[(row0 + i) * lds + j];
           F[r] = tc::fixed56(x, E);
-          sg[r] = (uint32_t)(((unsigned long long)__double_as_longlong(x) >> 48) & 0x8000u);
+          const uint32_t hiw = (uint32_t)((unsigned long long)__double_as_longlong(x) >> 32);
+          sp[r >> 1] |= (r & 1) ? (hiw & 0x80000000u) : ((hiw >> 16) & 0x8000u);
         }
         uint8_t* dst = sb + (j >> 3) * SBO + ig * LBO + (j & 7) * 16;
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          uint4 w4;
-          w4.x = tc::digit_bf16(F[0], s, sg[0]) | (tc::digit_bf16(F[1], s, sg[1]) << 16);
-          w4.y = tc::digit_bf16(F[2], s, sg[2]) | (tc::digit_bf16(F[3], s, sg[3]) << 16);
-          w4.z = tc::digit_bf16(F[4], s, sg[4]) | (tc::digit_bf16(F[5], s, sg[5]) << 16);
-          w4.w = tc::digit_bf16(F[6], s, sg[6]) | (tc::digit_bf16(F[7], s, sg[7]) << 16);
-          *(uint4*)(dst + plane_off(s)) = w4;
-        }
+        tc::store_plane<0>(dst, F, sp);
+        tc::store_plane<1>(dst, F, sp);
+        tc::store_plane<2>(dst, F, sp);
+        tc::store_plane<3>(dst, F, sp);
+        tc::store_plane<4>(dst, F, sp);
+        tc::store_plane<5>(dst, F, sp);
+        tc::store_plane<6>(dst, F, sp);
+        tc::store_plane<7>(dst, F, sp);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[stg])) : "memory");
