@@ -36,10 +36,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sCQR3 rows/s & % roofline at m×n; mixed/batched vs FP64 at ‖QᵀQ−I‖≤1e-13"
 FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
-# DRAM bytes per row of a fused solve+Gram launch of pass_kernel<64>, from the ncu capture
-# summarised in profiles/pass_kernel_fp64_1048576x64_full.md; valid only for that kernel source.
-PROFILED_KERNEL_SHA = "f9f2d688afe16ef4"
-PROFILED_BYTES_PER_ROW = 991.7
+# DRAM bytes per row of a pass_kernel<64> launch, fused solve+Gram and substitution only, from
+# the ncu captures summarised in profiles/pass_kernel_fp64_1048576x64_full.md; valid only for
+# that kernel source.
+PROFILED_KERNEL_SHA = "b447e14d15d0797f"
+PROFILED_BYTES_PER_ROW = 992.3
+PROFILED_SOLVE_BYTES_PER_ROW = 968.7
 
 
 def parse():
@@ -67,8 +69,8 @@ def parse():
     return ap.parse_args()
 
 
-def profiled_traffic(m, n):
-    """roofline.traffic for a fused launch, or None if the kernel changed since the capture."""
+def profiled_traffic(m, n, solve_only=False):
+    """roofline.traffic of a pass_kernel<64> launch, or None if the kernel changed since the capture."""
     import hashlib
 
     h = hashlib.sha256()
@@ -77,7 +79,7 @@ def profiled_traffic(m, n):
     sha = h.hexdigest()[:16]
     if sha != PROFILED_KERNEL_SHA or n != 64:
         return None
-    return PROFILED_BYTES_PER_ROW * m
+    return (PROFILED_SOLVE_BYTES_PER_ROW if solve_only else PROFILED_BYTES_PER_ROW) * m
 
 
 def max_over_ranks(ms, dist, device):
@@ -465,9 +467,9 @@ def run_gpu(args, rank, world, local_rank):
                      "kernel": "pass_kernel<64> (FP64 DFMA%s)" % (", substitution only" if tc_path else ""),
                      "achieved": achieved, "peak": FP64_PEAK_DERIVED_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_DERIVED_TFLOPS) if achieved else None,
-                     "traffic": None if tc_path else profiled_traffic(m, n), "traffic_note":
-                         "DRAM bytes of one fused solve+Gram launch (ncu, scaled by rows); null for the "
-                         "substitution-only launches of the tensor-core forms",
+                     "traffic": profiled_traffic(m, n, solve_only=tc_path), "traffic_note":
+                         "DRAM bytes of one %s launch (ncu at 1048576 rows, scaled by rows)"
+                         % ("substitution-only" if tc_path else "fused solve+Gram"),
                      "launches_timed": kl,
                      "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; cuBLAS DGEMM measured beside it",
                      "cublas_dgemm_tflops": dgemm},
