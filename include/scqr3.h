@@ -80,7 +80,7 @@ extern "C" {
  * the paper. n <= 64 and B = NULL. */
 #define SCQR3_PREC_TC 2
 /* The mixed form's substitution (FP32 pairs) with the Gram matrices of
- * SCQR3_PREC_TC; the iterates are kept in FP64 between passes. n <= 64 and
+ * SCQR3_PREC_TC, read directly from the float-pair iterates. n <= 64 and
  * B = NULL. Not in the paper. */
 #define SCQR3_PREC_MIXED_TC 3
 

@@ -106,8 +106,8 @@ df_pass_kernel(const double* src, int64_t lds, double* dst, int64_t ldd, Params 
     do_trsm = true;
     do_gram = st->gram_after[pass] != 0 && !P.solve_only;
   }
-  const bool src_fp64 = pass <= 0 || P.solve_only;  // solve-only: FP64 iterates between passes
-  const bool dst_fp64 = !do_gram;
+  const bool src_fp64 = pass <= 0;
+  const bool dst_fp64 = pass >= 0 && !st->gram_after[pass];  // pairs while another pass follows
   const float2* srcf = reinterpret_cast<const float2*>(src);
   float2* dstf = reinterpret_cast<float2*>(dst);
 
@@ -274,8 +274,8 @@ df2_pass_kernel(const double* src, int64_t lds, double* dst, int64_t ldd, Params
     do_trsm = true;
     do_gram = st->gram_after[pass] != 0 && !P.solve_only;
   }
-  const bool src_fp64 = pass <= 0 || P.solve_only;  // solve-only: FP64 iterates between passes
-  const bool dst_fp64 = !do_gram;
+  const bool src_fp64 = pass <= 0;
+  const bool dst_fp64 = pass >= 0 && !st->gram_after[pass];  // pairs while another pass follows
   const float2* srcf = reinterpret_cast<const float2*>(src);
   float2* dstf = reinterpret_cast<float2*>(dst);
 
@@ -445,8 +445,8 @@ dfp_pass_kernel(const double* src, int64_t lds, double* dst, int64_t ldd, Params
     do_trsm = true;
     do_gram = st->gram_after[pass] != 0 && !P.solve_only;
   }
-  const bool src_fp64 = pass <= 0 || P.solve_only;  // solve-only: FP64 iterates between passes
-  const bool dst_fp64 = !do_gram;
+  const bool src_fp64 = pass <= 0;
+  const bool dst_fp64 = pass >= 0 && !st->gram_after[pass];  // pairs while another pass follows
   const float2* srcf = reinterpret_cast<const float2*>(src);
   float2* dstf = reinterpret_cast<float2*>(dst);
   if (do_trsm && tid < NP) rinv[tid] = df_split(1.0 / rk[pk_row(NP, tid)]);

@@ -50,7 +50,7 @@ void launch_csr_gram(int np, int grid, cudaStream_t s, const double* src, int64_
 cudaError_t tc_setup();
 int tc_groups(int64_t m);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
-                    unsigned long long* colmax, double* partials, int part_stride, DevState* st);
+                    unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs);
 
 namespace {
 
@@ -473,7 +473,7 @@ int first_gram(Call& c, const double* X, int64_t ldx, int64_t r0, int64_t r1, in
   if (c.tc) {
     const int g0 = tc_groups(Pc.m);
     const int g = g0 < sm_count() ? (g0 < 1 ? 1 : g0) : sm_count();
-    launch_tc_gram(g, sm_count(), c.s, src, ldx, Pc, -1, c.colmax, part, c.L.part_stride, c.st);
+    launch_tc_gram(g, sm_count(), c.s, src, ldx, Pc, -1, c.colmax, part, c.L.part_stride, c.st, 0);
     return g;
   }
   if (c.csr) {  // the whole matrix only: rows reach across any split
@@ -535,7 +535,9 @@ void after_pass(Call& c, int k, const double* Q, int64_t ldq) {
     launch_gram256(c.grid, c.s, Q, ldq, c.P, k, c.partials, c.L.part_stride, c.st);
   } else if (c.tc) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
-    launch_tc_gram(c.L.tc_grid, sm_count(), c.s, Q, ldq, c.P, k, c.colmax, c.partials, c.L.part_stride, c.st);
+    // the mixed form keeps float pairs between passes
+    launch_tc_gram(c.L.tc_grid, sm_count(), c.s, Q, ldq, c.P, k, c.colmax, c.partials, c.L.part_stride, c.st,
+                   c.mixed ? 1 : 0);
   } else if (c.csr) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     launch_csr_gram(c.P.np, c.L.csr_grid, c.s, Q, ldq, c.P, k, c.B, c.partials, c.L.part_stride, c.st);
@@ -586,7 +588,7 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
     solve_rows(c, k, k == 0 ? X : Q, k == 0 ? ldx : ldq, Q, ldq, 0, m);
     if (k + 1 < c.P.max_passes) after_pass(c, k, Q, ldq);
   }
-  if (c.mixed && !c.P.solve_only) {  // float pairs may remain only when the solves fuse the Gram
+  if (c.mixed) {  // float pairs remain when the last solve was followed by a Gram step
     tick(c.s, SCQR3_KERNEL_FINISH, -1);
     launch_df_finish(sm_count() * 4, c.s, Q, ldq, m, n, c.P.max_passes, c.st);
   }
@@ -712,7 +714,7 @@ extern "C" int scqr3_factor_host(const double* X, int64_t m, int n, int64_t ldx,
     break;
   }
   if (!copied) {  // stopped by Alg. 2's test or a failure: Q as the device left it
-    if (c.mixed && !c.P.solve_only) {
+    if (c.mixed) {
       tick(s, SCQR3_KERNEL_FINISH, -1);
       launch_df_finish(sm_count() * 4, s, Qdev, n, m, n, c.P.max_passes, c.st);
     }

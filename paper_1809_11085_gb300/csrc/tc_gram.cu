@@ -144,6 +144,25 @@ __device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr) : "memory");
 }
 
+// The same for an element held as a float pair (hi, lo), value hi + lo (the
+// mixed form's iterates; hi in the low word). Each float becomes its own
+// fixed-point integer and the two are added as signed integers, so no FP64
+// arithmetic is needed; E must leave |hi + lo| < 2^E. Returns |F| and sets the
+// sign bit (bit 31) in *sign.
+__device__ __forceinline__ long long fix_float(uint32_t f, int E) {
+  int ex = (int)((f >> 23) & 0xFF);
+  long long mant = (long long)(f & 0x7FFFFFu);
+  if (ex) mant |= 0x800000ll; else ex = 1;
+  const int sh = ex - 94 - E;  // value mant 2^(ex - 150), times 2^(56 - E)
+  const long long F = sh >= 0 ? (sh <= 32 ? (mant << sh) : 0x7FFFFFFFFFFFFFll) : (sh > -40 ? (mant >> -sh) : 0ll);
+  return (f & 0x80000000u) ? -F : F;
+}
+__device__ __forceinline__ unsigned long long fixed56_pair(unsigned long long bits, int E, uint32_t* sign) {
+  const long long S = fix_float((uint32_t)bits, E) + fix_float((uint32_t)(bits >> 32), E);
+  *sign = S < 0 ? 0x80000000u : 0u;
+  return (unsigned long long)(S < 0 ? -S : S);
+}
+
 // Digit s of two entries (rows r and r + 1 of a column) as a BF16 pair with
 // their signs (bits 15 and 31 of `signs`). The digits a, b < 128 are placed
 // side by side and ORed into the BF16 pattern of 128 (0x4300): that is the
@@ -170,20 +189,22 @@ __device__ __forceinline__ void store_plane(uint8_t* dst, const unsigned long lo
 
 }  // namespace tc
 
-// Column scales: colmax[j] = max_i |q_ij| as the bit pattern of a double (the
+// Column scales: colmax[j] = max_i |q_ij| (pairs: max_i |hi_ij|) as the bit pattern of a double (the
 // patterns of non-negative doubles order like the numbers; an Inf or NaN
 // entry, exponent field all ones, orders above every finite one, so
 // colmax[j] is then non-finite) over rows [0, m) of src. Integer operations
 // only: the FP64 pipe is the slow one.
 __global__ void __launch_bounds__(256)
 colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int pass,
-              unsigned long long* __restrict__ colmax, const DevState* __restrict__ st) {
+              unsigned long long* __restrict__ colmax, const DevState* __restrict__ st, int pairs) {
   if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
   __shared__ unsigned long long red[256];
   const int tid = threadIdx.x;
   const int j = tid % 64, r0 = tid / 64;
   const unsigned long long* s64 = reinterpret_cast<const unsigned long long*>(src);
-  constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+  // pairs: the max of |hi| (the float's pattern in the low word; the Gram
+  // kernel widens the scale by one bit for lo)
+  const unsigned long long ABS = pairs ? 0x7FFFFFFFull : 0x7FFFFFFFFFFFFFFFull;
   unsigned long long mx = 0;
   if (j < n) {
     // 8 rows per thread in flight: the scan is bound by memory latency otherwise
@@ -206,6 +227,11 @@ colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int
   if (tid < 64 && j < n) {
     unsigned long long b = red[tid];
     for (int q = 1; q < 4; ++q) b = b > red[tid + 64 * q] ? b : red[tid + 64 * q];
+    if (pairs) {  // the float's value as a double pattern (Inf/NaN: +Inf)
+      const uint32_t fb = (uint32_t)b;
+      b = ((fb >> 23) & 0xFF) == 0xFF ? 0x7FF0000000000000ull
+                                      : (unsigned long long)__double_as_longlong((double)__uint_as_float(fb));
+    }
     atomicMax(&colmax[j], b);
   }
 }
@@ -213,7 +239,7 @@ colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int
 __global__ void __launch_bounds__(tc::THREADS + 32, 1)
 tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
                const unsigned long long* __restrict__ colmax, double* __restrict__ partials, int part_stride,
-               DevState* __restrict__ st, int bulk) {
+               DevState* __restrict__ st, int bulk, int pairs) {
   using namespace tc;
   if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
   extern __shared__ uint8_t dsm[];
@@ -243,7 +269,7 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
         bad = 1;  // non-finite input: the Gram matrix is NaN
       } else if (cm > 0.0) {
         const int ex = (int)((colmax[tid] >> 52) & 0x7FF);
-        E = (ex ? ex : 1) - 1023 + 1;  // cm < 2^E
+        E = (ex ? ex : 1) - 1023 + 1 + pairs;  // cm < 2^E (pairs: |hi + lo| < 2^E)
         sg = ldexp(1.0, E);
       }
     }
@@ -363,9 +389,14 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
           const int i = ig * 8 + r;
           double x = 0.0;
           if (j < n && i < rows) x = bulk ? xs[i * n + j] : src[(row0 + i) * lds + j];
-          F[r] = tc::fixed56(x, E);
-          const uint32_t hiw = (uint32_t)((unsigned long long)__double_as_longlong(x) >> 32);
-          sp[r >> 1] |= (r & 1) ? (hiw & 0x80000000u) : ((hiw >> 16) & 0x8000u);
+          uint32_t sgn;
+          if (pairs) {
+            F[r] = tc::fixed56_pair((unsigned long long)__double_as_longlong(x), E, &sgn);
+          } else {
+            F[r] = tc::fixed56(x, E);
+            sgn = (uint32_t)((unsigned long long)__double_as_longlong(x) >> 32) & 0x80000000u;
+          }
+          sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
         }
         uint8_t* dst = sb + (j >> 3) * SBO + ig * LBO + (j & 7) * 16;
         tc::store_plane<0>(dst, F, sp);
@@ -460,17 +491,17 @@ int tc_groups(int64_t m) { return (int)((m + tc::KC * tc::CHUNKS - 1) / (tc::KC 
 
 // Column scales then the tensor-core Gram of rows [0, P.m) of src into `grid` slots.
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
-                    unsigned long long* colmax, double* partials, int part_stride, DevState* st) {
+                    unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs) {
   if (P.np != tc::NP || part_stride != pk_size(tc::NP) + 1) return;  // the slots hold the 64-column layout
   cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * tc::NP, s);
   const int64_t want = (P.m + 3) / 4;
   const int cg = (int)(want < (int64_t)sms * 8 ? (want < 1 ? 1 : want) : (int64_t)sms * 8);
-  colmax_kernel<<<cg, 256, 0, s>>>(src, lds, P.m, P.n, pass, colmax, st);
+  colmax_kernel<<<cg, 256, 0, s>>>(src, lds, P.m, P.n, pass, colmax, st, pairs);
   // bulk copies need contiguous rows, 16-byte aligned, and chunk sizes that are
   // multiples of 16 bytes (m n even)
   const int bulk = (lds == P.n && ((uintptr_t)src & 15) == 0 && ((P.m * P.n) & 1) == 0) ? 1 : 0;
   tc_gram_kernel<<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials, part_stride, st,
-                                                          bulk);
+                                                          bulk, pairs);
 }
 
 }  // namespace scqr3
