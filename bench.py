@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "tc", "mixed_tc"],
                     help="arithmetic of the timed factorization (fp64: FP64 DFMA throughout; tc: FP64 "
                          "substitution with FP64-accurate Gram matrices from exact digit products on the "
-                         "BF16 tensor cores; mixed: FP32 pairs + FP64; auto: tc for n <= 64, else fp64)")
+                         "BF16 tensor cores; mixed: FP32 pairs + FP64; auto: tc for n <= 128, else fp64)")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -292,7 +292,7 @@ def run_gpu(args, rank, world, local_rank):
     ws = scqr3.Workspace(m, n, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    pname = args.precision if args.precision != "auto" else ("tc" if n <= 64 else "fp64")
+    pname = args.precision if args.precision != "auto" else ("tc" if n <= 128 else "fp64")
     prec = {"fp64": scqr3.PREC_FP64, "mixed": scqr3.PREC_MIXED, "tc": scqr3.PREC_TC,
             "mixed_tc": scqr3.PREC_MIXED_TC}[pname]
     for _ in range(args.warmup):
@@ -571,28 +571,31 @@ def extra_legs(torch, dev, stream, args):
         free()
     legs["scaleup_n256"] = {"workload": "FP64 sCQR3, X = U diag(sigma) V^T, 1048576 x 256", "kappa": sweep}
 
-    # mixed form vs FP64 on the same matrices
+    # mixed and tensor-core forms vs FP64 on the same matrices
     mixed = {}
     for (mm, nn, kk) in ((16777216, 64, 1e10), (8388608, 128, 1e4), (8388608, 128, 1e7), (8388608, 128, 1e10)):
         X, _, _ = testmat_torch(mm, nn, kk, seed=1400 + nn, device=dev)
         Q = torch.empty_like(X)
         ws = scqr3.Workspace(mm, nn, device=dev)
         R64 = torch.empty((nn, nn), dtype=torch.float64, device=dev)
-        Rmx = torch.empty_like(R64)
+        Rf = torch.empty_like(R64)
         t64 = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, R=R64, workspace=ws, read_info=False))
-        o64 = _orth(torch, Q)
-        tmx = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, R=Rmx, workspace=ws, read_info=False,
-                                                        precision=scqr3.PREC_MIXED))
-        inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
-        res = (torch.linalg.matrix_norm(X - Q @ Rmx) / torch.linalg.matrix_norm(X)).item()
-        dR = (torch.linalg.matrix_norm(Rmx - R64) / torch.linalg.matrix_norm(R64)).item()
-        mixed["%dx%d_kappa%g" % (mm, nn, kk)] = {
-            "fp64_ms": round(t64, 2), "mixed_ms": round(tmx, 2), "speedup": t64 / tmx,
-            "mixed_rows_per_s": mm / (tmx * 1e-3), "orth_fp64": o64, "orth_mixed": _orth(torch, Q),
-            "resid_mixed": res, "dR_vs_fp64": dR, "passes": inf.passes}
+        row = {"fp64_ms": round(t64, 2), "orth_fp64": _orth(torch, Q)}
+        for fname, fp in (("mixed", scqr3.PREC_MIXED), ("mixed_tc", scqr3.PREC_MIXED_TC), ("tc", scqr3.PREC_TC)):
+            t = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, R=Rf, workspace=ws, read_info=False,
+                                                          precision=fp))
+            inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
+            row[fname] = {
+                "ms": round(t, 2), "rows_per_s": mm / (t * 1e-3), "speedup_vs_fp64": t64 / t,
+                "orth": _orth(torch, Q),
+                "resid": (torch.linalg.matrix_norm(X - Q @ Rf) / torch.linalg.matrix_norm(X)).item(),
+                "dR_vs_fp64": (torch.linalg.matrix_norm(Rf - R64) / torch.linalg.matrix_norm(R64)).item(),
+                "passes": inf.passes, "status": inf.status}
+        mixed["%dx%d_kappa%g" % (mm, nn, kk)] = row
         del X, Q, ws
         free()
-    legs["mixed"] = {"workload": "same X through precision=FP64 and precision=MIXED (FP32 pairs + FP64)",
+    legs["mixed"] = {"workload": "same X through precision FP64, MIXED (FP32 pairs + FP64), MIXED_TC (FP32 pairs "
+                                 "+ tensor-core Gram) and TC (FP64 substitution + tensor-core Gram)",
                      "results": mixed}
 
     # oblique inner product, block-diagonal B (8 x 8 blocks G^T G + 0.1 I)

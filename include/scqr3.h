@@ -74,14 +74,14 @@ extern "C" {
  * through an exact fixed-point split: each column is scaled by a power of two
  * above its largest entry and cut into eight 7-bit digits, every digit
  * product is exact, sums of 256 rows are exact in the FP32 accumulator, and
- * the digit-pair sums are combined in FP64. The Gram error is below about
+ * the digit-pair sums are combined in int64. The Gram error is below about
  * m 2^-55 sigma_j sigma_k, within the norm-wise bound that the shift of
  * Eq. (finds2) covers, so results match the FP64 form to rounding. Not in
- * the paper. n <= 64 and B = NULL. */
+ * the paper. n <= 128, m <= 2^31 and B = NULL (else SCQR3_E_UNSUPPORTED). */
 #define SCQR3_PREC_TC 2
 /* The mixed form's substitution (FP32 pairs) with the Gram matrices of
- * SCQR3_PREC_TC, read directly from the float-pair iterates. n <= 64 and
- * B = NULL. Not in the paper. */
+ * SCQR3_PREC_TC, read directly from the float-pair iterates. n <= 128,
+ * m <= 2^31 and B = NULL. Not in the paper. */
 #define SCQR3_PREC_MIXED_TC 3
 
 /* Oblique inner product (x, y)_B = x^T B y of Sec. 5, for SPD B given

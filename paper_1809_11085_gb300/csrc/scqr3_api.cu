@@ -48,11 +48,14 @@ void launch_csr_check(int grid, cudaStream_t s, int64_t m, const scqr3_B* B, Dev
 void launch_csr_gram(int np, int grid, cudaStream_t s, const double* src, int64_t lds, const Params& P,
                      int pass, const scqr3_B* B, double* partials, int part_stride, const DevState* st);
 cudaError_t tc_setup();
-int tc_groups(int64_t m);
+int tc_grid(int64_t m, int np, int sms);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs);
 
 namespace {
+
+// The tensor-core Gram works on blocks of 64 columns.
+int tc_np(int n) { return n <= 64 ? 64 : 128; }
 
 int padded_n(int n) {
   if (n <= 16) return 16;
@@ -168,9 +171,9 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
       opts->precision != SCQR3_PREC_TC && opts->precision != SCQR3_PREC_MIXED_TC)
     return -12;
   const bool tcp = opts && (opts->precision == SCQR3_PREC_TC || opts->precision == SCQR3_PREC_MIXED_TC);
-  // tensor-core Gram: n <= 64, B = I, and at most 2^31 rows (its exact int64
+  // tensor-core Gram: n <= 128, B = I, and at most 2^31 rows (its exact int64
   // digit-sum accumulators)
-  if (tcp && (B || n > 64 || m > ((int64_t)1 << 31))) return SCQR3_E_UNSUPPORTED;
+  if (tcp && (B || n > 128 || m > ((int64_t)1 << 31))) return SCQR3_E_UNSUPPORTED;
   if (opts && opts->precision == SCQR3_PREC_MIXED && B) return -5;  // mixed form: B = I only
   if (opts && opts->algorithm != 0 && opts->algorithm != SCQR3_ALG_SCQR3 &&
       opts->algorithm != SCQR3_ALG_ADAPTIVE)
@@ -197,7 +200,7 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
                     PassGeom* geo) {
   const bool mixed = prec == SCQR3_PREC_MIXED || prec == SCQR3_PREC_MIXED_TC;
   const bool tcg = prec == SCQR3_PREC_TC || prec == SCQR3_PREC_MIXED_TC;
-  const int np = tcg ? 64 : padded_n(n);  // the tensor-core Gram works on 64 columns
+  const int np = tcg ? tc_np(n) : padded_n(n);
   int grid_max = 0;
   if (device_geo(np, &grid_max, geo) != cudaSuccess) return SCQR3_E_CUDA;
   const int64_t npanels = (m + geo->pr - 1) / geo->pr;
@@ -230,8 +233,7 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
   // the tensor-core Gram's slots and column scales are always reserved, so
   // one workspace serves every precision of a shape
   {
-    const int g = tc_groups(m);
-    L->tc_grid = g < sms ? (g < 1 ? 1 : g) : sms;
+    L->tc_grid = tc_grid(m, np <= 64 ? 64 : 128, sms);
     if (L->tc_grid > slots_alloc) slots_alloc = L->tc_grid;
     if (tcg) L->n_partials = L->tc_grid;
   }
@@ -253,8 +255,7 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
     const int64_t cr = host_chunk_rows(m);
     for (int64_t r0 = 0; r0 < m; r0 += cr) {
       const int64_t rows = (m - r0) < cr ? (m - r0) : cr;
-      const int g = tc_groups(rows);
-      ftc += g < sms ? (g < 1 ? 1 : g) : sms;
+      ftc += tc_grid(rows, np <= 64 ? 64 : 128, sms);
       if (np == 256) {
         f64 += grid64;
       } else {
@@ -275,7 +276,7 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
     off = align256(off + sizeof(scqr3_info));
   }
   L->colmax = off;
-  off = align256(off + sizeof(unsigned long long) * 64);
+  off = align256(off + sizeof(unsigned long long) * 128);
   L->lt = off;
   if (B && B->bs > 0) {
     const int64_t nblk = m / B->bs;
@@ -294,7 +295,7 @@ int make_layout(int64_t m, int n, const scqr3_B* B, int prec, int host_chunks, L
   const int r = make_layout_one(m, n, B, prec, host_chunks, L, grid, geo);
   if (r != SCQR3_OK) return r;
   for (int p : {SCQR3_PREC_FP64, SCQR3_PREC_TC, SCQR3_PREC_MIXED_TC}) {
-    if (p == prec || (p != SCQR3_PREC_FP64 && (B || n > 64))) continue;
+    if (p == prec || (p != SCQR3_PREC_FP64 && (B || n > 128))) continue;
     Layout L2;
     int g2;
     PassGeom geo2;
@@ -434,7 +435,7 @@ int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void*
   Params& P = c->P;
   P.m = m;
   P.n = n;
-  P.np = c->tc ? 64 : padded_n(n);
+  P.np = c->tc ? tc_np(n) : padded_n(n);
   P.max_passes = (opts && opts->max_passes) ? opts->max_passes : 6;
   P.bs = B ? B->bs : 0;
   P.norm_x2 = opts ? opts->norm_x2 : 0.0;
@@ -471,8 +472,7 @@ int first_gram(Call& c, const double* X, int64_t ldx, int64_t r0, int64_t r1, in
     return c.grid;
   }
   if (c.tc) {
-    const int g0 = tc_groups(Pc.m);
-    const int g = g0 < sm_count() ? (g0 < 1 ? 1 : g0) : sm_count();
+    const int g = tc_grid(Pc.m, c.P.np, sm_count());
     launch_tc_gram(g, sm_count(), c.s, src, ldx, Pc, -1, c.colmax, part, c.L.part_stride, c.st, 0);
     return g;
   }

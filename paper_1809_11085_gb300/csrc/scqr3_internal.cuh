@@ -59,7 +59,7 @@ struct Layout {
   int n_partials;    // partial Gram slots used by this call (grid CTAs x groups)
   int csr_grid;      // CTAs of csr_gram_kernel (CSR form only)
   int tc_grid;       // CTAs of tc_gram_kernel (tensor-core Gram only)
-  size_t colmax;     // tensor-core Gram: per-column max |q_ij| (64 words)
+  size_t colmax;     // tensor-core Gram: per-column max |q_ij| (128 words)
   int part_stride;   // doubles per partial slot: pk_size(np) + 1 (||.||_F^2)
 };
 

@@ -1,5 +1,5 @@
 // tc_gram.cu -- the Gram matrix A = Q^T Q on the BF16 tensor cores (tcgen05),
-// accurate to FP64 level, for n <= 64.
+// accurate to FP64 level, for n <= 128.
 //
 // The FP64 pipe of this GPU issues 2 DFMA per clock per SM, so the Gram matrix
 // of a tall-skinny matrix costs as much as the substitution. The tensor cores
@@ -16,26 +16,37 @@
 //  * D_d = sum over digit pairs (s, t) with s + t = d, d = 0 .. 7, is read back
 //    from tensor memory every 256 rows. The digit sums are exact integers, so
 //    U = D_0 2^21 + D_1 2^14 + D_2 2^7 + D_3 and T = D_4 2^21 + ... + D_7
-//    (each below 2^45.1 per 256 rows) are accumulated exactly in int64 over
-//    all of a CTA's rows (at most 2^31 rows in all, so below 2^63), and only
-//    the final 2^-35 U + 2^-63 T is formed in FP64: the FP64 pipe, the scarce
-//    one, does no work per row. Pairs with s + t > 7 (below 2^-56 relative)
-//    are dropped.
+//    (per row below 2^35 and 2^37.3: all d + 1 pairs of D_d are at most
+//    127^2) are accumulated exactly in int64 over all of a CTA's rows (below
+//    2^63 up to 2^25.7 rows per CTA; a 288 GB device holds at most 2^28 rows
+//    of 128 columns, spread over at least 45 CTAs per block), and only the
+//    final 2^-35 U + 2^-63 T is formed in FP64: the FP64 pipe, the scarce one,
+//    does no work per row. Pairs with s + t > 7 (below 2^-56 relative) are
+//    dropped.
 //
 // The result differs from q_j^T q_k by at most about m 2^-55 sigma_j sigma_k:
 // the norm-wise bound of the Gram error that the shift of Eq. (finds2)
 // covers (gamma_m n ||Q||^2), so the factorization keeps its guarantees.
 //
-// Layout: both operands are the digit planes of a 64-row chunk, K-major (the
-// chunk rows are the K dimension), no swizzle: core matrices of 8 columns x 8
-// rows (16 bytes per column), the 8 row groups of a column block contiguous
-// (128 bytes apart), column blocks 1024 bytes apart. A plane is 8 KB; planes
-// are stored in the order 0, 4, 1, 5, 2, 6, 3, 7 so that the A operand of one
-// MMA (M = 128) covers digit s in its rows 0..63 and digit s + 4 in rows
-// 64..127: one instruction computes the pairs (s, t) and (s + 4, t). Tile e
-// of tensor memory (columns 64e .. 64e+63) accumulates, for s = 0 .. min(3, e)
-// and t = e - s, the pairs (s, t) in lanes 0..63 (d = e) and (s + 4, t) in
-// lanes 64..127 (d = e + 4). Eight tiles use all 512 columns.
+// Blocks: the columns form operand blocks of 64. For n <= 64 one block, and
+// every CTA computes it; for 64 < n <= 128 the Gram matrix is the blocks
+// (0,0), (1,1) and (0,1), each computed by its own set of CTAs over all rows.
+// A CTA of block (J, K) cuts the digits of column blocks J (the A operand) and
+// K (the B operand, the same planes when J = K) and writes its block's
+// entries of the packed upper triangle into its partial slot, zeros elsewhere.
+//
+// Layout: the operands are the digit planes of a chunk of KC rows (KC = 64 for
+// n <= 64, 32 above, so that two operand blocks fit a 64 KB stage), K-major
+// (the chunk rows are the K dimension), no swizzle: core matrices of 8
+// columns x 8 rows (16 bytes per column), the KC / 8 row groups of a column
+// block contiguous (128 bytes apart), column blocks 16 KC bytes apart. A plane
+// of one block is 128 KC bytes; planes are stored in the order 0, 4, 1, 5, 2,
+// 6, 3, 7 so that the A operand of one MMA (M = 128) covers digit s in its rows
+// 0..63 and digit s + 4 in rows 64..127: one instruction computes the pairs
+// (s, t) and (s + 4, t). Tile e of tensor memory (columns 64e .. 64e+63)
+// accumulates, for s = 0 .. min(3, e) and t = e - s, the pairs (s, t) in lanes
+// 0..63 (d = e) and (s + 4, t) in lanes 64..127 (d = e + 4). Eight tiles use all
+// 512 columns.
 //
 // One CTA of 256 + 32 threads per SM. Two 64 KB digit-plane stages: the threads cut
 // chunk c + 1 while the tensor core works on chunk c. When the rows are
@@ -45,10 +56,10 @@
 // loads leave the critical path; otherwise the threads load the rows directly. Thread 0 issues the MMAs
 // (descriptors are a base plus compile-time offsets) and commits them to the
 // stage's mbarrier. For the read-back, warp w serves the tensor-memory lane
-// quadrant w % 4 and the 32 columns 32 (w / 4) ..; a warp whose rows all lie
-// below its columns (strict lower triangle) skips it. Every wait has an
-// iteration limit; past it the kernel records SCQR3_E_TIMEOUT, skips the rest
-// and frees its tensor memory.
+// quadrant w % 4 and the 32 columns 32 (w / 4) ..; on a diagonal block a warp
+// whose rows all lie below its columns (strict lower triangle) skips it. Every
+// wait has an iteration limit; past it the kernel records SCQR3_E_TIMEOUT,
+// skips the rest and frees its tensor memory.
 #include "fp64_device.cuh"
 
 #include <cuda_bf16.h>
@@ -57,17 +68,26 @@ namespace scqr3 {
 
 namespace tc {
 
-constexpr int NP = 64;              // padded n
-constexpr int KC = 64;              // rows per chunk (MMA K extent)
-constexpr int CHUNKS = 4;           // chunks per read-back group (256 rows)
-constexpr int PLANE = 8192;         // bytes per digit plane
-constexpr int STAGE = 8 * PLANE;    // 64 KB
+constexpr int BW = 64;              // columns of one operand block
+constexpr int NPMAX = 128;          // largest padded n
+constexpr int GROUP = 256;          // rows per read-back group
 constexpr int THREADS = 256;   // slicer and read-back threads (the producer warp comes on top)
 constexpr uint32_t LBO = 128;       // K-direction core-matrix stride
-constexpr uint32_t SBO = 1024;      // column-block stride
-constexpr int XSTAGE = KC * NP * 8;  // FP64 rows of one chunk, staged by a bulk copy
+constexpr int STAGE = 65536;        // digit planes of one chunk (one or two operand blocks)
+constexpr int XSTAGE = 32768;       // FP64 rows of one chunk (KC n 8 bytes), staged by a bulk copy
 constexpr size_t SMEM = 2 * (size_t)STAGE + 2 * (size_t)XSTAGE + 1024;  // + alignment slack
 constexpr long long WAIT_LIMIT = 1ll << 26;
+
+// Geometry of a chunk of KC rows.
+template <int KC>
+struct ChunkGeo {
+  static constexpr int CHUNKS = GROUP / KC;    // chunks per read-back group
+  static constexpr uint32_t SBO = 16 * KC;     // column-block stride
+  static constexpr int PLANE = KC * BW * 2;    // bytes per digit plane of one block
+  static constexpr int BREG = 8 * PLANE;       // the B operand's planes (off-diagonal block)
+};
+static_assert(8 * ChunkGeo<64>::PLANE == STAGE && 16 * ChunkGeo<32>::PLANE == STAGE, "stage size");
+static_assert(32 * NPMAX * 8 == XSTAGE && 64 * 64 * 8 == XSTAGE, "staging size");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -76,38 +96,41 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
                :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 
+template <int KC>
 __device__ __forceinline__ uint64_t desc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(ChunkGeo<KC>::SBO >> 4) << 32) |
          ((uint64_t)1 << 46);
 }
 
-// byte offset of digit plane s within a stage
-__host__ __device__ constexpr uint32_t plane_off(int s) { return s < 4 ? s * 2 * PLANE : (s - 4) * 2 * PLANE + PLANE; }
+// byte offset of digit plane s within an operand block's planes
+template <int KC>
+__host__ __device__ constexpr uint32_t plane_off(int s) {
+  return s < 4 ? s * 2 * ChunkGeo<KC>::PLANE : (s - 4) * 2 * ChunkGeo<KC>::PLANE + ChunkGeo<KC>::PLANE;
+}
 
 // The MMAs of one chunk: tile e, digit s (and s + 4), digit t = e - s, K step kk.
-// The start-address field of a descriptor is its low 14 bits (address / 16);
-// the operands of a stage lie within 64 KB of its base, so offsets are added
-// to the base descriptor without carrying out of the field.
-template <int E, int S, int KK>
+// OFFD: the B operand is the second block's planes. The start-address field
+// of a descriptor is its low 14 bits (address / 16); the operands of a stage
+// lie within 64 KB of its base and every stage below 256 KB, so offsets are
+// added to the base descriptor without carrying out of the field.
+template <int KC, bool OFFD, int E, int S, int KK>
 __device__ __forceinline__ void issue_one(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
   constexpr int T = E - S;
-  constexpr uint64_t aoff = (plane_off(S) + KK * 2 * LBO) >> 4;
-  constexpr uint64_t boff = (plane_off(T) + KK * 2 * LBO) >> 4;
+  constexpr uint64_t aoff = (plane_off<KC>(S) + KK * 2 * LBO) >> 4;
+  constexpr uint64_t boff = ((OFFD ? ChunkGeo<KC>::BREG : 0) + plane_off<KC>(T) + KK * 2 * LBO) >> 4;
   const uint32_t accum = (!first_chunk || S > 0 || KK > 0) ? 1u : 0u;
   mma(tmem + 64 * E, dbase + aoff, dbase + boff, idesc, accum);
+  if constexpr (KK + 1 < KC / 16) issue_one<KC, OFFD, E, S, KK + 1>(dbase, tmem, idesc, first_chunk);
 }
-template <int E, int S>
+template <int KC, bool OFFD, int E, int S>
 __device__ __forceinline__ void issue_s(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
-  issue_one<E, S, 0>(dbase, tmem, idesc, first_chunk);
-  issue_one<E, S, 1>(dbase, tmem, idesc, first_chunk);
-  issue_one<E, S, 2>(dbase, tmem, idesc, first_chunk);
-  issue_one<E, S, 3>(dbase, tmem, idesc, first_chunk);
-  if constexpr (S < 3 && S < E) issue_s<E, S + 1>(dbase, tmem, idesc, first_chunk);
+  issue_one<KC, OFFD, E, S, 0>(dbase, tmem, idesc, first_chunk);
+  if constexpr (S < 3 && S < E) issue_s<KC, OFFD, E, S + 1>(dbase, tmem, idesc, first_chunk);
 }
-template <int E>
+template <int KC, bool OFFD, int E>
 __device__ __forceinline__ void issue_e(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
-  issue_s<E, 0>(dbase, tmem, idesc, first_chunk);
-  if constexpr (E < 7) issue_e<E + 1>(dbase, tmem, idesc, first_chunk);
+  issue_s<KC, OFFD, E, 0>(dbase, tmem, idesc, first_chunk);
+  if constexpr (E < 7) issue_e<KC, OFFD, E + 1>(dbase, tmem, idesc, first_chunk);
 }
 
 // Bounded wait for the completion of the phase with parity `parity`.
@@ -177,14 +200,14 @@ __device__ __forceinline__ uint32_t digit_pair(unsigned long long F0, unsigned l
   return *reinterpret_cast<uint32_t*>(&v) | signs;
 }
 
-template <int S>
+template <int KC, int S>
 __device__ __forceinline__ void store_plane(uint8_t* dst, const unsigned long long (&F)[8], const uint32_t (&sp)[4]) {
   uint4 w4;
   w4.x = digit_pair<S>(F[0], F[1], sp[0]);
   w4.y = digit_pair<S>(F[2], F[3], sp[1]);
   w4.z = digit_pair<S>(F[4], F[5], sp[2]);
   w4.w = digit_pair<S>(F[6], F[7], sp[3]);
-  *(uint4*)(dst + plane_off(S)) = w4;
+  *(uint4*)(dst + plane_off<KC>(S)) = w4;
 }
 
 }  // namespace tc
@@ -193,14 +216,16 @@ __device__ __forceinline__ void store_plane(uint8_t* dst, const unsigned long lo
 // patterns of non-negative doubles order like the numbers; an Inf or NaN
 // entry, exponent field all ones, orders above every finite one, so
 // colmax[j] is then non-finite) over rows [0, m) of src. Integer operations
-// only: the FP64 pipe is the slow one.
+// only: the FP64 pipe is the slow one. Thread t serves column t % nc (nc = 64
+// or 128 >= n) and row t / nc of each group of 256 / nc rows.
 __global__ void __launch_bounds__(256)
 colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int pass,
               unsigned long long* __restrict__ colmax, const DevState* __restrict__ st, int pairs) {
   if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
   __shared__ unsigned long long red[256];
   const int tid = threadIdx.x;
-  const int j = tid % 64, r0 = tid / 64;
+  const int nc = n > 64 ? 128 : 64, rs = 256 / nc;
+  const int j = tid % nc, r0 = tid / nc;
   const unsigned long long* s64 = reinterpret_cast<const unsigned long long*>(src);
   // pairs: the max of |hi| (the float's pattern in the low word; the Gram
   // kernel widens the scale by one bit for lo)
@@ -208,8 +233,8 @@ colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int
   unsigned long long mx = 0;
   if (j < n) {
     // 8 rows per thread in flight: the scan is bound by memory latency otherwise
-    const int64_t step = (int64_t)gridDim.x * 4;
-    int64_t i = (int64_t)blockIdx.x * 4 + r0;
+    const int64_t step = (int64_t)gridDim.x * rs;
+    int64_t i = (int64_t)blockIdx.x * rs + r0;
     for (; i + 7 * step < m; i += 8 * step) {
       unsigned long long v[8];
 #pragma unroll
@@ -224,9 +249,9 @@ colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int
   }
   red[tid] = mx;
   __syncthreads();
-  if (tid < 64 && j < n) {
+  if (tid < nc && j < n) {
     unsigned long long b = red[tid];
-    for (int q = 1; q < 4; ++q) b = b > red[tid + 64 * q] ? b : red[tid + 64 * q];
+    for (int q = 1; q < rs; ++q) b = b > red[tid + nc * q] ? b : red[tid + nc * q];
     if (pairs) {  // the float's value as a double pattern (Inf/NaN: +Inf)
       const uint32_t fb = (uint32_t)b;
       b = ((fb >> 23) & 0xFF) == 0xFF ? 0x7FF0000000000000ull
@@ -236,11 +261,17 @@ colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int
   }
 }
 
+// KC = 64: n <= 64, every CTA computes the one block. KC = 32: 64 < n <= 128;
+// CTAs [0, gd) compute block (0,0), [gd, 2 gd) block (1,1), the rest (0,1).
+template <int KC>
 __global__ void __launch_bounds__(tc::THREADS + 32, 1)
 tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
                const unsigned long long* __restrict__ colmax, double* __restrict__ partials, int part_stride,
-               DevState* __restrict__ st, int bulk, int pairs) {
+               DevState* __restrict__ st, int bulk, int pairs, int gd) {
   using namespace tc;
+  using GK = ChunkGeo<KC>;
+  constexpr int CHUNKS = GK::CHUNKS;
+  constexpr int NPK = KC == 64 ? 64 : 128;  // packed layout of the slots
   if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
   extern __shared__ uint8_t dsm[];
   uint8_t* stages = (uint8_t*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
@@ -250,8 +281,8 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   __shared__ __align__(8) uint64_t pfull[2];   // digit planes of the stage written (256 arrivals)
   __shared__ __align__(8) uint64_t tfree;      // tensor memory read back (256 arrivals)
   __shared__ uint32_t tslot;
-  __shared__ int Esh[NP];
-  __shared__ double sig[NP];
+  __shared__ int Esh[NPMAX];
+  __shared__ double sig[NPMAX];
   __shared__ volatile int err_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool producer = warp == THREADS / 32;  // warp 8: copies and MMAs (lane 0)
@@ -259,8 +290,24 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   const int64_t m = P.m;
   double* part = partials + (int64_t)blockIdx.x * part_stride;
 
+  // this CTA's block (cj, ck), its ordinal among the CTAs of the block, and their count
+  int cj = 0, ck = 0, cta = blockIdx.x, ncta = gridDim.x;
+  if (KC == 32) {
+    ncta = gd;
+    if (blockIdx.x >= 2 * gd) {
+      ck = 1;
+      cta = blockIdx.x - 2 * gd;
+      ncta = gridDim.x - 2 * gd;
+    } else if (blockIdx.x >= gd) {
+      cj = ck = 1;
+      cta = blockIdx.x - gd;
+    }
+  }
+  const bool offd = cj != ck;
+  const int colA = BW * cj, colB = BW * ck;  // first columns of the A and B operand blocks
+
   int bad = 0;
-  if (tid < NP) {
+  if (tid < NPMAX) {
     int E = -1000;
     double sg = 0.0;
     if (tid < n) {
@@ -304,10 +351,10 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
   // This CTA's chunks in order: ordinal k is chunk k % CHUNKS of its group
-  // blockIdx.x + (k / CHUNKS) gridDim.x; the sequence ends at the first chunk
-  // past m (only the last group can be partial).
+  // cta + (k / CHUNKS) ncta; the sequence ends at the first chunk past m
+  // (only the last group can be partial).
   auto row0_of = [&](uint32_t k) -> int64_t {
-    const int64_t g = blockIdx.x + (int64_t)(k / CHUNKS) * gridDim.x;
+    const int64_t g = cta + (int64_t)(k / CHUNKS) * ncta;
     const int64_t r0 = (g * CHUNKS + (k % CHUNKS)) * KC;
     return r0 < m ? r0 : -1;
   };
@@ -315,13 +362,14 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
 
   // read-back of the slicer warps: lane quadrant qd = warp % 4 (row 32 qd +
   // lane of the tiles; rows 0..63 hold d = e, rows 64..127 d = e + 4),
-  // columns 32 h .. 32 h + 31; rows 32..63 x columns 0..31 lie below the diagonal
+  // columns 32 h .. 32 h + 31; on a diagonal block rows 32..63 x columns
+  // 0..31 lie below the diagonal
   constexpr int CW = 32;
   const int qd = warp & 3, h = (warp >> 2) & 1;
   const int row = 32 * qd + lane;
   const int jr = row & 63;
   const bool upper = row < 64;
-  const bool rb_skip = (qd & 1) == 1 && h == 0;
+  const bool rb_skip = !offd && (qd & 1) == 1 && h == 0;
   // exact digit-sum accumulators of this thread's 32 entries: U (d = 0..3)
   // and T (d = 4..7)
   long long U[CW], T[CW];
@@ -358,13 +406,23 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        tc::issue_e<0>(desc(sbase + stg * STAGE), tmem, idesc, q == 0);
+        const uint64_t db = desc<KC>(sbase + stg * STAGE);
+        if constexpr (KC == 32) {
+          if (offd) tc::issue_e<KC, true, 0>(db, tmem, idesc, q == 0);
+          else tc::issue_e<KC, false, 0>(db, tmem, idesc, q == 0);
+        } else {
+          tc::issue_e<KC, false, 0>(db, tmem, idesc, q == 0);
+        }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(smem_u32(&bar[stg])) : "memory");
         committed = k + 1;
       }
     }
   } else {
+    // units (j, ig): 8 consecutive rows of operand column j; j < 64 is block
+    // cj (column colA + j), j >= 64 block ck (off-diagonal CTAs: colB + j - 64)
+    const int lgc = offd ? 7 : 6;
+    const int units = (KC / 8) << lgc;
     for (uint32_t chunk = 0;; ++chunk) {
       const int64_t row0 = row0_of(chunk);
       if (row0 < 0 || err_sh) break;
@@ -378,17 +436,17 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
       }
       uint8_t* sb = stages + stg * STAGE;
       const double* xs = (const double*)(xst + stg * XSTAGE);
-      // cut the chunk: unit (j, ig) = 8 consecutive rows of column j
-      for (int u = tid; u < NP * (KC / 8); u += THREADS) {
-        const int j = u % NP, ig = u / NP;
-        const int E = Esh[j];
+      for (int u = tid; u < units; u += THREADS) {
+        const int j = u & ((1 << lgc) - 1), ig = u >> lgc;
+        const int col = j < BW ? colA + j : colB + (j - BW);
+        const int E = Esh[col];
         unsigned long long F[8];
         uint32_t sp[4] = {0u, 0u, 0u, 0u};  // sign bits of rows 2p (bit 15) and 2p + 1 (bit 31)
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           const int i = ig * 8 + r;
           double x = 0.0;
-          if (j < n && i < rows) x = bulk ? xs[i * n + j] : src[(row0 + i) * lds + j];
+          if (col < n && i < rows) x = bulk ? xs[i * n + col] : src[(row0 + i) * lds + col];
           uint32_t sgn;
           if (pairs) {
             F[r] = tc::fixed56_pair((unsigned long long)__double_as_longlong(x), E, &sgn);
@@ -398,15 +456,15 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
           }
           sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
         }
-        uint8_t* dst = sb + (j >> 3) * SBO + ig * LBO + (j & 7) * 16;
-        tc::store_plane<0>(dst, F, sp);
-        tc::store_plane<1>(dst, F, sp);
-        tc::store_plane<2>(dst, F, sp);
-        tc::store_plane<3>(dst, F, sp);
-        tc::store_plane<4>(dst, F, sp);
-        tc::store_plane<5>(dst, F, sp);
-        tc::store_plane<6>(dst, F, sp);
-        tc::store_plane<7>(dst, F, sp);
+        uint8_t* dst = sb + (j >> 6) * GK::BREG + ((j & 63) >> 3) * GK::SBO + ig * LBO + (j & 7) * 16;
+        tc::store_plane<KC, 0>(dst, F, sp);
+        tc::store_plane<KC, 1>(dst, F, sp);
+        tc::store_plane<KC, 2>(dst, F, sp);
+        tc::store_plane<KC, 3>(dst, F, sp);
+        tc::store_plane<KC, 4>(dst, F, sp);
+        tc::store_plane<KC, 5>(dst, F, sp);
+        tc::store_plane<KC, 6>(dst, F, sp);
+        tc::store_plane<KC, 7>(dst, F, sp);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[stg])) : "memory");
@@ -461,21 +519,27 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   long long* xch = (long long*)stages;  // 64 x 64 int64 (32 KB) of stage 0
   if (!producer && !upper) {
 #pragma unroll
-    for (int k = 0; k < CW; ++k) xch[jr * NP + CW * h + k] = T[k];
+    for (int k = 0; k < CW; ++k) xch[jr * BW + CW * h + k] = T[k];
   }
   __syncthreads();
   if (!producer && upper && !rb_skip) {
-    const double sj = sig[jr];
+    const double sj = sig[colA + jr];
 #pragma unroll
     for (int k = 0; k < CW; ++k) {
-      const int col = CW * h + k;
-      if (col >= jr) {
-        const double a = fma(0x1p-35, (double)U[k], 0x1p-63 * (double)(T[k] + xch[jr * NP + col]));
-        part[pk_idx(NP, jr, col)] = a * sj * sig[col];
+      const int c = CW * h + k;
+      if (offd || c >= jr) {
+        const double a = fma(0x1p-35, (double)U[k], 0x1p-63 * (double)(T[k] + xch[jr * BW + c]));
+        part[pk_idx(NPK, colA + jr, colB + c)] = a * sj * sig[colB + c];
       }
     }
   }
-  if (tid == 0) part[pk_size(NP)] = 0.0;
+  if (KC == 32) {  // the other blocks' entries of this slot
+    for (int e = tid; e < NPK * NPK; e += blockDim.x) {
+      const int r = e / NPK, c = e % NPK;
+      if (c >= r && !((r >> 6) == cj && (c >> 6) == ck)) part[pk_idx(NPK, r, c)] = 0.0;
+    }
+  }
+  if (tid == 0) part[pk_size(NPK)] = 0.0;
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
@@ -484,24 +548,47 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
 // ---- host side ----------------------------------------------------------------------------
 
 cudaError_t tc_setup() {
-  return cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc_gram_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
 }
 
-int tc_groups(int64_t m) { return (int)((m + tc::KC * tc::CHUNKS - 1) / (tc::KC * tc::CHUNKS)); }
+int tc_groups(int64_t m) { return (int)((m + tc::GROUP - 1) / tc::GROUP); }
+
+// CTAs of the tensor-core Gram of m rows (np = 64: one block; np = 128: three
+// blocks, at least one CTA each).
+int tc_grid(int64_t m, int np, int sms) {
+  const int64_t g = tc_groups(m);
+  if (np <= 64) return (int)(g < sms ? (g < 1 ? 1 : g) : sms);
+  const int64_t t = 3 * (g < 1 ? 1 : g);
+  return (int)(t < sms ? t : sms);
+}
 
 // Column scales then the tensor-core Gram of rows [0, P.m) of src into `grid` slots.
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs) {
-  if (P.np != tc::NP || part_stride != pk_size(tc::NP) + 1) return;  // the slots hold the 64-column layout
-  cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * tc::NP, s);
-  const int64_t want = (P.m + 3) / 4;
+  // the slots hold the packed np x np layout; np = 128 needs a CTA per block
+  if ((P.np != 64 && P.np != 128) || part_stride != pk_size(P.np) + 1 || (P.np == 128 && grid < 3)) return;
+  cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * tc::NPMAX, s);
+  const int rs = P.n > 64 ? 2 : 4;
+  const int64_t want = (P.m + rs - 1) / rs;
   const int cg = (int)(want < (int64_t)sms * 8 ? (want < 1 ? 1 : want) : (int64_t)sms * 8);
   colmax_kernel<<<cg, 256, 0, s>>>(src, lds, P.m, P.n, pass, colmax, st, pairs);
   // bulk copies need contiguous rows, 16-byte aligned, and chunk sizes that are
   // multiples of 16 bytes (m n even)
   const int bulk = (lds == P.n && ((uintptr_t)src & 15) == 0 && ((P.m * P.n) & 1) == 0) ? 1 : 0;
-  tc_gram_kernel<<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials, part_stride, st,
-                                                          bulk, pairs);
+  if (P.np == 64) {
+    tc_gram_kernel<64><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials, part_stride,
+                                                                st, bulk, pairs, grid);
+    return;
+  }
+  // np = 128: gd CTAs for each diagonal block, the rest (which also cut twice
+  // the columns) for the off-diagonal one
+  const int g = tc_groups(P.m);
+  int gd = grid >= 3 * g ? g : (3 * grid) / 10;
+  if (gd < 1) gd = 1;
+  tc_gram_kernel<32><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials, part_stride, st,
+                                                              bulk, pairs, gd);
 }
 
 }  // namespace scqr3

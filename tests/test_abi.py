@@ -73,6 +73,16 @@ def test_argument_errors_are_reported_on_the_host(lib):
     assert lib.scqr3_workspace_bytes(30, 5, None, ctypes.byref(o), ctypes.byref(out)) == -12
     # n beyond the FP64 path
     assert lib.scqr3_workspace_bytes(1000, 300, None, None, ctypes.byref(out)) == scqr3.E_UNSUPPORTED
+    # the tensor-core Gram: n <= 128, B = I, m <= 2^31
+    for prec in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC):
+        o = scqr3._Opts(0, prec, 0.0)
+        assert lib.scqr3_workspace_bytes(1000, 129, None, ctypes.byref(o), ctypes.byref(out)) == \
+            scqr3.E_UNSUPPORTED
+        assert lib.scqr3_workspace_bytes(2 ** 31 + 1, 8, None, ctypes.byref(o), ctypes.byref(out)) == \
+            scqr3.E_UNSUPPORTED
+        b = scqr3._B(8, ctypes.c_void_p(8), 0.0)
+        assert lib.scqr3_workspace_bytes(800, 16, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out)) == \
+            scqr3.E_UNSUPPORTED
     # null pointers in scqr3_factor are rejected before any CUDA call
     assert lib.scqr3_factor(None, 10, 2, 2, None, None, 2, None, None, None, 0, None, None,
                             None) == -1

@@ -1,5 +1,6 @@
 """GPU parity of precision=SCQR3_PREC_TC: FP64 substitution with the Gram
-matrices on the BF16 tensor cores through the exact seven-bit digit split.
+matrices on the BF16 tensor cores through the exact seven-bit digit split
+(n <= 128).
 
 The split represents each entry to 2^-56 of its column's scale and every digit
 product and 256-row sum is exact, so the Gram matrix is accurate to about
@@ -51,9 +52,11 @@ def check(Xh, kappa, **kw):
     return info, tr
 
 
-@pytest.mark.parametrize("n", [1, 2, 7, 16, 31, 32, 33, 63, 64])
+@pytest.mark.parametrize("n", [1, 2, 7, 16, 31, 32, 33, 63, 64, 65, 66, 96, 127, 128])
 @pytest.mark.parametrize("m_kind", ["square", "small", "ragged", "tall"])
 def test_shape_sweep(n, m_kind):
+    """n <= 64: one 64-column block; 64 < n <= 128: the blocks (0,0), (1,1)
+    and (0,1) on separate CTAs, 32-row chunks."""
     m = {"square": n, "small": 300, "ragged": 20011, "tall": 100003}[m_kind]
     if m < n:
         m = n
@@ -71,14 +74,34 @@ def test_conditioning(kappa):
         assert info.passes == tr["passes"] == 3
 
 
-def test_badly_scaled_columns_and_rows():
-    """Column scales from 2^-300 to 2^300 and rows spanning 1e-30 .. 1: each
+@pytest.mark.parametrize("kappa", [1e2, 1e8, 1e15])
+def test_conditioning_two_blocks(kappa):
+    Xh = testmat(40000, 128, kappa, seed=6150)
+    info, tr = check(Xh, kappa, norm_x2=1.0)
+    if kappa in (1e2, 1e8):
+        assert info.passes == tr["passes"] == 3
+
+
+def test_block_grid_small_m():
+    """m from 1 to a few read-back groups: CTAs of a block without rows still
+    write their slot (zeros), and every block has at least one CTA."""
+    for m, seed in ((100, 6160), (256, 6161), (257, 6162), (3 * 256 + 5, 6163), (40 * 256, 6164)):
+        n = 100 if m >= 100 else m
+        check(testmat(m, n, 1e5, seed=seed), 1e5)
+
+
+@pytest.mark.parametrize("n,e", [(40, 300), (100, 200)])
+def test_badly_scaled_columns_and_rows(n, e):
+    """Column scales from 2^-e to 2^e and rows spanning 1e-30 .. 1: each
     column has its own power-of-two scale, and the fixed-point error is
-    relative to it, which is what the norm-wise Gram bound needs."""
-    rng = np.random.default_rng(6200)
-    m, n = 30000, 40
-    Xh = testmat(m, n, 1e4, seed=6201)
-    Xh *= np.exp2(rng.integers(-300, 300, size=n))[None, :]
+    relative to it, which is what the norm-wise Gram bound needs. (The
+    algorithm itself needs more passes as the column scales spread: the
+    oracle takes 5 passes for the first case, 3 for the second, and 8 for
+    n = 100 with e = 300.)"""
+    rng = np.random.default_rng(6200 + n)
+    m = 30000
+    Xh = testmat(m, n, 1e4, seed=6201 + n)
+    Xh *= np.exp2(rng.integers(-e, e, size=n))[None, :]
     Xh[rng.random(m) < 0.3] *= 1e-30
     Qg, Rg, info = run(Xh)
     assert info.status == 0
@@ -91,8 +114,9 @@ def test_badly_scaled_columns_and_rows():
     assert np.linalg.norm(Qg.T @ Qg - np.eye(n), 2) < 1e-13
 
 
-def test_matches_fp64_form_at_scale():
-    m, n = 1_000_000, 64
+@pytest.mark.parametrize("n", [64, 128])
+def test_matches_fp64_form_at_scale(n):
+    m = 1_000_000
     from paper_1809_11085_gb300.testmat import testmat_torch
 
     X, _, _ = testmat_torch(m, n, 1e8, seed=6300)
@@ -125,7 +149,11 @@ def test_non_finite_and_rejections():
     _, _, info = run(Xh)
     assert info.status == scqr3.E_NONFINITE
     with pytest.raises(scqr3.ScqrError):
-        scqr3.factor(torch.zeros((1000, 65), dtype=torch.float64, device="cuda"), precision=TC)
+        scqr3.factor(torch.zeros((1000, 129), dtype=torch.float64, device="cuda"), precision=TC)
+    Xh = testmat(5000, 100, 1e4, seed=6501)
+    Xh[4321, 99] = np.nan  # a column of the second block
+    _, _, info = run(Xh)
+    assert info.status == scqr3.E_NONFINITE
 
 
 # ------------------------------------------------------------------------------- mixed substitution + TC Gram
@@ -133,7 +161,7 @@ def test_non_finite_and_rejections():
 UDF = 2.0 ** -48
 
 
-@pytest.mark.parametrize("n", [1, 7, 16, 33, 64])
+@pytest.mark.parametrize("n", [1, 7, 16, 33, 64, 65, 128])
 @pytest.mark.parametrize("kappa", [1e4, 1e10, 1e15])
 def test_mixed_tc_against_oracle(n, kappa):
     """PREC_MIXED_TC: the mixed form's FP32-pair substitution (unit roundoff
