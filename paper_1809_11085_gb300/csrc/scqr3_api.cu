@@ -49,6 +49,11 @@ void launch_csr_gram(int np, int grid, cudaStream_t s, const double* src, int64_
                      int pass, const scqr3_B* B, double* partials, int part_stride, const DevState* st);
 cudaError_t tc_setup();
 int tc_grid(int64_t m, int np, int sms);
+cudaError_t tc_solve_setup();
+void launch_tc_split_r(cudaStream_t s, const double* rk, int np1, int pass, const DevState* st, double* r00,
+                       double* r11);
+void launch_tc_update(int sms, cudaStream_t s, const double* y, int64_t ldy, const double* x1, int64_t ldx,
+                      double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, DevState* st);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs);
 
@@ -113,6 +118,8 @@ cudaError_t device_geo(int np, int* grid_max, PassGeom* geo) {
     e = csr_setup(d.csr_ctas_per_sm);
     if (e != cudaSuccess) return e;
     e = tc_setup();
+    if (e != cudaSuccess) return e;
+    e = tc_solve_setup();
     if (e != cudaSuccess) return e;
     for (int k = 0; k < 4; ++k)
       if (d.csr_ctas_per_sm[k] < 1) return cudaErrorInvalidConfiguration;
@@ -277,6 +284,8 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
   }
   L->colmax = off;
   off = align256(off + sizeof(unsigned long long) * 128);
+  L->tcr = off;
+  off = align256(off + sizeof(double) * 2 * pk_size(32));
   L->lt = off;
   if (B && B->bs > 0) {
     const int64_t nblk = m / B->bs;
@@ -399,6 +408,7 @@ struct Call {
   double *gram = nullptr, *rstack = nullptr, *racc = nullptr, *lt = nullptr, *partials = nullptr;
   double *S = nullptr, *Ra = nullptr;  // n = 256: Cholesky work buffers
   unsigned long long* colmax = nullptr;  // tensor-core Gram: column scales
+  double* tcr = nullptr;                 // tensor-core substitution: R00, R11 packed
   double *R = nullptr, *Rpass = nullptr;
   scqr3_info* info = nullptr;
 };
@@ -427,6 +437,7 @@ int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void*
   c->partials = (double*)(ws + c->L.partials);
   c->S = (double*)(ws + c->L.chol);
   c->colmax = (unsigned long long*)(ws + c->L.colmax);
+  c->tcr = (double*)(ws + c->L.tcr);
   c->Ra = c->S + pk_size(256);
   c->R = R;
   c->Rpass = Rpass;
@@ -503,6 +514,41 @@ void launch_any_chol(Call& c, int pass) {
 // Pass k's solve Q := Q R_k^{-1} over rows [r0, r1) (src -> dst), with the
 // fused Gram when the device asks for it (FP64 and mixed forms, whole range
 // only: a range is used only for a final solve, which has no Gram).
+// CTAs of the pass kernel for a padded size and m rows.
+int pass_grid(int np, int64_t m) {
+  int gm = 0;
+  PassGeom geo;
+  if (device_geo(np, &gm, &geo) != cudaSuccess) return 1;
+  const int64_t pn = (m + geo.pr - 1) / geo.pr;
+  return (int)(pn < gm ? (pn < 1 ? 1 : pn) : gm);
+}
+
+// The tensor-core form's substitution for 32 < n <= 64: with R_k = [R00 R01;
+// 0 R11], Y0 = X0 R00^{-1} (FP64), X1 := X1 - Y0 R01 (tensor cores, exact
+// digit split), Y1 = X1 R11^{-1} (FP64).
+void tc_solve_rows(Call& c, int k, const double* rk, const double* src, int64_t lds, double* dst, int64_t ldd,
+                   const Params& Pc) {
+  const int n1 = Pc.n - 32, np1 = n1 <= 16 ? 16 : 32;
+  double* r00 = c.tcr;
+  double* r11 = c.tcr + pk_size(32);
+  tick(c.s, SCQR3_KERNEL_TCUPDATE, k);
+  launch_tc_split_r(c.s, rk, np1, k, c.st, r00, r11);
+  tick(c.s, SCQR3_KERNEL_PASS, k);
+  Params P0 = Pc;
+  P0.n = 32;
+  P0.np = 32;
+  launch_pass(32, pass_grid(32, Pc.m), c.s, src, lds, dst, ldd, P0, k, r00, nullptr, c.partials, c.L.part_stride,
+              c.st);
+  tick(c.s, SCQR3_KERNEL_TCUPDATE, k);
+  launch_tc_update(sm_count(), c.s, dst, ldd, src + 32, lds, dst + 32, ldd, Pc.m, n1, k, rk, c.st);
+  tick(c.s, SCQR3_KERNEL_PASS, k);
+  Params P1 = Pc;
+  P1.n = n1;
+  P1.np = np1;
+  launch_pass(np1, pass_grid(np1, Pc.m), c.s, dst + 32, ldd, dst + 32, ldd, P1, k, r11, nullptr, c.partials,
+              c.L.part_stride, c.st);
+}
+
 void solve_rows(Call& c, int k, const double* src, int64_t lds, double* dst, int64_t ldd, int64_t r0,
                 int64_t r1) {
   Params Pc = c.P;
@@ -510,6 +556,10 @@ void solve_rows(Call& c, int k, const double* src, int64_t lds, double* dst, int
   src += r0 * lds;
   dst += r0 * ldd;
   const double* rk = c.rstack + (size_t)k * pk_size(c.P.np);
+  if (c.tc && !c.mixed && c.P.np == 64 && c.P.n > 32) {
+    tc_solve_rows(c, k, rk, src, lds, dst, ldd, Pc);
+    return;
+  }
   if (c.P.np == 256) {
     tick(c.s, SCQR3_KERNEL_TRSM, k);
     launch_trsm256(trsm256_grid(Pc.m), c.s, src, lds, dst, ldd, Pc, k, rk, c.st);

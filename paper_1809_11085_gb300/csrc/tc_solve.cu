@@ -1,0 +1,320 @@
+// tc_solve.cu -- the row-wise substitution Q := X R^{-1} (Eq. backward2) for
+// 32 < n <= 64 with its off-diagonal block on the tensor cores.
+//
+// Blocking R = [R00 R01; 0 R11] (R00 the leading 32 x 32 block) splits the
+// substitution of each row x^T = [x0^T x1^T] into
+//   y0^T = x0^T R00^{-1},   x1'^T = x1^T - y0^T R01,   y1^T = x1'^T R11^{-1}:
+// the same terms forward substitution over columns takes, grouped by block.
+// The two triangular solves run in FP64 on the pass kernel over 32-column
+// blocks. The product y0^T R01 -- half of the substitution's flops, and a
+// dense contraction -- runs here on the BF16 tensor cores through the exact
+// digit split of the Gram kernel:
+//  * row i of Y0 gets the scale sigma_i = 2^E_i > max_k |y_ik| (its own 32
+//    values), column l of R01 the scale tau_l = 2^E_l > max_k |r_kl|;
+//  * both are cut into eight signed 7-bit digits (56 bits); digit products are
+//    exact in FP32, and tile e of tensor memory sums the pairs (s, t) with
+//    s + t = e over the 32 columns k: at most 8 * 32 * 127^2 < 2^24, exact;
+//  * per entry the tile sums fold exactly into int64, U = sum_{e<=3} D_e
+//    2^{7(3-e)} (< 2^40.1) and T = sum_{e>=4} D_e 2^{7(7-e)} (< 2^42.3), then
+//    W = 2^21 U + floor(T / 2^7) (< 2^61.2, truncation below 2^-56 of
+//    sigma_i tau_l), and x1'_il = x1_il - sigma_i (2^-56 tau_l) W in FP64.
+// The computed product differs from y0_i^T r_l by less than about
+// 2^-54 (sigma_i ||r_l||_1 + tau_l ||y0_i||_1), a perturbation of R01 of norm
+// O(u ||R||): the order of the row-wise backward error of FP64 substitution
+// (Eq. backward2) on which the analysis of Sec. 3 rests.
+//
+// Kernel layout: 2 slots of 128 threads (one 128-row tile each, thread r the
+// tile's row r and tensor-memory lane r) plus a producer warp. A slot loads
+// its rows of Y0, cuts them into 8 digit planes (A operand, M = 128 rows, K =
+// 32, K-major, no swizzle: core matrices of 8 rows x 16 bytes, K step 128 B,
+// 8-row step 512 B), and signals the producer, which issues the 72 MMAs
+// (M = 128, N = 16 or 32, K = 16) of the tile into the slot's 256 columns of
+// tensor memory and commits them to the slot's mbarrier. The slot then reads
+// its row's sums back (tcgen05.ld 32x32b) and writes x1'. While one slot
+// waits for its MMAs the other cuts or applies. Every wait has an iteration
+// limit; past it the kernel records SCQR3_E_TIMEOUT, waits (bounded) for its
+// own MMAs and frees its tensor memory.
+#include "tc_common.cuh"
+
+namespace scqr3 {
+
+namespace tcs {
+
+constexpr int K = 32;                    // columns of the leading block: the contraction length
+constexpr int ROWS = 128;                // rows per tile
+constexpr int SLOTS = 2;                 // tiles in flight per CTA
+constexpr int THREADS = ROWS * SLOTS;    // slot threads (the producer warp comes on top)
+constexpr uint32_t LBO = 128;            // K-direction core-matrix stride
+constexpr uint32_t SBO = 512;            // 8-row (A) or 8-column (B) group stride
+constexpr int APLANE = ROWS * K * 2;     // 8 KB per digit plane of a tile
+constexpr int ASLOT = 8 * APLANE;        // 64 KB of A planes per slot
+constexpr int BPLANE = 32 * K * 2;       // 2 KB per digit plane of R01 (N <= 32)
+constexpr uint32_t TSLOT = 256;          // tensor-memory columns per slot: 8 tiles x 32
+constexpr size_t SMEM = SLOTS * (size_t)ASLOT + 8 * (size_t)BPLANE + 1024;  // + alignment slack
+
+__device__ __forceinline__ uint64_t desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+// The 72 MMAs of a tile: tile e, digit s of Y0, digit t = e - s of R01, K step kk.
+// Descriptor offsets stay inside the start-address field (all of shared
+// memory lies below 256 KB).
+template <int N, int E, int S, int KK>
+__device__ __forceinline__ void issue(uint64_t adesc, uint64_t bdesc, uint32_t tmem, uint32_t idesc) {
+  constexpr uint64_t aoff = ((uint32_t)S * APLANE + KK * 2 * LBO) >> 4;
+  constexpr uint64_t boff = ((uint32_t)(E - S) * BPLANE + KK * 2 * LBO) >> 4;
+  tc::mma(tmem + 32 * E, adesc + aoff, bdesc + boff, idesc, (S > 0 || KK > 0) ? 1u : 0u);
+  if constexpr (KK == 0) {
+    issue<N, E, S, 1>(adesc, bdesc, tmem, idesc);
+  } else if constexpr (S < E) {
+    issue<N, E, S + 1, 0>(adesc, bdesc, tmem, idesc);
+  } else if constexpr (E < 7) {
+    issue<N, E + 1, 0, 0>(adesc, bdesc, tmem, idesc);
+  }
+}
+
+// Eight consecutive values of a row (or column) as 8 digit planes of one
+// core-matrix row each (16 bytes: 8 BF16 digits), at dst + s * plane.
+__device__ __forceinline__ void cut8(const double (&x)[8], int E, uint8_t* dst, uint32_t plane) {
+  unsigned long long F[8];
+  uint32_t sp[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    F[r] = tc::fixed56(x[r], E);
+    const uint32_t sgn = (uint32_t)((unsigned long long)__double_as_longlong(x[r]) >> 32) & 0x80000000u;
+    sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
+  }
+#define SCQR3_CUT(S)                                                                                \
+  {                                                                                                 \
+    uint4 w;                                                                                        \
+    w.x = tc::digit_pair<S>(F[0], F[1], sp[0]);                                                     \
+    w.y = tc::digit_pair<S>(F[2], F[3], sp[1]);                                                     \
+    w.z = tc::digit_pair<S>(F[4], F[5], sp[2]);                                                     \
+    w.w = tc::digit_pair<S>(F[6], F[7], sp[3]);                                                     \
+    *(uint4*)(dst + (S) * plane) = w;                                                               \
+  }
+  SCQR3_CUT(0) SCQR3_CUT(1) SCQR3_CUT(2) SCQR3_CUT(3) SCQR3_CUT(4) SCQR3_CUT(5) SCQR3_CUT(6) SCQR3_CUT(7)
+#undef SCQR3_CUT
+}
+
+// Scale exponent of a non-negative bit-pattern maximum: 2^E > the value
+// (-1000 for zero, so every digit is 0).
+__device__ __forceinline__ int scale_exp(unsigned long long mx) {
+  if (mx == 0) return -1000;
+  const int ex = (int)(mx >> 52);
+  return (ex ? ex : 1) - 1023 + 1;
+}
+
+}  // namespace tcs
+
+// R00 and R11 of the packed 64 x 64 R_k as packed 32 x 32 and np1 x np1
+// (np1 = 16 or 32; the padding of R_k is the identity, and so is theirs).
+__global__ void tc_split_r_kernel(const double* __restrict__ rk, int np1, int pass, const DevState* __restrict__ st,
+                                  double* __restrict__ r00, double* __restrict__ r11) {
+  if (!st->run_trsm[pass]) return;
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int j = e / 32, k = e % 32;
+    if (k < j) continue;
+    r00[pk_idx(32, j, k)] = rk[pk_idx(64, j, k)];
+    if (k < np1) r11[pk_idx(np1, j, k)] = rk[pk_idx(64, 32 + j, 32 + k)];
+  }
+}
+
+// x1' = x1 - Y0 R01 for rows [0, m): y holds Y0 (32 columns), x1 and q1 the
+// columns 32 .. 32 + n1 - 1 of the pass's input and output (they may be the
+// same memory); rk is R_k packed 64 x 64.
+template <int N>
+__global__ void __launch_bounds__(tcs::THREADS + 32, 1)
+tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, int64_t ldx, double* q1, int64_t ldq,
+                 int64_t m, int n1, int pass, const double* __restrict__ rk, DevState* __restrict__ st) {
+  using namespace tcs;
+  using tc::smem_u32;
+  if (!st->run_trsm[pass]) return;
+  extern __shared__ uint8_t dsm[];
+  uint8_t* abuf = (uint8_t*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
+  uint8_t* bbuf = abuf + SLOTS * ASLOT;
+  __shared__ __align__(8) uint64_t pfull[SLOTS];  // A planes of the slot's tile written (128 arrivals)
+  __shared__ __align__(8) uint64_t mdone[SLOTS];  // MMAs of the slot's tile done (tcgen05.commit)
+  __shared__ uint32_t tslot;
+  __shared__ int Eb[32];
+  __shared__ double cscale[32];  // 2^-56 tau_l
+  __shared__ volatile int err_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool producer = warp == THREADS / 32;
+  const int slot = (warp >> 2) & 1;
+  const int r = tid & (ROWS - 1);  // tile row and tensor-memory lane (warp w serves lanes 32 (w % 4) ..)
+
+  // column scales of R01 (columns >= n1: zero)
+  if (tid < 32) {
+    unsigned long long mx = 0;
+    if (tid < n1)
+      for (int k = 0; k < K; ++k) {
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(rk[pk_idx(64, k, 32 + tid)]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = mx > b ? mx : b;
+      }
+    const int E = scale_exp(mx);
+    Eb[tid] = E;
+    cscale[tid] = mx ? ldexp(1.0, E - 56) : 0.0;
+  }
+  if (tid == 0) {
+    err_sh = 0;
+    for (int g = 0; g < SLOTS; ++g) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&pfull[g])), "r"(ROWS));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mdone[g])), "r"(1));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  // R01 digit planes (B operand: N columns x 32 rows, K-major)
+  for (int u = tid; u < N * (K / 8); u += THREADS + 32) {
+    const int l = u % N, kg = u / N;
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = l < n1 ? rk[pk_idx(64, 8 * kg + q, 32 + l)] : 0.0;
+    cut8(v, Eb[l], bbuf + (l >> 3) * SBO + kg * LBO + (l & 7) * 16, BPLANE);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+  // D F32, A and B BF16, both K-major, N, M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+
+  // this CTA's tiles: ordinal k is tile blockIdx.x + k gridDim.x; slot k % 2
+  auto tile_row0 = [&](uint32_t k) -> int64_t {
+    const int64_t r0 = ((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * ROWS;
+    return r0 < m ? r0 : -1;
+  };
+
+  uint32_t committed = 0;
+  if (producer) {
+    if (lane == 0) {
+      for (uint32_t k = 0; tile_row0(k) >= 0; ++k) {
+        const int g = k & 1;
+        if (!tc::wait_parity(smem_u32(&pfull[g]), (k >> 1) & 1) || err_sh) {
+          err_sh = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        issue<N, 0, 0, 0>(desc(smem_u32(abuf + g * ASLOT)), desc(smem_u32(bbuf)), tmem + g * TSLOT, idesc);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_u32(&mdone[g])) : "memory");
+        committed = k + 1;
+      }
+    }
+  } else {
+    uint8_t* arow = abuf + slot * ASLOT + (r >> 3) * SBO + (r & 7) * 16;
+    const uint32_t tq = tmem + slot * TSLOT + ((uint32_t)(32 * (warp & 3)) << 16);
+    for (uint32_t j = 0;; ++j) {
+      const int64_t row0 = tile_row0(2 * j + slot);
+      if (row0 < 0 || err_sh) break;
+      const int64_t i = row0 + r;
+      const bool live = i < m;
+      double yv[K];
+      unsigned long long mx = 0;
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        yv[c] = live ? y[i * ldy + c] : 0.0;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(yv[c]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = mx > b ? mx : b;
+      }
+      const bool finite = (mx >> 52) != 0x7FF;
+      const int E = finite ? scale_exp(mx) : 0;
+      const double sig = ldexp(1.0, E);
+#pragma unroll
+      for (int kg = 0; kg < K / 8; ++kg) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = yv[8 * kg + q];
+        cut8(v, E, arow + kg * LBO, APLANE);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[slot])) : "memory");
+      if (!tc::wait_parity(smem_u32(&mdone[slot]), j & 1)) {
+        err_sh = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int c0 = 0; c0 < N; c0 += 8) {
+        long long U[8], T[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) U[q] = T[q] = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          uint32_t v[8];
+          tc::ld8(tq + 32 * e + c0, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int sh = e < 4 ? 7 * (3 - e) : 7 * (7 - e);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const long long dv = (long long)__float2int_rn(__uint_as_float(v[q])) << sh;
+            if (e < 4) U[q] += dv;
+            else T[q] += dv;
+          }
+        }
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int l = c0 + q;
+            if (l < n1) {
+              const long long W = (U[q] << 21) + (T[q] >> 7);
+              const double upd = __ll2double_rn(W) * cscale[l];
+              const double xv = x1[i * ldx + l];
+              q1[i * ldq + l] = finite ? fma(-upd, sig, xv) : (double)NAN;
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+  }
+  __syncthreads();
+  if (err_sh) {
+    atomicCAS(&st->status, SCQR3_OK, SCQR3_E_TIMEOUT);
+    // let the MMAs already issued finish (bounded) before the memory goes away
+    if (producer && lane == 0 && committed > 0) {
+      const uint32_t k = committed - 1;
+      tc::wait_parity(smem_u32(&mdone[k & 1]), (k >> 1) & 1);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+}
+
+// ---- host side ----------------------------------------------------------------------------
+
+cudaError_t tc_solve_setup() {
+  cudaError_t e = cudaFuncSetAttribute(tc_update_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tcs::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc_update_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcs::SMEM);
+}
+
+void launch_tc_split_r(cudaStream_t s, const double* rk, int np1, int pass, const DevState* st, double* r00,
+                       double* r11) {
+  tc_split_r_kernel<<<1, 256, 0, s>>>(rk, np1, pass, st, r00, r11);
+}
+
+// x1' = x1 - Y0 R01 over rows [0, m); n1 = n - 32 in 1 .. 32.
+void launch_tc_update(int sms, cudaStream_t s, const double* y, int64_t ldy, const double* x1, int64_t ldx,
+                      double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, DevState* st) {
+  const int64_t tiles = (m + tcs::ROWS - 1) / tcs::ROWS;
+  const int grid = (int)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
+  if (n1 <= 16)
+    tc_update_kernel<16><<<grid, tcs::THREADS + 32, tcs::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, pass, rk, st);
+  else
+    tc_update_kernel<32><<<grid, tcs::THREADS + 32, tcs::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, pass, rk, st);
+}
+
+}  // namespace scqr3
