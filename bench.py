@@ -42,6 +42,7 @@ FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
 PROFILED_KERNEL_SHA = "b447e14d15d0797f"
 PROFILED_BYTES_PER_ROW = 992.3
 PROFILED_SOLVE_BYTES_PER_ROW = 968.7
+PROFILED_BLOCK_BYTES_PER_ROW = None  # pass_kernel<32> on one 32-column block of a 64-column X
 
 
 def parse():
@@ -69,8 +70,10 @@ def parse():
     return ap.parse_args()
 
 
-def profiled_traffic(m, n, solve_only=False):
-    """roofline.traffic of a pass_kernel<64> launch, or None if the kernel changed since the capture."""
+def profiled_traffic(m, n, solve_only=False, tcs=False):
+    """roofline.traffic of a pass_kernel<64> launch (tcs: a pass_kernel<32>
+    launch on a 32-column block), or None if the kernel changed since the
+    capture or none was taken."""
     import hashlib
 
     h = hashlib.sha256()
@@ -79,6 +82,8 @@ def profiled_traffic(m, n, solve_only=False):
     sha = h.hexdigest()[:16]
     if sha != PROFILED_KERNEL_SHA or n != 64:
         return None
+    if tcs:
+        return PROFILED_BLOCK_BYTES_PER_ROW * m if PROFILED_BLOCK_BYTES_PER_ROW else None
     return (PROFILED_SOLVE_BYTES_PER_ROW if solve_only else PROFILED_BYTES_PER_ROW) * m
 
 
@@ -123,10 +128,11 @@ def tc_gram_roofline(m, n, ms_list):
             "traffic": None}
 
 
-def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True):
+def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True, block=None):
     """FP64 flops done by one pass_kernel launch (0 when the device skipped it).
     gram_in_pass=False: the Gram matrices run on the tensor cores, the pass
-    kernel only solves."""
+    kernel only solves. block = 0 or 1: the launch solves the leading 32
+    columns or the remaining n - 32 (tensor-core substitution, 32 < n <= 64)."""
     from paper_1809_11085_gb300 import scqr3
 
     if kernel == scqr3.KERNEL_GRAM:
@@ -134,11 +140,37 @@ def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True):
     if kernel == scqr3.KERNEL_PASS:
         if pass_idx >= passes:
             return 0
+        if block is not None:
+            w = 32 if block == 0 else n - 32
+            return m * w * w
         f = m * n * n
         if pass_idx < passes - 1 and gram_in_pass:
             f += m * n * (n + 1)
         return f
     return 0
+
+
+def tc_solve_used(prec, n):
+    from paper_1809_11085_gb300 import scqr3
+
+    return prec == scqr3.PREC_TC and 32 < n <= 64
+
+
+def tc_update_roofline(m, n, ms_list):
+    """HBM figures of the tensor-core substitution update x1 -= y0 R01: per row
+    it reads y0 (32 values) and x1 (n - 32) and writes x1' (n - 32), 8 bytes each."""
+    if not ms_list:
+        return None
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    byts = m * 8 * (32 + 2 * (n - 32))
+    t = statistics.median(ms_list) * 1e-3
+    mma_flops = ((m + 127) // 128) * 72 * 2 * 128 * (16 if n - 32 <= 16 else 32) * 16
+    return {"bound": "hbm", "kernel": "tc_update_kernel", "achieved": byts / t / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": byts / t / 1e9 / peak, "bytes_per_launch": byts, "ms_per_launch": statistics.median(ms_list),
+            "tensor_tflops_issued": mma_flops / t / 1e12,
+            "peak_note": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback", "traffic": None}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -334,17 +366,31 @@ def run_gpu(args, rank, world, local_rank):
     # dominant kernel: pass_kernel launches that did work
     kflops, kms, kl = 0.0, 0.0, 0
     share = {}
-    tc_gram_ms = []
+    tc_gram_ms, tc_upd_ms = [], []
     tc_path = prec in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC)
+    tcs = tc_solve_used(prec, n)
+    seen = {}  # (kernel, pass) -> records so far in the current factorization
     for kernel, p, t in recs:
         name = scqr3.KERNEL_NAMES.get(kernel, str(kernel))
+        block = None
+        if kernel == scqr3.KERNEL_CHOL and p == 0:
+            seen = {}  # a new factorization begins
+        j = seen.get((kernel, p), 0)
+        seen[(kernel, p)] = j + 1
         if tc_path and kernel == scqr3.KERNEL_GRAM:
             name = "tc_gram_kernel (+ colmax_kernel)"
             if p <= passes - 1:
                 tc_gram_ms.append(t)
+        if tcs and kernel == scqr3.KERNEL_PASS:
+            block = j % 2
+            name = "pass_kernel<32> (FP64 diagonal blocks)"
+        if tcs and kernel == scqr3.KERNEL_TCUPDATE:
+            name = "tc_update_kernel" if j % 2 == 1 else "tc_split_r_kernel"
+            if j % 2 == 1 and p < passes:
+                tc_upd_ms.append(t)
         share[name] = share.get(name, 0.0) + t
         f = pass_kernel_flops(m, n, kernel, p, passes,
-                              gram_in_pass=prec not in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC))
+                              gram_in_pass=prec not in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC), block=block)
         if f > 0:
             kflops += f
             kms += t
@@ -365,7 +411,7 @@ def run_gpu(args, rank, world, local_rank):
         Rref = R.clone()
         for fname, fp in (("fp64", scqr3.PREC_FP64), ("tc", scqr3.PREC_TC), ("mixed", scqr3.PREC_MIXED),
                           ("mixed_tc", scqr3.PREC_MIXED_TC)):
-            if fp == prec or (n > 64 and fp in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC)):
+            if fp == prec or (n > 128 and fp in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC)):
                 continue
             fms = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, workspace=ws, read_info=False, precision=fp),
                         reps=2)
@@ -455,7 +501,8 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "dtype_note": {"fp64": "FP64 throughout",
-                       "tc": "FP64 substitution, Cholesky and accumulation; Gram digit products exact "
+                       "tc": "FP64 Cholesky, accumulation and triangular substitution blocks; the Gram and "
+                             "(32 < n <= 64) the off-diagonal substitution block from exact digit products "
                              "(7-bit integers in BF16, sums below 2^24 in FP32, folded in int64)",
                        "mixed": "FP32 pairs for Gram and substitution, FP64 shift/Cholesky/accumulation",
                        "mixed_tc": "FP32-pair substitution, exact tensor-core Gram"}[pname],
@@ -464,17 +511,21 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "inputs (%.1f GB) larger than the 129 MB L2; no flush" % (m * n * 8 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu",
-                     "kernel": "pass_kernel<64> (FP64 DFMA%s)" % (", substitution only" if tc_path else ""),
+                     "kernel": ("pass_kernel<32> (FP64 DFMA substitution of the two 32-column diagonal blocks; "
+                                "the off-diagonal block on the tensor cores)") if tcs else
+                               "pass_kernel<64> (FP64 DFMA%s)" % (", substitution only" if tc_path else ""),
                      "achieved": achieved, "peak": FP64_PEAK_DERIVED_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_DERIVED_TFLOPS) if achieved else None,
-                     "traffic": profiled_traffic(m, n, solve_only=tc_path), "traffic_note":
+                     "traffic": profiled_traffic(m, n, solve_only=tc_path, tcs=tcs), "traffic_note":
                          "DRAM bytes of one %s launch (ncu at 1048576 rows, scaled by rows)"
-                         % ("substitution-only" if tc_path else "fused solve+Gram"),
+                         % ("32-column diagonal-block" if tcs else "substitution-only" if tc_path
+                            else "fused solve+Gram"),
                      "launches_timed": kl,
                      "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; cuBLAS DGEMM measured beside it",
                      "cublas_dgemm_tflops": dgemm},
         "precision": pname,
         "roofline_tc_gram": tc_gram_roofline(m, n, tc_gram_ms) if tc_path else None,
+        "roofline_tc_update": tc_update_roofline(m, n, tc_upd_ms) if tcs else None,
         "forms": forms,
         "path_tflops": fl / (ms * 1e-3) / 1e12,
         "gflops_6mn2": 6 * m * n * n / (ms * 1e-3) / 1e9,

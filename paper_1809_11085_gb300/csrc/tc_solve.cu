@@ -17,21 +17,27 @@
 //  * per entry the tile sums fold exactly into int64, U = sum_{e<=3} D_e
 //    2^{7(3-e)} (< 2^40.1) and T = sum_{e>=4} D_e 2^{7(7-e)} (< 2^42.3), then
 //    W = 2^21 U + floor(T / 2^7) (< 2^61.2, truncation below 2^-56 of
-//    sigma_i tau_l), and x1'_il = x1_il - sigma_i (2^-56 tau_l) W in FP64.
+//    sigma_i tau_l); sigma_i tau_l 2^-56 W is assembled as a double from the
+//    bits of W (integer operations), and x1'_il = x1_il - that, one FP64
+//    subtraction per entry.
 // The computed product differs from y0_i^T r_l by less than about
 // 2^-54 (sigma_i ||r_l||_1 + tau_l ||y0_i||_1), a perturbation of R01 of norm
 // O(u ||R||): the order of the row-wise backward error of FP64 substitution
 // (Eq. backward2) on which the analysis of Sec. 3 rests.
 //
-// Kernel layout: 2 slots of 128 threads (one 128-row tile each, thread r the
-// tile's row r and tensor-memory lane r) plus a producer warp. A slot loads
-// its rows of Y0, cuts them into 8 digit planes (A operand, M = 128 rows, K =
+// Kernel layout: 2 slots of 256 threads (one 128-row tile each; threads r and
+// r + 128 of a slot share the tile's row r and tensor-memory lane r, each with
+// half of the row) plus a producer warp. A slot stages its tile of Y0 in
+// shared memory (coalesced loads, rows padded to 33 words), each thread cuts
+// its half row into 8 digit planes (A operand, M = 128 rows, K =
 // 32, K-major, no swizzle: core matrices of 8 rows x 16 bytes, K step 128 B,
-// 8-row step 512 B), and signals the producer, which issues the 72 MMAs
-// (M = 128, N = 16 or 32, K = 16) of the tile into the slot's 256 columns of
-// tensor memory and commits them to the slot's mbarrier. The slot then reads
-// its row's sums back (tcgen05.ld 32x32b) and writes x1'. While one slot
-// waits for its MMAs the other cuts or applies. Every wait has an iteration
+// 8-row step 512 B) and the slot signals the producer, which issues the 72
+// MMAs (M = 128, N = 16 or 32, K = 16) of the tile into the slot's 256
+// columns of tensor memory and commits them to the slot's mbarrier. Meanwhile
+// the slot stages its tile of x1; then each thread reads its row's sums back
+// (tcgen05.ld 32x32b), updates its row of x1 in shared memory, and the slot
+// writes the tile out coalesced. While one slot waits for its MMAs the other
+// cuts or applies. Every wait has an iteration
 // limit; past it the kernel records SCQR3_E_TIMEOUT, waits (bounded) for its
 // own MMAs and frees its tensor memory.
 #include "tc_common.cuh"
@@ -43,14 +49,30 @@ namespace tcs {
 constexpr int K = 32;                    // columns of the leading block: the contraction length
 constexpr int ROWS = 128;                // rows per tile
 constexpr int SLOTS = 2;                 // tiles in flight per CTA
-constexpr int THREADS = ROWS * SLOTS;    // slot threads (the producer warp comes on top)
+constexpr int SLOT_THREADS = 2 * ROWS;  // two threads per row: each cuts and applies half of it
+constexpr int THREADS = SLOT_THREADS * SLOTS;  // slot threads (the producer warp comes on top)
 constexpr uint32_t LBO = 128;            // K-direction core-matrix stride
 constexpr uint32_t SBO = 512;            // 8-row (A) or 8-column (B) group stride
 constexpr int APLANE = ROWS * K * 2;     // 8 KB per digit plane of a tile
 constexpr int ASLOT = 8 * APLANE;        // 64 KB of A planes per slot
 constexpr int BPLANE = 32 * K * 2;       // 2 KB per digit plane of R01 (N <= 32)
 constexpr uint32_t TSLOT = 256;          // tensor-memory columns per slot: 8 tiles x 32
-constexpr size_t SMEM = SLOTS * (size_t)ASLOT + 8 * (size_t)BPLANE + 1024;  // + alignment slack
+constexpr int YLD = K + 1;               // row stride (doubles) of a slot's staged tile: conflict-free rows
+constexpr int YSLOT = ROWS * YLD * 8;    // 33 KB: the slot's Y0 tile, then its x1 tile
+constexpr size_t SMEM = SLOTS * (size_t)ASLOT + 8 * (size_t)BPLANE + SLOTS * (size_t)YSLOT + 1024;  // + slack
+static_assert(SMEM <= 227 * 1024, "shared memory");
+
+// Barrier among the 256 threads of a slot (ids 1, 2), returning whether any
+// of them passed a non-zero `pred`: decisions that must be uniform in the slot.
+__device__ __forceinline__ int slot_any(int slot, int pred) {
+  int r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.b32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.b32 %0, 1, 0, q;\n}"
+               : "=r"(r) : "r"(pred), "r"(1 + slot), "r"(SLOT_THREADS) : "memory");
+  return r;
+}
+__device__ __forceinline__ void slot_sync(int slot) {
+  asm volatile("bar.sync %0, %1;" :: "r"(1 + slot), "r"(SLOT_THREADS) : "memory");
+}
 
 __device__ __forceinline__ uint64_t desc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
@@ -98,6 +120,22 @@ __device__ __forceinline__ void cut8(const double (&x)[8], int E, uint8_t* dst, 
 #undef SCQR3_CUT
 }
 
+// W 2^e2 as a double, built from the bits of W with integer operations (the
+// FP64 pipe, the scarce one, is left for the update itself): W's leading 53
+// bits (truncated: relative error below 2^-52), exponent 63 - clz(|W|) + e2.
+// Zero for W = 0 or a value below the normal range (an update below 2^-1022),
+// +-Inf above it.
+__device__ __forceinline__ double scaled_int(long long W, int e2) {
+  const unsigned long long sgn = (unsigned long long)W & 0x8000000000000000ull;
+  unsigned long long a = W < 0 ? 0ull - (unsigned long long)W : (unsigned long long)W;
+  const int lz = __clzll((long long)a);
+  a <<= (lz & 63);
+  const int ex = 1023 + 63 - lz + e2;
+  unsigned long long bits = sgn | ((unsigned long long)(ex < 2047 ? ex : 2047) << 52);
+  if (ex < 2047) bits |= (a >> 11) & 0xFFFFFFFFFFFFFull;
+  return (W == 0 || ex <= 0) ? 0.0 : __longlong_as_double((long long)bits);
+}
+
 // Scale exponent of a non-negative bit-pattern maximum: 2^E > the value
 // (-1000 for zero, so every digit is 0).
 __device__ __forceinline__ int scale_exp(unsigned long long mx) {
@@ -134,16 +172,18 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
   extern __shared__ uint8_t dsm[];
   uint8_t* abuf = (uint8_t*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
   uint8_t* bbuf = abuf + SLOTS * ASLOT;
-  __shared__ __align__(8) uint64_t pfull[SLOTS];  // A planes of the slot's tile written (128 arrivals)
+  double* ystage = (double*)(bbuf + 8 * BPLANE);
+  __shared__ __align__(8) uint64_t pfull[SLOTS];  // A planes of the slot's tile written (256 arrivals)
   __shared__ __align__(8) uint64_t mdone[SLOTS];  // MMAs of the slot's tile done (tcgen05.commit)
   __shared__ uint32_t tslot;
-  __shared__ int Eb[32];
-  __shared__ double cscale[32];  // 2^-56 tau_l
+  __shared__ int Eb[32];  // tau_l = 2^Eb[l]
   __shared__ volatile int err_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool producer = warp == THREADS / 32;
-  const int slot = (warp >> 2) & 1;
-  const int r = tid & (ROWS - 1);  // tile row and tensor-memory lane (warp w serves lanes 32 (w % 4) ..)
+  const int slot = (warp >> 3) & 1;
+  const int tis = tid & (SLOT_THREADS - 1);  // thread within the slot
+  const int r = tis & (ROWS - 1);  // tile row and tensor-memory lane (warp w serves lanes 32 (w % 4) ..)
+  const int hf = tis >> 7;         // which half of the row: K groups 2 hf, 2 hf + 1; columns N/2 hf ..
 
   // column scales of R01 (columns >= n1: zero)
   if (tid < 32) {
@@ -154,14 +194,12 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
             (unsigned long long)__double_as_longlong(rk[pk_idx(64, k, 32 + tid)]) & 0x7FFFFFFFFFFFFFFFull;
         mx = mx > b ? mx : b;
       }
-    const int E = scale_exp(mx);
-    Eb[tid] = E;
-    cscale[tid] = mx ? ldexp(1.0, E - 56) : 0.0;
+    Eb[tid] = scale_exp(mx);
   }
   if (tid == 0) {
     err_sh = 0;
     for (int g = 0; g < SLOTS; ++g) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&pfull[g])), "r"(ROWS));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&pfull[g])), "r"(SLOT_THREADS));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mdone[g])), "r"(1));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -212,39 +250,67 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
   } else {
     uint8_t* arow = abuf + slot * ASLOT + (r >> 3) * SBO + (r & 7) * 16;
     const uint32_t tq = tmem + slot * TSLOT + ((uint32_t)(32 * (warp & 3)) << 16);
+    double* ys = ystage + slot * (ROWS * YLD);  // the slot's staged tile: Y0, then x1 / x1'
     for (uint32_t j = 0;; ++j) {
       const int64_t row0 = tile_row0(2 * j + slot);
-      if (row0 < 0 || err_sh) break;
-      const int64_t i = row0 + r;
-      const bool live = i < m;
-      double yv[K];
+      if (slot_any(slot, row0 < 0 || err_sh)) break;
+      const int rows = (int)((m - row0) < ROWS ? (m - row0) : ROWS);
+      // the tile's Y0 rows, coalesced (one row of 32 per warp instruction),
+      // every load in flight before the first store
+      {
+        constexpr int IT = ROWS * K / SLOT_THREADS;
+        double t[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          const int rr = (tis + SLOT_THREADS * it) >> 5;
+          t[it] = rr < rows ? y[(row0 + rr) * ldy + (tis & 31)] : 0.0;
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) >> 5) * YLD + (tis & 31)] = t[it];
+      }
+      slot_sync(slot);
+      // the row's scale from all 32 values; this thread cuts its half
       unsigned long long mx = 0;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        yv[c] = live ? y[i * ldy + c] : 0.0;
-        const unsigned long long b = (unsigned long long)__double_as_longlong(yv[c]) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(ys[r * YLD + c]) & 0x7FFFFFFFFFFFFFFFull;
         mx = mx > b ? mx : b;
       }
       const bool finite = (mx >> 52) != 0x7FF;
       const int E = finite ? scale_exp(mx) : 0;
-      const double sig = ldexp(1.0, E);
 #pragma unroll
-      for (int kg = 0; kg < K / 8; ++kg) {
+      for (int kh = 0; kh < 2; ++kh) {
+        const int kg = 2 * hf + kh;
         double v[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = yv[8 * kg + q];
+        for (int q = 0; q < 8; ++q) v[q] = ys[r * YLD + 8 * kg + q];
         cut8(v, E, arow + kg * LBO, APLANE);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[slot])) : "memory");
-      if (!tc::wait_parity(smem_u32(&mdone[slot]), j & 1)) {
+      slot_sync(slot);  // Y0 read by every thread of the slot
+      // the tile's x1 rows while the tensor core works
+      {
+        constexpr int IT = ROWS * N / SLOT_THREADS;
+        double t[IT];
+        const int c = tis % N;
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          const int rr = (tis + SLOT_THREADS * it) / N;
+          t[it] = (rr < rows && c < n1) ? x1[(row0 + rr) * ldx + c] : 0.0;
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) / N) * YLD + c] = t[it];
+      }
+      const bool ok = tc::wait_parity(smem_u32(&mdone[slot]), j & 1);
+      if (slot_any(slot, !ok)) {  // also: the x1 tile is complete
         err_sh = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-      for (int c0 = 0; c0 < N; c0 += 8) {
+      for (int c0 = hf * (N / 2); c0 < (hf + 1) * (N / 2); c0 += 8) {
         long long U[8], T[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) U[q] = T[q] = 0;
@@ -261,20 +327,26 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
             else T[q] += dv;
           }
         }
-        if (live) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int l = c0 + q;
-            if (l < n1) {
-              const long long W = (U[q] << 21) + (T[q] >> 7);
-              const double upd = __ll2double_rn(W) * cscale[l];
-              const double xv = x1[i * ldx + l];
-              q1[i * ldq + l] = finite ? fma(-upd, sig, xv) : (double)NAN;
-            }
-          }
+        for (int q = 0; q < 8; ++q) {
+          const int l = c0 + q;
+          const long long W = (U[q] << 21) + (T[q] >> 7);
+          const double upd = scaled_int(W, E + Eb[l] - 56);  // sigma_i tau_l 2^-56 W
+          ys[r * YLD + l] = finite ? ys[r * YLD + l] - upd : (double)NAN;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
+      slot_sync(slot);
+      {
+        constexpr int IT = ROWS * N / SLOT_THREADS;
+        const int c = tis % N;
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          const int rr = (tis + SLOT_THREADS * it) / N;
+          if (rr < rows && c < n1) q1[(row0 + rr) * ldq + c] = ys[rr * YLD + c];
+        }
+      }
+      slot_sync(slot);  // the tile is out before the next one is staged
     }
   }
   __syncthreads();

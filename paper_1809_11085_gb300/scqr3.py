@@ -92,6 +92,7 @@ class _Info(ctypes.Structure):
 INFO_BYTES = ctypes.sizeof(_Info)
 
 KERNEL_GRAM, KERNEL_PASS, KERNEL_REDUCE, KERNEL_CHOL, KERNEL_BFACTOR = 0, 1, 2, 3, 4
+KERNEL_TCUPDATE = 7
 KERNEL_NAMES = {0: "pass_kernel(gram)", 1: "pass_kernel(solve+gram)", 2: "reduce_kernel",
                 3: "chol_kernel", 4: "bfactor_kernel", 5: "trsm256_kernel", 6: "df_finish_kernel",
                 7: "tc_update_kernel"}
