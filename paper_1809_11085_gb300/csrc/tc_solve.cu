@@ -31,8 +31,8 @@
 // shared memory (coalesced loads, rows padded to 33 words), each thread cuts
 // its half row into 8 digit planes (A operand, M = 128 rows, K =
 // 32, K-major, no swizzle: core matrices of 8 rows x 16 bytes, K step 128 B,
-// 8-row step 512 B) and the slot signals the producer, which issues the 72
-// MMAs (M = 128, N = 16 or 32, K = 16) of the tile into the slot's 256
+// 8-row step 512 B) and the slot signals the producer, which issues the 16
+// MMAs (M = 128, N = 32 (8 - s), K = 16) of the tile into the slot's 256
 // columns of tensor memory and commits them to the slot's mbarrier. Meanwhile
 // the slot stages its tile of x1; then each thread reads its row's sums back
 // (tcgen05.ld 32x32b), updates its row of x1 in shared memory, and the slot
@@ -79,20 +79,21 @@ __device__ __forceinline__ uint64_t desc(uint32_t addr) {
          ((uint64_t)1 << 46);
 }
 
-// The 72 MMAs of a tile: tile e, digit s of Y0, digit t = e - s of R01, K step kk.
-// Descriptor offsets stay inside the start-address field (all of shared
-// memory lies below 256 KB).
-template <int N, int E, int S, int KK>
-__device__ __forceinline__ void issue(uint64_t adesc, uint64_t bdesc, uint32_t tmem, uint32_t idesc) {
+// The 16 MMAs of a tile: digit s of Y0 (A) against the planes t = 0 .. 7 - s
+// of R01 side by side (B, N = 32 (8 - s): the planes are contiguous, 32
+// columns each), accumulating at tensor-memory column 32 s, so that the pair
+// (s, t) lands in tile e = s + t; K step kk. Descriptor offsets stay inside
+// the start-address field (all of shared memory lies below 256 KB).
+template <int S, int KK>
+__device__ __forceinline__ void issue(uint64_t adesc, uint64_t bdesc, uint32_t tmem, uint32_t idesc0) {
+  constexpr uint32_t NS = 32 * (8 - S);
   constexpr uint64_t aoff = ((uint32_t)S * APLANE + KK * 2 * LBO) >> 4;
-  constexpr uint64_t boff = ((uint32_t)(E - S) * BPLANE + KK * 2 * LBO) >> 4;
-  tc::mma(tmem + 32 * E, adesc + aoff, bdesc + boff, idesc, (S > 0 || KK > 0) ? 1u : 0u);
+  constexpr uint64_t boff = (KK * 2 * LBO) >> 4;
+  tc::mma(tmem + 32 * S, adesc + aoff, bdesc + boff, idesc0 | ((NS >> 3) << 17), (S > 0 || KK > 0) ? 1u : 0u);
   if constexpr (KK == 0) {
-    issue<N, E, S, 1>(adesc, bdesc, tmem, idesc);
-  } else if constexpr (S < E) {
-    issue<N, E, S + 1, 0>(adesc, bdesc, tmem, idesc);
-  } else if constexpr (E < 7) {
-    issue<N, E + 1, 0, 0>(adesc, bdesc, tmem, idesc);
+    issue<S, 1>(adesc, bdesc, tmem, idesc0);
+  } else if constexpr (S < 7) {
+    issue<S + 1, 0>(adesc, bdesc, tmem, idesc0);
   }
 }
 
@@ -222,8 +223,8 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
-  // D F32, A and B BF16, both K-major, N, M = 128
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+  // D F32, A and B BF16, both K-major, M = 128 (N set per MMA)
+  const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 4) << 24);
 
   // this CTA's tiles: ordinal k is tile blockIdx.x + k gridDim.x; slot k % 2
   auto tile_row0 = [&](uint32_t k) -> int64_t {
@@ -241,7 +242,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        issue<N, 0, 0, 0>(desc(smem_u32(abuf + g * ASLOT)), desc(smem_u32(bbuf)), tmem + g * TSLOT, idesc);
+        issue<0, 0>(desc(smem_u32(abuf + g * ASLOT)), desc(smem_u32(bbuf)), tmem + g * TSLOT, idesc0);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(smem_u32(&mdone[g])) : "memory");
         committed = k + 1;
