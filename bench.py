@@ -42,7 +42,22 @@ FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
 PROFILED_KERNEL_SHA = "b447e14d15d0797f"
 PROFILED_BYTES_PER_ROW = 992.3
 PROFILED_SOLVE_BYTES_PER_ROW = 968.7
-PROFILED_BLOCK_BYTES_PER_ROW = None  # pass_kernel<32> on one 32-column block of a 64-column X
+PROFILED_BLOCK_BYTES_PER_ROW = 464.4  # pass_kernel<32> on the first 32-column block of a 64-column X
+# ncu DRAM bytes per row of the tensor-core kernels at 1048576 x 64 (profiles/tc_update_kernel_* and
+# profiles/tc_gram_kernel_*), valid for the sources they were taken on.
+PROFILED_TC = {"tc_solve": ("ae4873aaabbe7a3d", ("tc_common.cuh", "tc_solve.cu"), 740.4),
+               "tc_gram": ("ba3a9f333151bc26", ("tc_common.cuh", "tc_gram.cu"), 516.4)}
+
+
+def profiled_tc_traffic(kind, m, n):
+    """DRAM bytes of one launch of a tensor-core kernel (64-column X), or None."""
+    import hashlib
+
+    sha, files, per_row = PROFILED_TC[kind]
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1809_11085_gb300", "csrc", f), "rb").read())
+    return per_row * m if h.hexdigest()[:16] == sha and n == 64 else None
 
 
 def parse():
@@ -125,7 +140,7 @@ def tc_gram_roofline(m, n, ms_list):
             "achieved": issued / t / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": issued / t / 1e12 / peak,
             "useful_digit_tflops": useful / t / 1e12, "ms_per_gram": statistics.median(ms_list),
             "peak_note": "measured sustained bf16 (MEASURED_PEAKS.json)" if peaks else "fallback",
-            "traffic": None}
+            "traffic": profiled_tc_traffic("tc_gram", m, n)}
 
 
 def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True, block=None):
@@ -170,7 +185,8 @@ def tc_update_roofline(m, n, ms_list):
     return {"bound": "hbm", "kernel": "tc_update_kernel", "achieved": byts / t / 1e9, "peak": peak, "unit": "GB/s",
             "frac": byts / t / 1e9 / peak, "bytes_per_launch": byts, "ms_per_launch": statistics.median(ms_list),
             "tensor_tflops_issued": mma_flops / t / 1e12,
-            "peak_note": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback", "traffic": None}
+            "peak_note": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback",
+            "traffic": profiled_tc_traffic("tc_solve", m, n)}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -439,8 +455,11 @@ def run_gpu(args, rank, world, local_rank):
         f0, f1 = torch.cuda.Event(True), torch.cuda.Event(True)
         t0 = time.perf_counter()
         f0.record(stream)
+        step_ms = []
         for _ in range(ksteps):
+            ts = time.perf_counter()
             _, _, hinf = scqr3.factor_host(Xh, Q=Qh, R=Rh, workspace=hws, precision=prec)
+            step_ms.append(round((time.perf_counter() - ts) * 1e3, 2))
         f1.record(stream)
         torch.cuda.synchronize(dev)
         wall = (time.perf_counter() - t0) * 1e3 / ksteps
@@ -450,7 +469,7 @@ def run_gpu(args, rank, world, local_rank):
         del Qchk
         e2e = {"value": world * m / (ems * 1e-3), "unit": "rows/s", "ms_per_step": ems,
                "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": m * n * 8 + n * n * 8 + scqr3.INFO_BYTES,
-               "status": hinf.status, "passes": hinf.passes,
+               "status": hinf.status, "passes": hinf.passes, "step_ms": step_ms,
                "path": "pinned host X -> scqr3_factor_host (row-chunked copies overlapped with the first "
                        "Gram and the last solve) -> pinned host Q, R, info; synchronous call per step",
                "orth": e2e_orth}
