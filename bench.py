@@ -146,8 +146,8 @@ def tc_gram_roofline(m, n, ms_list):
 def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True, block=None):
     """FP64 flops done by one pass_kernel launch (0 when the device skipped it).
     gram_in_pass=False: the Gram matrices run on the tensor cores, the pass
-    kernel only solves. block = 0 or 1: the launch solves the leading 32
-    columns or the remaining n - 32 (tensor-core substitution, 32 < n <= 64)."""
+    kernel only solves. block = J: the launch solves the J-th 32-column block
+    (tensor-core substitution)."""
     from paper_1809_11085_gb300 import scqr3
 
     if kernel == scqr3.KERNEL_GRAM:
@@ -156,7 +156,7 @@ def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True, block=N
         if pass_idx >= passes:
             return 0
         if block is not None:
-            w = 32 if block == 0 else n - 32
+            w = min(32, n - 32 * block)
             return m * w * w
         f = m * n * n
         if pass_idx < passes - 1 and gram_in_pass:
@@ -168,22 +168,33 @@ def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True, block=N
 def tc_solve_used(prec, n):
     from paper_1809_11085_gb300 import scqr3
 
-    return prec == scqr3.PREC_TC and 32 < n <= 64
+    return prec == scqr3.PREC_TC and n <= 128
 
 
-def tc_update_roofline(m, n, ms_list):
-    """HBM figures of the tensor-core substitution update x1 -= y0 R01: per row
-    it reads y0 (32 values) and x1 (n - 32) and writes x1' (n - 32), 8 bytes each."""
-    if not ms_list:
+def tc_update_cols(n):
+    """Columns updated by each tensor-core update launch of one pass, in launch order."""
+    nb = (n + 31) // 32
+    return [min(32, n - 32 * K) for J in range(nb) for K in range(J + 1, nb)]
+
+
+def tc_update_roofline(m, n, upd):
+    """HBM figures of the tensor-core substitution updates x_K -= y_J R_JK: per
+    row a launch reads y_J (32 values) and x_K (n1 <= 32) and writes x_K' (n1),
+    8 bytes each. upd: (ms, n1) per launch that did work."""
+    if not upd:
         return None
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
-    byts = m * 8 * (32 + 2 * (n - 32))
-    t = statistics.median(ms_list) * 1e-3
-    mma_flops = ((m + 127) // 128) * 72 * 2 * 128 * (16 if n - 32 <= 16 else 32) * 16
+    tsum = sum(t for t, _ in upd) * 1e-3
+    byts_all = sum(m * 8 * (32 + 2 * n1) for _, n1 in upd)
+    byts = byts_all / len(upd)
+    t = tsum / len(upd)
+    # 16 MMAs per 128-row tile: digit s against planes 0..7-s, N = 32 (8 - s), K = 32
+    mma_flops = ((m + 127) // 128) * 2 * 128 * 32 * 36 * 32
     return {"bound": "hbm", "kernel": "tc_update_kernel", "achieved": byts / t / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": byts / t / 1e9 / peak, "bytes_per_launch": byts, "ms_per_launch": statistics.median(ms_list),
+            "frac": byts / t / 1e9 / peak, "bytes_per_launch": byts, "ms_per_launch": t * 1e3,
+            "launches_per_pass": len(tc_update_cols(n)),
             "tensor_tflops_issued": mma_flops / t / 1e12,
             "peak_note": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback",
             "traffic": profiled_tc_traffic("tc_solve", m, n)}
@@ -398,12 +409,14 @@ def run_gpu(args, rank, world, local_rank):
             if p <= passes - 1:
                 tc_gram_ms.append(t)
         if tcs and kernel == scqr3.KERNEL_PASS:
-            block = j % 2
-            name = "pass_kernel<32> (FP64 diagonal blocks)"
+            block = j % ((n + 31) // 32)
+            name = "pass_kernel<32|16> (FP64 diagonal blocks)"
         if tcs and kernel == scqr3.KERNEL_TCUPDATE:
-            name = "tc_update_kernel" if j % 2 == 1 else "tc_split_r_kernel"
-            if j % 2 == 1 and p < passes:
-                tc_upd_ms.append(t)
+            ucols = tc_update_cols(n)
+            jj = j % (len(ucols) + 1)
+            name = "tc_update_kernel" if jj > 0 else "tc_split_r_kernel"
+            if jj > 0 and p < passes:
+                tc_upd_ms.append((t, ucols[jj - 1]))
         share[name] = share.get(name, 0.0) + t
         f = pass_kernel_flops(m, n, kernel, p, passes,
                               gram_in_pass=prec not in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC), block=block)
@@ -530,8 +543,8 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "inputs (%.1f GB) larger than the 129 MB L2; no flush" % (m * n * 8 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu",
-                     "kernel": ("pass_kernel<32> (FP64 DFMA substitution of the two 32-column diagonal blocks; "
-                                "the off-diagonal block on the tensor cores)") if tcs else
+                     "kernel": ("pass_kernel<32|16> (FP64 DFMA substitution of the 32-column diagonal blocks; "
+                                "the off-diagonal blocks on the tensor cores)") if tcs else
                                "pass_kernel<64> (FP64 DFMA%s)" % (", substitution only" if tc_path else ""),
                      "achieved": achieved, "peak": FP64_PEAK_DERIVED_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_DERIVED_TFLOPS) if achieved else None,

@@ -76,11 +76,11 @@ extern "C" {
  * product is exact, sums of 256 rows are exact in the FP32 accumulator, and
  * the digit-pair sums are combined in int64. The Gram error is below about
  * m 2^-55 sigma_j sigma_k, within the norm-wise bound that the shift of
- * Eq. (finds2) covers, so results match the FP64 form to rounding. For
- * 32 < n <= 64 the substitution's off-diagonal block (x1 -= y0 R01 with
- * R = [R00 R01; 0 R11], R00 32 x 32) runs on the tensor cores by the same
- * split, the two triangular blocks in FP64. Not in the paper. n <= 128,
- * m <= 2^31 and B = NULL (else SCQR3_E_UNSUPPORTED). */
+ * Eq. (finds2) covers, so results match the FP64 form to rounding. The
+ * substitution runs in 32-column blocks of R: the triangular diagonal blocks
+ * in FP64, the products with the off-diagonal blocks (x_K -= y_J R_JK) on the
+ * tensor cores by the same split. Not in the paper. n <= 128, m <= 2^31 and
+ * B = NULL (else SCQR3_E_UNSUPPORTED). */
 #define SCQR3_PREC_TC 2
 /* The mixed form's substitution (FP32 pairs) with the Gram matrices of
  * SCQR3_PREC_TC, read directly from the float-pair iterates. n <= 128,
@@ -334,8 +334,8 @@ int scqr3_factor_noalloc(const double *X, int64_t m, int n, int64_t ldx,
 #define SCQR3_KERNEL_TRSM 5     /* Q := Q R_k^{-1} alone (n > 128)          */
 #define SCQR3_KERNEL_FINISH 6   /* mixed form: float-pair Q to FP64, if the
                                    last solve left it in pairs             */
-#define SCQR3_KERNEL_TCUPDATE 7 /* tensor-core form, 32 < n <= 64: split of
-                                   R_k, X1 -= Y0 R01 on the tensor cores   */
+#define SCQR3_KERNEL_TCUPDATE 7 /* tensor-core form: diagonal blocks of R_k,
+                                   X_K -= Y_J R_JK on the tensor cores     */
 
 typedef struct {
   int kernel;  /* SCQR3_KERNEL_*                                          */

@@ -50,10 +50,11 @@ void launch_csr_gram(int np, int grid, cudaStream_t s, const double* src, int64_
 cudaError_t tc_setup();
 int tc_grid(int64_t m, int np, int sms);
 cudaError_t tc_solve_setup();
-void launch_tc_split_r(cudaStream_t s, const double* rk, int np1, int pass, const DevState* st, double* r00,
-                       double* r11);
+void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int pass, const DevState* st,
+                       double* rdiag);
 void launch_tc_update(int sms, cudaStream_t s, const double* y, int64_t ldy, const double* x1, int64_t ldx,
-                      double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, DevState* st);
+                      double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np, int r0,
+                      int c0, DevState* st);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs);
 
@@ -285,7 +286,7 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
   L->colmax = off;
   off = align256(off + sizeof(unsigned long long) * 128);
   L->tcr = off;
-  off = align256(off + sizeof(double) * 2 * pk_size(32));
+  off = align256(off + sizeof(double) * 4 * pk_size(32));
   L->lt = off;
   if (B && B->bs > 0) {
     const int64_t nblk = m / B->bs;
@@ -408,7 +409,7 @@ struct Call {
   double *gram = nullptr, *rstack = nullptr, *racc = nullptr, *lt = nullptr, *partials = nullptr;
   double *S = nullptr, *Ra = nullptr;  // n = 256: Cholesky work buffers
   unsigned long long* colmax = nullptr;  // tensor-core Gram: column scales
-  double* tcr = nullptr;                 // tensor-core substitution: R00, R11 packed
+  double* tcr = nullptr;                 // tensor-core substitution: diagonal blocks of R_k, packed
   double *R = nullptr, *Rpass = nullptr;
   scqr3_info* info = nullptr;
 };
@@ -523,30 +524,36 @@ int pass_grid(int np, int64_t m) {
   return (int)(pn < gm ? (pn < 1 ? 1 : pn) : gm);
 }
 
-// The tensor-core form's substitution for 32 < n <= 64: with R_k = [R00 R01;
-// 0 R11], Y0 = X0 R00^{-1} (FP64), X1 := X1 - Y0 R01 (tensor cores, exact
-// digit split), Y1 = X1 R11^{-1} (FP64).
+// The tensor-core form's substitution (n <= 128) in 32-column blocks: for
+// J = 0, 1, ..: Y_J = X_J R_JJ^{-1} (FP64 pass kernel), then X_K := X_K -
+// Y_J R_JK for every later 32-column block K (tensor cores, exact digit
+// split). Block 0 reads the pass's input; every later block is updated and
+// solved in place in the output.
 void tc_solve_rows(Call& c, int k, const double* rk, const double* src, int64_t lds, double* dst, int64_t ldd,
                    const Params& Pc) {
-  const int n1 = Pc.n - 32, np1 = n1 <= 16 ? 16 : 32;
-  double* r00 = c.tcr;
-  double* r11 = c.tcr + pk_size(32);
+  const int n = Pc.n, nb = (n + 31) / 32;
   tick(c.s, SCQR3_KERNEL_TCUPDATE, k);
-  launch_tc_split_r(c.s, rk, np1, k, c.st, r00, r11);
-  tick(c.s, SCQR3_KERNEL_PASS, k);
-  Params P0 = Pc;
-  P0.n = 32;
-  P0.np = 32;
-  launch_pass(32, pass_grid(32, Pc.m), c.s, src, lds, dst, ldd, P0, k, r00, nullptr, c.partials, c.L.part_stride,
-              c.st);
-  tick(c.s, SCQR3_KERNEL_TCUPDATE, k);
-  launch_tc_update(sm_count(), c.s, dst, ldd, src + 32, lds, dst + 32, ldd, Pc.m, n1, k, rk, c.st);
-  tick(c.s, SCQR3_KERNEL_PASS, k);
-  Params P1 = Pc;
-  P1.n = n1;
-  P1.np = np1;
-  launch_pass(np1, pass_grid(np1, Pc.m), c.s, dst + 32, ldd, dst + 32, ldd, P1, k, r11, nullptr, c.partials,
-              c.L.part_stride, c.st);
+  launch_tc_split_r(c.s, rk, c.P.np, n, k, c.st, c.tcr);
+  for (int J = 0; J < nb; ++J) {
+    const int w = n - 32 * J < 32 ? n - 32 * J : 32;
+    const int npj = w <= 16 ? 16 : 32;
+    Params PJ = Pc;
+    PJ.n = w;
+    PJ.np = npj;
+    tick(c.s, SCQR3_KERNEL_PASS, k);
+    const double* in = J == 0 ? src + 0 : dst + 32 * J;
+    const int64_t ldin = J == 0 ? lds : ldd;
+    launch_pass(npj, pass_grid(npj, Pc.m), c.s, in, ldin, dst + 32 * J, ldd, PJ, k, c.tcr + J * pk_size(32),
+                nullptr, c.partials, c.L.part_stride, c.st);
+    for (int K = J + 1; K < nb; ++K) {
+      const int n1 = n - 32 * K < 32 ? n - 32 * K : 32;
+      tick(c.s, SCQR3_KERNEL_TCUPDATE, k);
+      const double* x1 = J == 0 ? src + 32 * K : dst + 32 * K;
+      const int64_t ldx1 = J == 0 ? lds : ldd;
+      launch_tc_update(sm_count(), c.s, dst + 32 * J, ldd, x1, ldx1, dst + 32 * K, ldd, Pc.m, n1, k, rk, c.P.np,
+                       32 * J, 32 * K, c.st);
+    }
+  }
 }
 
 void solve_rows(Call& c, int k, const double* src, int64_t lds, double* dst, int64_t ldd, int64_t r0,
@@ -556,7 +563,7 @@ void solve_rows(Call& c, int k, const double* src, int64_t lds, double* dst, int
   src += r0 * lds;
   dst += r0 * ldd;
   const double* rk = c.rstack + (size_t)k * pk_size(c.P.np);
-  if (c.tc && !c.mixed && c.P.np == 64 && c.P.n > 32) {
+  if (c.tc && !c.mixed) {
     tc_solve_rows(c, k, rk, src, lds, dst, ldd, Pc);
     return;
   }

@@ -1,14 +1,15 @@
 // tc_solve.cu -- the row-wise substitution Q := X R^{-1} (Eq. backward2) for
-// 32 < n <= 64 with its off-diagonal block on the tensor cores.
+// n <= 128 with its off-diagonal blocks on the tensor cores.
 //
-// Blocking R = [R00 R01; 0 R11] (R00 the leading 32 x 32 block) splits the
-// substitution of each row x^T = [x0^T x1^T] into
-//   y0^T = x0^T R00^{-1},   x1'^T = x1^T - y0^T R01,   y1^T = x1'^T R11^{-1}:
+// Blocking R in 32-column blocks R_IJ splits the substitution of each row
+// x^T = [x_0^T .. x_{nb-1}^T] into, for J = 0, 1, ..:
+//   y_J^T = x_J^T R_JJ^{-1},   x_K^T := x_K^T - y_J^T R_JK  (K > J):
 // the same terms forward substitution over columns takes, grouped by block.
-// The two triangular solves run in FP64 on the pass kernel over 32-column
-// blocks. The product y0^T R01 -- half of the substitution's flops, and a
-// dense contraction -- runs here on the BF16 tensor cores through the exact
-// digit split of the Gram kernel:
+// The triangular solves run in FP64 on the pass kernel over 32-column
+// blocks. The products y_J^T R_JK -- most of the substitution's flops, and
+// dense contractions -- run here (one 32-column block K per launch; written
+// below for the first pair, Y0 = Y_J and R01 = R_JK) on the BF16 tensor cores
+// through the exact digit split of the Gram kernel:
 //  * row i of Y0 gets the scale sigma_i = 2^E_i > max_k |y_ik| (its own 32
 //    values), column l of R01 the scale tau_l = 2^E_l > max_k |r_kl|;
 //  * both are cut into eight signed 7-bit digits (56 bits); digit products are
@@ -147,26 +148,32 @@ __device__ __forceinline__ int scale_exp(unsigned long long mx) {
 
 }  // namespace tcs
 
-// R00 and R11 of the packed 64 x 64 R_k as packed 32 x 32 and np1 x np1
-// (np1 = 16 or 32; the padding of R_k is the identity, and so is theirs).
-__global__ void tc_split_r_kernel(const double* __restrict__ rk, int np1, int pass, const DevState* __restrict__ st,
-                                  double* __restrict__ r00, double* __restrict__ r11) {
+// The diagonal blocks R_JJ (32 columns each, the last one w = n - 32 J
+// wide) of the packed np x np R_k, each packed 32 x 32 (16 x 16 when w <= 16)
+// at rdiag + J * pk_size(32); the padding of R_k is the identity, and so is
+// theirs.
+__global__ void tc_split_r_kernel(const double* __restrict__ rk, int np, int n, int pass,
+                                  const DevState* __restrict__ st, double* __restrict__ rdiag) {
   if (!st->run_trsm[pass]) return;
-  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-    const int j = e / 32, k = e % 32;
-    if (k < j) continue;
-    r00[pk_idx(32, j, k)] = rk[pk_idx(64, j, k)];
-    if (k < np1) r11[pk_idx(np1, j, k)] = rk[pk_idx(64, 32 + j, 32 + k)];
+  const int nb = (n + 31) / 32;
+  for (int e = threadIdx.x; e < nb * 32 * 32; e += blockDim.x) {
+    const int J = e >> 10, j = (e >> 5) & 31, k = e & 31;
+    const int w = n - 32 * J < 32 ? n - 32 * J : 32;
+    const int npj = w <= 16 ? 16 : 32;
+    if (k < j || k >= npj) continue;
+    rdiag[J * pk_size(32) + pk_idx(npj, j, k)] = rk[pk_idx(np, 32 * J + j, 32 * J + k)];
   }
 }
 
 // x1' = x1 - Y0 R01 for rows [0, m): y holds Y0 (32 columns), x1 and q1 the
-// columns 32 .. 32 + n1 - 1 of the pass's input and output (they may be the
-// same memory); rk is R_k packed 64 x 64.
+// n1 <= 32 columns to update of the pass's input and output (they may be the
+// same memory); R01 is rows r0 .. r0 + 31, columns c0 .. c0 + n1 - 1 of R_k,
+// packed np x np.
 template <int N>
 __global__ void __launch_bounds__(tcs::THREADS + 32, 1)
 tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, int64_t ldx, double* q1, int64_t ldq,
-                 int64_t m, int n1, int pass, const double* __restrict__ rk, DevState* __restrict__ st) {
+                 int64_t m, int n1, int pass, const double* __restrict__ rk, int np, int r0, int c0,
+                 DevState* __restrict__ st) {
   using namespace tcs;
   using tc::smem_u32;
   if (!st->run_trsm[pass]) return;
@@ -192,7 +199,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
     if (tid < n1)
       for (int k = 0; k < K; ++k) {
         const unsigned long long b =
-            (unsigned long long)__double_as_longlong(rk[pk_idx(64, k, 32 + tid)]) & 0x7FFFFFFFFFFFFFFFull;
+            (unsigned long long)__double_as_longlong(rk[pk_idx(np, r0 + k, c0 + tid)]) & 0x7FFFFFFFFFFFFFFFull;
         mx = mx > b ? mx : b;
       }
     Eb[tid] = scale_exp(mx);
@@ -215,7 +222,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
     const int l = u % N, kg = u / N;
     double v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = l < n1 ? rk[pk_idx(64, 8 * kg + q, 32 + l)] : 0.0;
+    for (int q = 0; q < 8; ++q) v[q] = l < n1 ? rk[pk_idx(np, r0 + 8 * kg + q, c0 + l)] : 0.0;
     cut8(v, Eb[l], bbuf + (l >> 3) * SBO + kg * LBO + (l & 7) * 16, BPLANE);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -374,20 +381,23 @@ cudaError_t tc_solve_setup() {
   return cudaFuncSetAttribute(tc_update_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcs::SMEM);
 }
 
-void launch_tc_split_r(cudaStream_t s, const double* rk, int np1, int pass, const DevState* st, double* r00,
-                       double* r11) {
-  tc_split_r_kernel<<<1, 256, 0, s>>>(rk, np1, pass, st, r00, r11);
+void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int pass, const DevState* st,
+                       double* rdiag) {
+  tc_split_r_kernel<<<1, 256, 0, s>>>(rk, np, n, pass, st, rdiag);
 }
 
-// x1' = x1 - Y0 R01 over rows [0, m); n1 = n - 32 in 1 .. 32.
+// x1' = x1 - Y0 R01 over rows [0, m); n1 in 1 .. 32 columns; R01 at (r0, c0) of R_k (packed np).
 void launch_tc_update(int sms, cudaStream_t s, const double* y, int64_t ldy, const double* x1, int64_t ldx,
-                      double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, DevState* st) {
+                      double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np, int r0,
+                      int c0, DevState* st) {
   const int64_t tiles = (m + tcs::ROWS - 1) / tcs::ROWS;
   const int grid = (int)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
   if (n1 <= 16)
-    tc_update_kernel<16><<<grid, tcs::THREADS + 32, tcs::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, pass, rk, st);
+    tc_update_kernel<16><<<grid, tcs::THREADS + 32, tcs::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, pass, rk, np,
+                                                                    r0, c0, st);
   else
-    tc_update_kernel<32><<<grid, tcs::THREADS + 32, tcs::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, pass, rk, st);
+    tc_update_kernel<32><<<grid, tcs::THREADS + 32, tcs::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, pass, rk, np,
+                                                                    r0, c0, st);
 }
 
 }  // namespace scqr3
