@@ -98,7 +98,7 @@ def profiled_traffic(m, n, solve_only=False, tcs=False):
     if sha != PROFILED_KERNEL_SHA or n != 64:
         return None
     if tcs:
-        return PROFILED_BLOCK_BYTES_PER_ROW * m if PROFILED_BLOCK_BYTES_PER_ROW else None
+        return PROFILED_BLOCK_BYTES_PER_ROW * m if PROFILED_BLOCK_BYTES_PER_ROW and tc_block_width(n) == 32 else None
     return (PROFILED_SOLVE_BYTES_PER_ROW if solve_only else PROFILED_BYTES_PER_ROW) * m
 
 
@@ -156,7 +156,8 @@ def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True, block=N
         if pass_idx >= passes:
             return 0
         if block is not None:
-            w = min(32, n - 32 * block)
+            bw = tc_block_width(n)
+            w = min(bw, n - bw * block)
             return m * w * w
         f = m * n * n
         if pass_idx < passes - 1 and gram_in_pass:
@@ -171,27 +172,33 @@ def tc_solve_used(prec, n):
     return prec == scqr3.PREC_TC and n <= 128
 
 
+def tc_block_width(n):
+    """Diagonal-block width of the tensor-core substitution (the library's choice)."""
+    return 16 if n <= 64 else 32
+
+
 def tc_update_cols(n):
-    """Columns updated by each tensor-core update launch of one pass, in launch order."""
-    nb = (n + 31) // 32
-    return [min(32, n - 32 * K) for J in range(nb) for K in range(J + 1, nb)]
+    """(block width, columns updated) of each tensor-core update launch of one pass, in launch order."""
+    w = tc_block_width(n)
+    nb = (n + w - 1) // w
+    return [(w, min(32, n - c0)) for J in range(nb) for c0 in range(w * (J + 1), n, 32)]
 
 
 def tc_update_roofline(m, n, upd):
     """HBM figures of the tensor-core substitution updates x_K -= y_J R_JK: per
-    row a launch reads y_J (32 values) and x_K (n1 <= 32) and writes x_K' (n1),
-    8 bytes each. upd: (ms, n1) per launch that did work."""
+    row a launch reads y_J (k = 16 or 32 values) and x_K (n1 <= 32) and writes
+    x_K' (n1), 8 bytes each. upd: (ms, (k, n1)) per launch that did work."""
     if not upd:
         return None
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     tsum = sum(t for t, _ in upd) * 1e-3
-    byts_all = sum(m * 8 * (32 + 2 * n1) for _, n1 in upd)
+    byts_all = sum(m * 8 * (k + 2 * n1) for _, (k, n1) in upd)
     byts = byts_all / len(upd)
     t = tsum / len(upd)
-    # 16 MMAs per 128-row tile: digit s against planes 0..7-s, N = 32 (8 - s), K = 32
-    mma_flops = ((m + 127) // 128) * 2 * 128 * 32 * 36 * 32
+    # per 128-row tile: digit s against planes 0..7-s, N = 32 (8 - s), contraction k
+    mma_flops = sum(((m + 127) // 128) * 2 * 128 * 32 * 36 * k for _, (k, _) in upd) / len(upd)
     return {"bound": "hbm", "kernel": "tc_update_kernel", "achieved": byts / t / 1e9, "peak": peak, "unit": "GB/s",
             "frac": byts / t / 1e9 / peak, "bytes_per_launch": byts, "ms_per_launch": t * 1e3,
             "launches_per_pass": len(tc_update_cols(n)),
@@ -409,7 +416,7 @@ def run_gpu(args, rank, world, local_rank):
             if p <= passes - 1:
                 tc_gram_ms.append(t)
         if tcs and kernel == scqr3.KERNEL_PASS:
-            block = j % ((n + 31) // 32)
+            block = j % ((n + tc_block_width(n) - 1) // tc_block_width(n))
             name = "pass_kernel<32|16> (FP64 diagonal blocks)"
         if tcs and kernel == scqr3.KERNEL_TCUPDATE:
             ucols = tc_update_cols(n)

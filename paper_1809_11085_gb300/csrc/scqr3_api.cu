@@ -50,11 +50,11 @@ void launch_csr_gram(int np, int grid, cudaStream_t s, const double* src, int64_
 cudaError_t tc_setup();
 int tc_grid(int64_t m, int np, int sms);
 cudaError_t tc_solve_setup();
-void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int pass, const DevState* st,
+void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int w, int pass, const DevState* st,
                        double* rdiag);
-void launch_tc_update(int sms, cudaStream_t s, const double* y, int64_t ldy, const double* x1, int64_t ldx,
-                      double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np, int r0,
-                      int c0, DevState* st);
+void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t ldy, const double* x1,
+                      int64_t ldx, double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np,
+                      int r0, int c0, DevState* st);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs);
 
@@ -286,7 +286,7 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
   L->colmax = off;
   off = align256(off + sizeof(unsigned long long) * 128);
   L->tcr = off;
-  off = align256(off + sizeof(double) * 4 * pk_size(32));
+  off = align256(off + sizeof(double) * 8 * pk_size(32));
   L->lt = off;
   if (B && B->bs > 0) {
     const int64_t nblk = m / B->bs;
@@ -524,34 +524,38 @@ int pass_grid(int np, int64_t m) {
   return (int)(pn < gm ? (pn < 1 ? 1 : pn) : gm);
 }
 
-// The tensor-core form's substitution (n <= 128) in 32-column blocks: for
+// Width of the diagonal blocks of the tensor-core substitution: 16 columns
+// halve the FP64 work again but multiply the tensor-core updates.
+int tc_block_width(int n) { return n <= 64 ? 16 : 32; }
+
+// The tensor-core form's substitution (n <= 128) in blocks of w columns: for
 // J = 0, 1, ..: Y_J = X_J R_JJ^{-1} (FP64 pass kernel), then X_K := X_K -
-// Y_J R_JK for every later 32-column block K (tensor cores, exact digit
+// Y_J R_JK for the later columns, 32 at a time (tensor cores, exact digit
 // split). Block 0 reads the pass's input; every later block is updated and
 // solved in place in the output.
 void tc_solve_rows(Call& c, int k, const double* rk, const double* src, int64_t lds, double* dst, int64_t ldd,
                    const Params& Pc) {
-  const int n = Pc.n, nb = (n + 31) / 32;
+  const int n = Pc.n, w = tc_block_width(n), nb = (n + w - 1) / w;
   tick(c.s, SCQR3_KERNEL_TCUPDATE, k);
-  launch_tc_split_r(c.s, rk, c.P.np, n, k, c.st, c.tcr);
+  launch_tc_split_r(c.s, rk, c.P.np, n, w, k, c.st, c.tcr);
   for (int J = 0; J < nb; ++J) {
-    const int w = n - 32 * J < 32 ? n - 32 * J : 32;
-    const int npj = w <= 16 ? 16 : 32;
+    const int wj = n - w * J < w ? n - w * J : w;
+    const int npj = wj <= 16 ? 16 : 32;
     Params PJ = Pc;
-    PJ.n = w;
+    PJ.n = wj;
     PJ.np = npj;
     tick(c.s, SCQR3_KERNEL_PASS, k);
-    const double* in = J == 0 ? src + 0 : dst + 32 * J;
+    const double* in = J == 0 ? src : dst + w * J;
     const int64_t ldin = J == 0 ? lds : ldd;
-    launch_pass(npj, pass_grid(npj, Pc.m), c.s, in, ldin, dst + 32 * J, ldd, PJ, k, c.tcr + J * pk_size(32),
+    launch_pass(npj, pass_grid(npj, Pc.m), c.s, in, ldin, dst + w * J, ldd, PJ, k, c.tcr + J * pk_size(32),
                 nullptr, c.partials, c.L.part_stride, c.st);
-    for (int K = J + 1; K < nb; ++K) {
-      const int n1 = n - 32 * K < 32 ? n - 32 * K : 32;
+    for (int c0 = w * (J + 1); c0 < n; c0 += 32) {
+      const int n1 = n - c0 < 32 ? n - c0 : 32;
       tick(c.s, SCQR3_KERNEL_TCUPDATE, k);
-      const double* x1 = J == 0 ? src + 32 * K : dst + 32 * K;
+      const double* x1 = J == 0 ? src + c0 : dst + c0;
       const int64_t ldx1 = J == 0 ? lds : ldd;
-      launch_tc_update(sm_count(), c.s, dst + 32 * J, ldd, x1, ldx1, dst + 32 * K, ldd, Pc.m, n1, k, rk, c.P.np,
-                       32 * J, 32 * K, c.st);
+      launch_tc_update(sm_count(), c.s, w, dst + w * J, ldd, x1, ldx1, dst + c0, ldd, Pc.m, n1, k, rk, c.P.np,
+                       w * J, c0, c.st);
     }
   }
 }

@@ -60,7 +60,7 @@ struct Layout {
   int csr_grid;      // CTAs of csr_gram_kernel (CSR form only)
   int tc_grid;       // CTAs of tc_gram_kernel (tensor-core Gram only)
   size_t colmax;     // tensor-core Gram: per-column max |q_ij| (128 words)
-  size_t tcr;        // tensor-core substitution: the diagonal blocks of R_k packed 32 x 32 (4 x 528 doubles)
+  size_t tcr;        // tensor-core substitution: the diagonal blocks of R_k packed 32 x 32 (8 x 528 doubles)
   int part_stride;   // doubles per partial slot: pk_size(np) + 1 (||.||_F^2)
 };
 

@@ -47,21 +47,25 @@ namespace scqr3 {
 
 namespace tcs {
 
-constexpr int K = 32;                    // columns of the leading block: the contraction length
 constexpr int ROWS = 128;                // rows per tile
 constexpr int SLOTS = 2;                 // tiles in flight per CTA
 constexpr int SLOT_THREADS = 2 * ROWS;  // two threads per row: each cuts and applies half of it
 constexpr int THREADS = SLOT_THREADS * SLOTS;  // slot threads (the producer warp comes on top)
 constexpr uint32_t LBO = 128;            // K-direction core-matrix stride
-constexpr uint32_t SBO = 512;            // 8-row (A) or 8-column (B) group stride
-constexpr int APLANE = ROWS * K * 2;     // 8 KB per digit plane of a tile
-constexpr int ASLOT = 8 * APLANE;        // 64 KB of A planes per slot
-constexpr int BPLANE = 32 * K * 2;       // 2 KB per digit plane of R01 (N <= 32)
 constexpr uint32_t TSLOT = 256;          // tensor-memory columns per slot: 8 tiles x 32
-constexpr int YLD = K + 1;               // row stride (doubles) of a slot's staged tile: conflict-free rows
-constexpr int YSLOT = ROWS * YLD * 8;    // 33 KB: the slot's Y0 tile, then its x1 tile
-constexpr size_t SMEM = SLOTS * (size_t)ASLOT + 8 * (size_t)BPLANE + SLOTS * (size_t)YSLOT + 1024;  // + slack
-static_assert(SMEM <= 227 * 1024, "shared memory");
+constexpr int YLD = 33;                  // row stride (doubles) of a slot's staged tile: conflict-free rows
+constexpr int YSLOT = ROWS * YLD * 8;    // 33 KB: the slot's Y tile, then its x tile (<= 32 columns each)
+
+// Geometry for a block of K = 16 or 32 columns (the contraction length).
+template <int K>
+struct UGeo {
+  static constexpr uint32_t SBO = 16 * K;     // 8-row (A) or 8-column (B) group stride: K / 8 core matrices
+  static constexpr int APLANE = ROWS * K * 2;  // per digit plane of a tile (8 KB for K = 32)
+  static constexpr int ASLOT = 8 * APLANE;     // the slot's 8 planes
+  static constexpr int BPLANE = 32 * K * 2;    // per digit plane of R_JK (32 columns)
+  static constexpr size_t SMEM = SLOTS * (size_t)ASLOT + 8 * (size_t)BPLANE + SLOTS * (size_t)YSLOT + 1024;
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
 
 // Barrier among the 256 threads of a slot (ids 1, 2), returning whether any
 // of them passed a non-zero `pred`: decisions that must be uniform in the slot.
@@ -75,8 +79,9 @@ __device__ __forceinline__ void slot_sync(int slot) {
   asm volatile("bar.sync %0, %1;" :: "r"(1 + slot), "r"(SLOT_THREADS) : "memory");
 }
 
+template <int K>
 __device__ __forceinline__ uint64_t desc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(UGeo<K>::SBO >> 4) << 32) |
          ((uint64_t)1 << 46);
 }
 
@@ -85,16 +90,16 @@ __device__ __forceinline__ uint64_t desc(uint32_t addr) {
 // columns each), accumulating at tensor-memory column 32 s, so that the pair
 // (s, t) lands in tile e = s + t; K step kk. Descriptor offsets stay inside
 // the start-address field (all of shared memory lies below 256 KB).
-template <int S, int KK>
+template <int K, int S, int KK>
 __device__ __forceinline__ void issue(uint64_t adesc, uint64_t bdesc, uint32_t tmem, uint32_t idesc0) {
   constexpr uint32_t NS = 32 * (8 - S);
-  constexpr uint64_t aoff = ((uint32_t)S * APLANE + KK * 2 * LBO) >> 4;
+  constexpr uint64_t aoff = ((uint32_t)S * UGeo<K>::APLANE + KK * 2 * LBO) >> 4;
   constexpr uint64_t boff = (KK * 2 * LBO) >> 4;
   tc::mma(tmem + 32 * S, adesc + aoff, bdesc + boff, idesc0 | ((NS >> 3) << 17), (S > 0 || KK > 0) ? 1u : 0u);
-  if constexpr (KK == 0) {
-    issue<S, 1>(adesc, bdesc, tmem, idesc0);
+  if constexpr (KK + 1 < K / 16) {
+    issue<K, S, KK + 1>(adesc, bdesc, tmem, idesc0);
   } else if constexpr (S < 7) {
-    issue<S + 1, 0>(adesc, bdesc, tmem, idesc0);
+    issue<K, S + 1, 0>(adesc, bdesc, tmem, idesc0);
   }
 }
 
@@ -148,20 +153,20 @@ __device__ __forceinline__ int scale_exp(unsigned long long mx) {
 
 }  // namespace tcs
 
-// The diagonal blocks R_JJ (32 columns each, the last one w = n - 32 J
-// wide) of the packed np x np R_k, each packed 32 x 32 (16 x 16 when w <= 16)
-// at rdiag + J * pk_size(32); the padding of R_k is the identity, and so is
-// theirs.
-__global__ void tc_split_r_kernel(const double* __restrict__ rk, int np, int n, int pass,
+// The diagonal blocks R_JJ (w = 16 or 32 columns each, the last one n - w J
+// wide) of the packed np x np R_k, each packed 32 x 32 (16 x 16 when at most
+// 16 wide) at rdiag + J * pk_size(32); the padding of R_k is the identity,
+// and so is theirs.
+__global__ void tc_split_r_kernel(const double* __restrict__ rk, int np, int n, int w, int pass,
                                   const DevState* __restrict__ st, double* __restrict__ rdiag) {
   if (!st->run_trsm[pass]) return;
-  const int nb = (n + 31) / 32;
+  const int nb = (n + w - 1) / w;
   for (int e = threadIdx.x; e < nb * 32 * 32; e += blockDim.x) {
     const int J = e >> 10, j = (e >> 5) & 31, k = e & 31;
-    const int w = n - 32 * J < 32 ? n - 32 * J : 32;
-    const int npj = w <= 16 ? 16 : 32;
+    const int wj = n - w * J < w ? n - w * J : w;
+    const int npj = wj <= 16 ? 16 : 32;
     if (k < j || k >= npj) continue;
-    rdiag[J * pk_size(32) + pk_idx(npj, j, k)] = rk[pk_idx(np, 32 * J + j, 32 * J + k)];
+    rdiag[J * pk_size(32) + pk_idx(npj, j, k)] = rk[pk_idx(np, w * J + j, w * J + k)];
   }
 }
 
@@ -169,13 +174,15 @@ __global__ void tc_split_r_kernel(const double* __restrict__ rk, int np, int n, 
 // n1 <= 32 columns to update of the pass's input and output (they may be the
 // same memory); R01 is rows r0 .. r0 + 31, columns c0 .. c0 + n1 - 1 of R_k,
 // packed np x np.
-template <int N>
+template <int K, int N>
 __global__ void __launch_bounds__(tcs::THREADS + 32, 1)
 tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, int64_t ldx, double* q1, int64_t ldq,
                  int64_t m, int n1, int pass, const double* __restrict__ rk, int np, int r0, int c0,
                  DevState* __restrict__ st) {
   using namespace tcs;
   using tc::smem_u32;
+  constexpr uint32_t SBO = UGeo<K>::SBO;
+  constexpr int APLANE = UGeo<K>::APLANE, ASLOT = UGeo<K>::ASLOT, BPLANE = UGeo<K>::BPLANE;
   if (!st->run_trsm[pass]) return;
   extern __shared__ uint8_t dsm[];
   uint8_t* abuf = (uint8_t*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
@@ -191,7 +198,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
   const int slot = (warp >> 3) & 1;
   const int tis = tid & (SLOT_THREADS - 1);  // thread within the slot
   const int r = tis & (ROWS - 1);  // tile row and tensor-memory lane (warp w serves lanes 32 (w % 4) ..)
-  const int hf = tis >> 7;         // which half of the row: K groups 2 hf, 2 hf + 1; columns N/2 hf ..
+  const int hf = tis >> 7;         // which half of the row: K groups hf K/16 ..; columns N/2 hf ..
 
   // column scales of R01 (columns >= n1: zero)
   if (tid < 32) {
@@ -217,9 +224,9 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   __syncthreads();
-  // R01 digit planes (B operand: N columns x 32 rows, K-major)
-  for (int u = tid; u < N * (K / 8); u += THREADS + 32) {
-    const int l = u % N, kg = u / N;
+  // R_JK digit planes (B operand: 32 columns, zero past n1, x K rows, K-major)
+  for (int u = tid; u < 32 * (K / 8); u += THREADS + 32) {
+    const int l = u & 31, kg = u >> 5;
     double v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = l < n1 ? rk[pk_idx(np, r0 + 8 * kg + q, c0 + l)] : 0.0;
@@ -249,7 +256,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        issue<0, 0>(desc(smem_u32(abuf + g * ASLOT)), desc(smem_u32(bbuf)), tmem + g * TSLOT, idesc0);
+        issue<K, 0, 0>(desc<K>(smem_u32(abuf + g * ASLOT)), desc<K>(smem_u32(bbuf)), tmem + g * TSLOT, idesc0);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(smem_u32(&mdone[g])) : "memory");
         committed = k + 1;
@@ -263,21 +270,21 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
       const int64_t row0 = tile_row0(2 * j + slot);
       if (slot_any(slot, row0 < 0 || err_sh)) break;
       const int rows = (int)((m - row0) < ROWS ? (m - row0) : ROWS);
-      // the tile's Y0 rows, coalesced (one row of 32 per warp instruction),
+      // the tile's Y rows, coalesced (one row of K per warp or half warp),
       // every load in flight before the first store
       {
         constexpr int IT = ROWS * K / SLOT_THREADS;
         double t[IT];
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
-          const int rr = (tis + SLOT_THREADS * it) >> 5;
-          t[it] = rr < rows ? y[(row0 + rr) * ldy + (tis & 31)] : 0.0;
+          const int rr = (tis + SLOT_THREADS * it) / K;
+          t[it] = rr < rows ? y[(row0 + rr) * ldy + (tis % K)] : 0.0;
         }
 #pragma unroll
-        for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) >> 5) * YLD + (tis & 31)] = t[it];
+        for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) / K) * YLD + (tis % K)] = t[it];
       }
       slot_sync(slot);
-      // the row's scale from all 32 values; this thread cuts its half
+      // the row's scale from all K values; this thread cuts its half
       unsigned long long mx = 0;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
@@ -287,8 +294,8 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
       const bool finite = (mx >> 52) != 0x7FF;
       const int E = finite ? scale_exp(mx) : 0;
 #pragma unroll
-      for (int kh = 0; kh < 2; ++kh) {
-        const int kg = 2 * hf + kh;
+      for (int kh = 0; kh < K / 16; ++kh) {
+        const int kg = (K / 16) * hf + kh;
         double v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = ys[r * YLD + 8 * kg + q];
@@ -375,29 +382,43 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
 // ---- host side ----------------------------------------------------------------------------
 
 cudaError_t tc_solve_setup() {
-  cudaError_t e = cudaFuncSetAttribute(tc_update_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tcs::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_update_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcs::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(tc_update_kernel<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tcs::UGeo<16>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_update_kernel<16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tcs::UGeo<16>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_update_kernel<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tcs::UGeo<32>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_update_kernel<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tcs::UGeo<32>::SMEM);
+  return e;
 }
 
-void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int pass, const DevState* st,
+void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int w, int pass, const DevState* st,
                        double* rdiag) {
-  tc_split_r_kernel<<<1, 256, 0, s>>>(rk, np, n, pass, st, rdiag);
+  tc_split_r_kernel<<<1, 256, 0, s>>>(rk, np, n, w, pass, st, rdiag);
 }
 
-// x1' = x1 - Y0 R01 over rows [0, m); n1 in 1 .. 32 columns; R01 at (r0, c0) of R_k (packed np).
-void launch_tc_update(int sms, cudaStream_t s, const double* y, int64_t ldy, const double* x1, int64_t ldx,
-                      double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np, int r0,
-                      int c0, DevState* st) {
+// x1' = x1 - Y R_JK over rows [0, m); Y has k = 16 or 32 columns, n1 in 1 .. 32 columns are
+// updated; R_JK at (r0, c0) of R_k (packed np).
+void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t ldy, const double* x1,
+                      int64_t ldx, double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np,
+                      int r0, int c0, DevState* st) {
   const int64_t tiles = (m + tcs::ROWS - 1) / tcs::ROWS;
   const int grid = (int)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
-  if (n1 <= 16)
-    tc_update_kernel<16><<<grid, tcs::THREADS + 32, tcs::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, pass, rk, np,
-                                                                    r0, c0, st);
-  else
-    tc_update_kernel<32><<<grid, tcs::THREADS + 32, tcs::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, pass, rk, np,
-                                                                    r0, c0, st);
+#define SCQR3_UPD(KV, NV)                                                                                   \
+  tc_update_kernel<KV, NV><<<grid, tcs::THREADS + 32, tcs::UGeo<KV>::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, \
+                                                                             pass, rk, np, r0, c0, st)
+  if (k == 16) {
+    if (n1 <= 16) SCQR3_UPD(16, 16);
+    else SCQR3_UPD(16, 32);
+  } else {
+    if (n1 <= 16) SCQR3_UPD(32, 16);
+    else SCQR3_UPD(32, 32);
+  }
+#undef SCQR3_UPD
 }
 
 }  // namespace scqr3

@@ -201,3 +201,59 @@ def test_mixed_tc_alg2_host_and_scale():
     Qh, Rh, ih = scqr3.factor_host(Xp, precision=scqr3.PREC_MIXED_TC, algorithm=scqr3.ALG_ADAPTIVE)
     assert ih.status == 0
     assert np.array_equal(Qh.numpy(), Qa.cpu().numpy()) and np.array_equal(Rh.numpy(), Ra.cpu().numpy())
+
+
+# ------------------------------------------------------------------ blocked substitution layouts
+
+@pytest.mark.parametrize("n", [24, 40, 100, 128])
+def test_in_place_leading_dimension_and_separate_output(n):
+    """The substitution reads block 0 from the pass's input and updates and
+    solves every later 32-column block in the output: in place (Q = X) with a
+    leading dimension above n, and a separate Q with its own leading
+    dimension, give the same bits, and the columns around the view stay
+    untouched."""
+    m = 20011
+    Xh = testmat(m, n, 1e9, seed=6800 + n)
+    wide = torch.zeros((m, n + 5), dtype=torch.float64, device="cuda")
+    wide[:, 2:2 + n] = torch.from_numpy(Xh).cuda()
+    Xv = wide[:, 2:2 + n]
+    outw = torch.full((m, n + 3), 7.0, dtype=torch.float64, device="cuda")
+    Qv = outw[:, 1:1 + n]
+    Qa, Ra, ia = scqr3.factor(torch.from_numpy(Xh).cuda(), Q=Qv, precision=TC)
+    Qb, Rb, ib = scqr3.factor(Xv, Q=Xv, precision=TC)
+    torch.cuda.synchronize()
+    assert ia.status == 0 and ib.status == 0
+    assert torch.equal(Qa, Qb) and torch.equal(Ra, Rb)
+    assert torch.all(wide[:, :2] == 0) and torch.all(wide[:, 2 + n:] == 0)
+    assert torch.all(outw[:, :1] == 7.0) and torch.all(outw[:, 1 + n:] == 7.0)
+    Q, R = Qb.cpu().numpy(), Rb.cpu().numpy()
+    assert np.linalg.norm(Q.T @ Q - np.eye(n), 2) <= 1e-13
+    assert np.linalg.norm(Xh - Q @ R) / np.linalg.norm(Xh) <= 1e-13
+
+
+@pytest.mark.parametrize("n", [100, 128])
+def test_host_form_alg2_and_small_shift_wide(n):
+    """factor_host runs the last substitution in row chunks (each one the full
+    block sequence). With one chunk (m <= 262144) it makes the device call's
+    launches and is bitwise equal to it; with three, the first Gram is summed
+    per chunk, so the result differs at the rounding level amplified by kappa
+    and is held to the FP64 tolerances instead. Alg. 2 and the smaller first
+    shift go through the same blocked substitution."""
+    for m, seed in ((200000, 6900 + n), (600000, 6950 + n)):
+        Xh = testmat(m, n, 1e10, seed=seed)
+        Qd, Rd, idv = run(Xh)
+        X = torch.empty(Xh.shape, dtype=torch.float64, pin_memory=True)
+        X.copy_(torch.from_numpy(Xh))
+        Qh, Rh, ih = scqr3.factor_host(X, precision=TC)
+        Qh, Rh = Qh.numpy(), Rh.numpy()
+        assert ih.status == 0 and idv.status == 0
+        if m <= 262144:
+            assert np.array_equal(Qh, Qd) and np.array_equal(Rh, Rd)
+        else:
+            assert np.linalg.norm(Qh.T @ Qh - np.eye(n), 2) <= 1e-13
+            assert np.linalg.norm(Xh - Qh @ Rh) / np.linalg.norm(Xh) <= 1e-13
+            assert np.linalg.norm(Rh - Rd) / np.linalg.norm(Rd) <= 100 * n * 1e10 * U
+    check(testmat(60000, n, 1e5, seed=6910 + n), 1e5, algorithm=scqr3.ALG_ADAPTIVE)
+    Qs, Rs, isv = run(testmat(60000, n, 1e7, seed=6920 + n), shift_scale=500.0)
+    assert isv.status == 0
+    assert np.linalg.norm(Qs.T @ Qs - np.eye(n), 2) <= 1e-13
