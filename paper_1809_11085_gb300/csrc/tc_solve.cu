@@ -57,13 +57,20 @@ constexpr int YLD = 33;                  // row stride (doubles) of a slot's sta
 constexpr int YSLOT = ROWS * YLD * 8;    // 33 KB: the slot's Y tile, then its x tile (<= 32 columns each)
 
 // Geometry for a block of K = 16 or 32 columns (the contraction length).
+// K = 16 leaves room to prefetch each slot's next tile of Y (two buffers per
+// slot, filled by cp.async while the current tile is cut, multiplied and
+// applied).
 template <int K>
 struct UGeo {
   static constexpr uint32_t SBO = 16 * K;     // 8-row (A) or 8-column (B) group stride: K / 8 core matrices
   static constexpr int APLANE = ROWS * K * 2;  // per digit plane of a tile (8 KB for K = 32)
   static constexpr int ASLOT = 8 * APLANE;     // the slot's 8 planes
   static constexpr int BPLANE = 32 * K * 2;    // per digit plane of R_JK (32 columns)
-  static constexpr size_t SMEM = SLOTS * (size_t)ASLOT + 8 * (size_t)BPLANE + SLOTS * (size_t)YSLOT + 1024;
+  static constexpr bool PREF = K == 16;        // prefetch the next tile of Y
+  static constexpr int YPLD = K + 1;           // row stride of a prefetch buffer: conflict-free rows
+  static constexpr size_t YPRE = PREF ? SLOTS * 2 * (size_t)ROWS * YPLD * 8 : 0;
+  static constexpr size_t SMEM =
+      SLOTS * (size_t)ASLOT + 8 * (size_t)BPLANE + SLOTS * (size_t)YSLOT + YPRE + 1024;
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -263,16 +270,44 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
       }
     }
   } else {
+    constexpr bool PREF = UGeo<K>::PREF;
+    constexpr int YPLD = UGeo<K>::YPLD;
     uint8_t* arow = abuf + slot * ASLOT + (r >> 3) * SBO + (r & 7) * 16;
     const uint32_t tq = tmem + slot * TSLOT + ((uint32_t)(32 * (warp & 3)) << 16);
-    double* ys = ystage + slot * (ROWS * YLD);  // the slot's staged tile: Y0, then x1 / x1'
+    double* ys = ystage + slot * (ROWS * YLD);  // the slot's staged tile: Y (without prefetch), then x / x'
+    double* ypre = ystage + SLOTS * (ROWS * YLD) + slot * 2 * (ROWS * YPLD);  // PREF: two Y buffers
+    // PREF: copy the Y rows of the tile at row r0n into buf asynchronously
+    // (zeros past m; nothing for r0n < 0), as one cp.async group
+    auto prefetch_y = [&](int64_t r0n, double* buf) {
+      if (r0n >= 0) {
+        constexpr int IT = ROWS * K / SLOT_THREADS;
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          const int rr = (tis + SLOT_THREADS * it) / K, c = tis % K;
+          const bool ok = r0n + rr < m;
+          const double* g = ok ? y + (r0n + rr) * ldy + c : y;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
+                       :: "r"(smem_u32(buf + rr * YPLD + c)), "l"(g), "r"(ok ? 8 : 0) : "memory");
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (PREF) prefetch_y(tile_row0(slot), ypre);
     for (uint32_t j = 0;; ++j) {
       const int64_t row0 = tile_row0(2 * j + slot);
       if (slot_any(slot, row0 < 0 || err_sh)) break;
       const int rows = (int)((m - row0) < ROWS ? (m - row0) : ROWS);
-      // the tile's Y rows, coalesced (one row of K per warp or half warp),
-      // every load in flight before the first store
-      {
+      const double* yb = ys;
+      int yld = YLD;
+      if (PREF) {
+        // the next tile of this slot into the other buffer; this tile's copies done
+        prefetch_y(tile_row0(2 * (j + 1) + slot), ypre + ((j + 1) & 1) * (ROWS * YPLD));
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        yb = ypre + (j & 1) * (ROWS * YPLD);
+        yld = YPLD;
+      } else {
+        // the tile's Y rows, coalesced (one row of K per warp or half warp),
+        // every load in flight before the first store
         constexpr int IT = ROWS * K / SLOT_THREADS;
         double t[IT];
 #pragma unroll
@@ -288,7 +323,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
       unsigned long long mx = 0;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(ys[r * YLD + c]) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(yb[r * yld + c]) & 0x7FFFFFFFFFFFFFFFull;
         mx = mx > b ? mx : b;
       }
       const bool finite = (mx >> 52) != 0x7FF;
@@ -298,7 +333,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
         const int kg = (K / 16) * hf + kh;
         double v[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = ys[r * YLD + 8 * kg + q];
+        for (int q = 0; q < 8; ++q) v[q] = yb[r * yld + 8 * kg + q];
         cut8(v, E, arow + kg * LBO, APLANE);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -364,6 +399,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
       slot_sync(slot);  // the tile is out before the next one is staged
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");  // no copy into shared memory outlives the CTA
   __syncthreads();
   if (err_sh) {
     atomicCAS(&st->status, SCQR3_OK, SCQR3_E_TIMEOUT);
