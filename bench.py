@@ -42,10 +42,11 @@ FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
 PROFILED_KERNEL_SHA = "b447e14d15d0797f"
 PROFILED_BYTES_PER_ROW = 992.3
 PROFILED_SOLVE_BYTES_PER_ROW = 968.7
-PROFILED_BLOCK_BYTES_PER_ROW = 464.4  # pass_kernel<32> on the first 32-column block of a 64-column X
-# ncu DRAM bytes per row of the tensor-core kernels at 1048576 x 64 (profiles/tc_update_kernel_* and
-# profiles/tc_gram_kernel_*), valid for the sources they were taken on.
-PROFILED_TC = {"tc_solve": ("ae4873aaabbe7a3d", ("tc_common.cuh", "tc_solve.cu"), 740.4),
+PROFILED_BLOCK_BYTES_PER_ROW = 210.3  # pass_kernel<16> on the first 16-column block of a 64-column X
+# ncu DRAM bytes per row of the tensor-core kernels at 1048576 x 64 (profiles/tc_solve_kernels_* and
+# profiles/tc_gram_kernel_*; for the substitution, the mean over its two update launch shapes), valid for
+# the sources they were taken on.
+PROFILED_TC = {"tc_solve": ("27e8cfecfccc30eb", ("tc_common.cuh", "tc_solve.cu"), 478.7),
                "tc_gram": ("ba3a9f333151bc26", ("tc_common.cuh", "tc_gram.cu"), 516.4)}
 
 
@@ -98,7 +99,7 @@ def profiled_traffic(m, n, solve_only=False, tcs=False):
     if sha != PROFILED_KERNEL_SHA or n != 64:
         return None
     if tcs:
-        return PROFILED_BLOCK_BYTES_PER_ROW * m if PROFILED_BLOCK_BYTES_PER_ROW and tc_block_width(n) == 32 else None
+        return PROFILED_BLOCK_BYTES_PER_ROW * m if PROFILED_BLOCK_BYTES_PER_ROW and tc_block_width(n) == 16 else None
     return (PROFILED_SOLVE_BYTES_PER_ROW if solve_only else PROFILED_BYTES_PER_ROW) * m
 
 
