@@ -473,6 +473,16 @@ def run_gpu(args, rank, world, local_rank):
         ksteps = max(2, min(args.steps, 4))
         scqr3.factor_host(Xh, Q=Qh, R=Rh, workspace=hws, precision=prec)  # warm-up
         torch.cuda.synchronize(dev)
+        # the pinned-memory link right before the steps (host memory and the
+        # CPU-GPU link are shared with the machine's other jobs)
+        tl0 = time.perf_counter()
+        hws.Qdev.copy_(Xh, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        tl1 = time.perf_counter()
+        Qh.copy_(hws.Qdev, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        tl2 = time.perf_counter()
+        link = {"h2d_gbs": m * n * 8 / (tl1 - tl0) / 1e9, "d2h_gbs": m * n * 8 / (tl2 - tl1) / 1e9}
         f0, f1 = torch.cuda.Event(True), torch.cuda.Event(True)
         t0 = time.perf_counter()
         f0.record(stream)
@@ -491,6 +501,7 @@ def run_gpu(args, rank, world, local_rank):
         e2e = {"value": world * m / (ems * 1e-3), "unit": "rows/s", "ms_per_step": ems,
                "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": m * n * 8 + n * n * 8 + scqr3.INFO_BYTES,
                "status": hinf.status, "passes": hinf.passes, "step_ms": step_ms,
+               "median_step_ms": statistics.median(step_ms), "link": link,
                "path": "pinned host X -> scqr3_factor_host (row-chunked copies overlapped with the first "
                        "Gram and the last solve) -> pinned host Q, R, info; synchronous call per step",
                "orth": e2e_orth}

@@ -1,46 +1,49 @@
 // tc_solve.cu -- the row-wise substitution Q := X R^{-1} (Eq. backward2) for
 // n <= 128 with its off-diagonal blocks on the tensor cores.
 //
-// Blocking R in 32-column blocks R_IJ splits the substitution of each row
-// x^T = [x_0^T .. x_{nb-1}^T] into, for J = 0, 1, ..:
+// Blocking R in diagonal blocks of w = 16 or 32 columns splits the
+// substitution of each row x^T = [x_0^T .. x_{nb-1}^T] into, for J = 0, 1, ..:
 //   y_J^T = x_J^T R_JJ^{-1},   x_K^T := x_K^T - y_J^T R_JK  (K > J):
 // the same terms forward substitution over columns takes, grouped by block.
-// The triangular solves run in FP64 on the pass kernel over 32-column
-// blocks. The products y_J^T R_JK -- most of the substitution's flops, and
-// dense contractions -- run here (one 32-column block K per launch; written
-// below for the first pair, Y0 = Y_J and R01 = R_JK) on the BF16 tensor cores
-// through the exact digit split of the Gram kernel:
-//  * row i of Y0 gets the scale sigma_i = 2^E_i > max_k |y_ik| (its own 32
+// The triangular solves run in FP64 on the pass kernel. The products
+// y_J^T R_JK -- most of the substitution's flops, and dense contractions --
+// run here on the BF16 tensor cores (one launch per 32 columns to update;
+// written below as Y = Y_J with k = w columns and R01 = the updated columns
+// of R_JK) through the exact digit split of the Gram kernel:
+//  * row i of Y gets the scale sigma_i = 2^E_i > max_k |y_ik| (its own k
 //    values), column l of R01 the scale tau_l = 2^E_l > max_k |r_kl|;
 //  * both are cut into eight signed 7-bit digits (56 bits); digit products are
 //    exact in FP32, and tile e of tensor memory sums the pairs (s, t) with
-//    s + t = e over the 32 columns k: at most 8 * 32 * 127^2 < 2^24, exact;
+//    s + t = e over the k columns: at most 8 * 32 * 127^2 < 2^24, exact;
 //  * per entry the tile sums fold exactly into int64, U = sum_{e<=3} D_e
 //    2^{7(3-e)} (< 2^40.1) and T = sum_{e>=4} D_e 2^{7(7-e)} (< 2^42.3), then
 //    W = 2^21 U + floor(T / 2^7) (< 2^61.2, truncation below 2^-56 of
 //    sigma_i tau_l); sigma_i tau_l 2^-56 W is assembled as a double from the
-//    bits of W (integer operations), and x1'_il = x1_il - that, one FP64
+//    bits of W (integer operations), and x'_il = x_il - that, one FP64
 //    subtraction per entry.
-// The computed product differs from y0_i^T r_l by less than about
-// 2^-54 (sigma_i ||r_l||_1 + tau_l ||y0_i||_1), a perturbation of R01 of norm
+// The computed product differs from y_i^T r_l by less than about
+// 2^-54 (sigma_i ||r_l||_1 + tau_l ||y_i||_1), a perturbation of R01 of norm
 // O(u ||R||): the order of the row-wise backward error of FP64 substitution
 // (Eq. backward2) on which the analysis of Sec. 3 rests.
 //
 // Kernel layout: 2 slots of 256 threads (one 128-row tile each; threads r and
 // r + 128 of a slot share the tile's row r and tensor-memory lane r, each with
-// half of the row) plus a producer warp. A slot stages its tile of Y0 in
-// shared memory (coalesced loads, rows padded to 33 words), each thread cuts
-// its half row into 8 digit planes (A operand, M = 128 rows, K =
-// 32, K-major, no swizzle: core matrices of 8 rows x 16 bytes, K step 128 B,
-// 8-row step 512 B) and the slot signals the producer, which issues the 16
-// MMAs (M = 128, N = 32 (8 - s), K = 16) of the tile into the slot's 256
-// columns of tensor memory and commits them to the slot's mbarrier. Meanwhile
-// the slot stages its tile of x1; then each thread reads its row's sums back
-// (tcgen05.ld 32x32b), updates its row of x1 in shared memory, and the slot
-// writes the tile out coalesced. While one slot waits for its MMAs the other
-// cuts or applies. Every wait has an iteration
-// limit; past it the kernel records SCQR3_E_TIMEOUT, waits (bounded) for its
-// own MMAs and frees its tensor memory.
+// half of the row) plus a producer warp. A slot stages its tile of Y in shared
+// memory (coalesced loads, rows padded to an odd number of words; for k = 16
+// the next tile is prefetched by cp.async into a second buffer), each thread
+// cuts its half row into 8 digit planes (A operand, M = 128 rows, K = k,
+// K-major, no swizzle: core matrices of 8 rows x 16 bytes, K step 128 B,
+// 8-row step 16 k bytes) and the slot signals the producer. The producer
+// issues one MMA per digit s and K step, digit s of Y against the planes
+// t = 0 .. 7 - s of R01 side by side (M = 128, N = 32 (8 - s), K = 16), into
+// the slot's 256 columns of tensor memory from column 32 s, so that the pair
+// (s, t) lands in tile e = s + t, and commits them to the slot's mbarrier.
+// Meanwhile the slot stages its tile of x; then each thread reads its row's
+// sums back (tcgen05.ld 32x32b), updates its row of x in shared memory, and the
+// slot writes the tile out coalesced. While one slot waits for its MMAs the
+// other cuts or applies. Every wait has an iteration limit; past it the kernel
+// records SCQR3_E_TIMEOUT, waits (bounded) for its own MMAs and copies and
+// frees its tensor memory.
 #include "tc_common.cuh"
 
 namespace scqr3 {
@@ -177,10 +180,10 @@ __global__ void tc_split_r_kernel(const double* __restrict__ rk, int np, int n, 
   }
 }
 
-// x1' = x1 - Y0 R01 for rows [0, m): y holds Y0 (32 columns), x1 and q1 the
-// n1 <= 32 columns to update of the pass's input and output (they may be the
-// same memory); R01 is rows r0 .. r0 + 31, columns c0 .. c0 + n1 - 1 of R_k,
-// packed np x np.
+// x' = x - Y R01 for rows [0, m): y holds Y (K = 16 or 32 columns), x1 and q1
+// the n1 <= N columns to update of the pass's input and output (they may be
+// the same memory); R01 is rows r0 .. r0 + K - 1, columns c0 .. c0 + n1 - 1 of
+// R_k, packed np x np.
 template <int K, int N>
 __global__ void __launch_bounds__(tcs::THREADS + 32, 1)
 tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, int64_t ldx, double* q1, int64_t ldq,
