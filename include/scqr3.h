@@ -74,9 +74,10 @@ extern "C" {
  * through an exact fixed-point split: each column is scaled by a power of two
  * above its largest entry and cut into eight 7-bit digits, every digit
  * product is exact, sums of 256 rows are exact in the FP32 accumulator, and
- * the digit-pair sums are combined in int64. The Gram error is below about
- * m 2^-55 sigma_j sigma_k, within the norm-wise bound that the shift of
- * Eq. (finds2) covers, so results match the FP64 form to rounding. The
+ * the digit-pair sums are combined in int64. The Gram error is below
+ * m 2^-53 sigma_j sigma_k (about 4.3 m u ||q_j|| ||q_k||), within the
+ * norm-wise bound that the shift of Eq. (finds2) covers, so results match the
+ * FP64 form to rounding. The
  * substitution runs in 32-column blocks of R: the triangular diagonal blocks
  * in FP64, the products with the off-diagonal blocks (x_K -= y_J R_JK) on the
  * tensor cores by the same split. Not in the paper. n <= 128, m <= 2^31 and

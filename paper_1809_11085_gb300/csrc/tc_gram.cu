@@ -24,9 +24,13 @@
 //    does no work per row. Pairs with s + t > 7 (below 2^-56 relative) are
 //    dropped.
 //
-// The result differs from q_j^T q_k by at most about m 2^-55 sigma_j sigma_k:
-// the norm-wise bound of the Gram error that the shift of Eq. (finds2)
-// covers (gamma_m n ||Q||^2), so the factorization keeps its guarantees.
+// The result differs from q_j^T q_k by at most m 2^-53 sigma_j sigma_k (each
+// value truncated to 2^-56 of its scale, and the pairs s + t > 7 not formed,
+// below 2^-53.2 sigma_j sigma_k per row). With sigma <= 2 max |q| that is at
+// most about 4.3 m u ||q_j|| ||q_k||, so ||E|| <= 4.3 m n u ||Q||^2: a
+// norm-wise Gram error of the FP64 form's order, inside the
+// 11 (mn + n(n+1)) u ||Q||^2 shift of Eq. (finds2), so the factorization keeps
+// its guarantees.
 //
 // Blocks: the columns form operand blocks of 64. For n <= 64 one block, and
 // every CTA computes it; for 64 < n <= 128 the Gram matrix is the blocks

@@ -16,14 +16,16 @@
 //    exact in FP32, and tile e of tensor memory sums the pairs (s, t) with
 //    s + t = e over the k columns: at most 8 * 32 * 127^2 < 2^24, exact;
 //  * per entry the tile sums fold exactly into int64, U = sum_{e<=3} D_e
-//    2^{7(3-e)} (< 2^40.1) and T = sum_{e>=4} D_e 2^{7(7-e)} (< 2^42.3), then
+//    2^{7(3-e)} (< 2^40.1) and T = sum_{e>=4} D_e 2^{7(7-e)} (< 2^42.4), then
 //    W = 2^21 U + floor(T / 2^7) (< 2^61.2, truncation below 2^-56 of
 //    sigma_i tau_l); sigma_i tau_l 2^-56 W is assembled as a double from the
 //    bits of W (integer operations), and x'_il = x_il - that, one FP64
 //    subtraction per entry.
-// The computed product differs from y_i^T r_l by less than about
-// 2^-54 (sigma_i ||r_l||_1 + tau_l ||y_i||_1), a perturbation of R01 of norm
-// O(u ||R||): the order of the row-wise backward error of FP64 substitution
+// The computed product differs from y_i^T r_l by less than
+// 2^-56 (sigma_i ||r_l||_1 + tau_l ||y_i||_1) + k 2^-53 sigma_i tau_l (the
+// truncation of each value, and the digit pairs s + t > 7 not formed): at
+// most about 4 k u ||y_i|| ||r_l||, a perturbation of R01 of norm O(u ||R||),
+// the order of the row-wise backward error of FP64 substitution
 // (Eq. backward2) on which the analysis of Sec. 3 rests.
 //
 // Kernel layout: 2 slots of 256 threads (one 128-row tile each; threads r and
