@@ -553,7 +553,7 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "dtype_note": {"fp64": "FP64 throughout",
                        "tc": "FP64 Cholesky, accumulation and triangular substitution blocks; the Gram and "
-                             "(32 < n <= 64) the off-diagonal substitution block from exact digit products "
+                             "the off-diagonal substitution blocks from exact digit products "
                              "(7-bit integers in BF16, sums below 2^24 in FP32, folded in int64)",
                        "mixed": "FP32 pairs for Gram and substitution, FP64 shift/Cholesky/accumulation",
                        "mixed_tc": "FP32-pair substitution, exact tensor-core Gram"}[pname],
