@@ -709,10 +709,21 @@ def extra_legs(torch, dev, stream, args):
     ms = _time(torch, stream, lambda: scqr3.factor(X, B, Q=Q, workspace=ws, read_info=False))
     inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
     BQ = torch.matmul(B, Q.view(-1, 8, nn)).view(mm, nn)
+    orth_b = _orth(torch, Q, BQ)
+    R64 = scqr3.factor(X, B, Q=Q, workspace=ws)[1].clone()
+    # the same through the tensor-core form (Gram of Z = L^T Q and the blocked substitution)
+    mst = _time(torch, stream, lambda: scqr3.factor(X, B, Q=Q, workspace=ws, read_info=False,
+                                                    precision=scqr3.PREC_TC))
+    _, Rt, inft = scqr3.factor(X, B, Q=Q, workspace=ws, precision=scqr3.PREC_TC)
+    BQ = torch.matmul(B, Q.view(-1, 8, nn)).view(mm, nn)
     legs["oblique"] = {"workload": "FP64 sCQR3 in the B inner product, X 4194304 x 128 (kappa 1e10), "
                                    "B block diagonal 8x8 G^T G + 0.1 I",
                        "ms": round(ms, 2), "rows_per_s": mm / (ms * 1e-3), "passes": inf.passes,
-                       "status": inf.status, "orth_B": _orth(torch, Q, BQ)}
+                       "status": inf.status, "orth_B": orth_b,
+                       "tc": {"ms": round(mst, 2), "rows_per_s": mm / (mst * 1e-3), "speedup": ms / mst,
+                              "passes": inft.passes, "status": inft.status, "orth_B": _orth(torch, Q, BQ),
+                              "dR_vs_fp64": (torch.linalg.matrix_norm(Rt - R64) /
+                                             torch.linalg.matrix_norm(R64)).item()}}
     del X, B, Q, ws, BQ
     free()
 

@@ -56,7 +56,8 @@ void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t l
                       int64_t ldx, double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np,
                       int r0, int c0, DevState* st);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
-                    unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs);
+                    unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
+                    const double* lt, int64_t blk0);
 
 namespace {
 
@@ -181,7 +182,10 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
   const bool tcp = opts && (opts->precision == SCQR3_PREC_TC || opts->precision == SCQR3_PREC_MIXED_TC);
   // tensor-core Gram: n <= 128, B = I, and at most 2^31 rows (its exact int64
   // digit-sum accumulators)
-  if (tcp && (B || n > 128 || m > ((int64_t)1 << 31))) return SCQR3_E_UNSUPPORTED;
+  if (tcp && (n > 128 || m > ((int64_t)1 << 31))) return SCQR3_E_UNSUPPORTED;
+  // tensor-core forms with B: block-diagonal with blocks of 1, 2, 4 or 8 rows
+  // (they divide the kernel's 8-row units), FP64 substitution only
+  if (tcp && B && (B->bs == 0 || B->bs > 8 || opts->precision == SCQR3_PREC_MIXED_TC)) return SCQR3_E_UNSUPPORTED;
   if (opts && opts->precision == SCQR3_PREC_MIXED && B) return -5;  // mixed form: B = I only
   if (opts && opts->algorithm != 0 && opts->algorithm != SCQR3_ALG_SCQR3 &&
       opts->algorithm != SCQR3_ALG_ADAPTIVE)
@@ -305,7 +309,8 @@ int make_layout(int64_t m, int n, const scqr3_B* B, int prec, int host_chunks, L
   const int r = make_layout_one(m, n, B, prec, host_chunks, L, grid, geo);
   if (r != SCQR3_OK) return r;
   for (int p : {SCQR3_PREC_FP64, SCQR3_PREC_TC, SCQR3_PREC_MIXED_TC}) {
-    if (p == prec || (p != SCQR3_PREC_FP64 && (B || n > 128))) continue;
+    const bool tc_ok = n <= 128 && (!B || (p == SCQR3_PREC_TC && B->bs > 0 && B->bs <= 8));
+    if (p == prec || (p != SCQR3_PREC_FP64 && !tc_ok)) continue;
     Layout L2;
     int g2;
     PassGeom geo2;
@@ -485,7 +490,8 @@ int first_gram(Call& c, const double* X, int64_t ldx, int64_t r0, int64_t r1, in
   }
   if (c.tc) {
     const int g = tc_grid(Pc.m, c.P.np, sm_count());
-    launch_tc_gram(g, sm_count(), c.s, src, ldx, Pc, -1, c.colmax, part, c.L.part_stride, c.st, 0);
+    launch_tc_gram(g, sm_count(), c.s, src, ldx, Pc, -1, c.colmax, part, c.L.part_stride, c.st, 0, c.lt,
+                   c.lt ? r0 / c.P.bs : 0);
     return g;
   }
   if (c.csr) {  // the whole matrix only: rows reach across any split
@@ -598,7 +604,7 @@ void after_pass(Call& c, int k, const double* Q, int64_t ldq) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     // the mixed form keeps float pairs between passes
     launch_tc_gram(c.L.tc_grid, sm_count(), c.s, Q, ldq, c.P, k, c.colmax, c.partials, c.L.part_stride, c.st,
-                   c.mixed ? 1 : 0);
+                   c.mixed ? 1 : 0, c.lt, 0);
   } else if (c.csr) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     launch_csr_gram(c.P.np, c.L.csr_grid, c.s, Q, ldq, c.P, k, c.B, c.partials, c.L.part_stride, c.st);

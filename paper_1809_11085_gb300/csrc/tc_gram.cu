@@ -188,13 +188,86 @@ colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int
   }
 }
 
+namespace tc {
+// z = L_b^T x for the 8 consecutive rows x of one column (BS-row blocks b, b + 1, ..),
+// as the oblique Gram's Z = L^T Q of Alg. 4. Only the first nvalid rows exist;
+// m is a multiple of BS, so a block lies wholly among them or wholly past them
+// (past rows are zero, and their blocks are not read).
+template <int BS>
+__device__ __forceinline__ void apply_lt8(double (&x)[8], const double* __restrict__ lt, int64_t b, int nvalid) {
+  constexpr int BSP = BS * (BS + 1) / 2;
+#pragma unroll
+  for (int o = 0; o < 8; o += BS) {
+    if (o >= nvalid) break;
+    const double* L = lt + (b + o / BS) * BSP;
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+      double z = 0.0;
+#pragma unroll
+      for (int l = i; l < BS; ++l) z = fma(__ldg(L + pk_idx(BS, i, l)), x[o + l], z);
+      x[o + i] = z;
+    }
+  }
+}
+}  // namespace tc
+
+// Oblique column scales: colmax[j] = max_i |z_ij| over Z = L^T Q (Alg. 4) as
+// the bit pattern of a double, with z formed exactly as the Gram kernel forms
+// it (tc::apply_lt8 on the same 8-row units), so the scales bound the values
+// the kernel cuts. Thread units are (8-row group, column), consecutive columns
+// in consecutive threads.
+__global__ void __launch_bounds__(256)
+colmax_obl_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int pass,
+                  unsigned long long* __restrict__ colmax, const DevState* __restrict__ st,
+                  const double* __restrict__ lt, int bs, int64_t blk0) {
+  if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
+  __shared__ unsigned long long red[256];
+  const int tid = threadIdx.x;
+  const int nc = n > 64 ? 128 : 64, gs = 256 / nc;  // column slots, 8-row groups per block pass
+  const int j = tid % nc, g0 = tid / nc;
+  unsigned long long mx = 0;
+  if (j < n) {
+    for (int64_t g = blockIdx.x * (int64_t)gs + g0; g * 8 < m; g += (int64_t)gridDim.x * gs) {
+      double x[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[r] = g * 8 + r < m ? src[(g * 8 + r) * lds + j] : 0.0;
+      const int64_t b = blk0 + (g * 8) / bs;
+      const int nv = m - g * 8 < 8 ? (int)(m - g * 8) : 8;
+      switch (bs) {
+        case 1: tc::apply_lt8<1>(x, lt, b, nv); break;
+        case 2: tc::apply_lt8<2>(x, lt, b, nv); break;
+        case 4: tc::apply_lt8<4>(x, lt, b, nv); break;
+        default: tc::apply_lt8<8>(x, lt, b, nv); break;
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(x[r]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = mx > v ? mx : v;
+      }
+    }
+  }
+  red[tid] = mx;
+  __syncthreads();
+  if (tid < nc && j < n) {
+    unsigned long long b = red[tid];
+    for (int q = 1; q < gs; ++q) b = b > red[tid + nc * q] ? b : red[tid + nc * q];
+    atomicMax(&colmax[j], b);
+  }
+}
+
 // KC = 64: n <= 64, every CTA computes the one block. KC = 32: 64 < n <= 128;
 // CTAs [0, gd) compute block (0,0), [gd, 2 gd) block (1,1), the rest (0,1).
-template <int KC>
+// OBL: the Gram matrix Z^T Z of Z = L^T Q for an oblique B given by the
+// packed L_j^T (lt; row 0 of src is in block blk0; B's blocks of bs = 1, 2, 4
+// or 8 rows divide the 8-row units), with the column scales of Z from
+// colmax_obl_kernel; the CTAs of the diagonal blocks also return ||Q||_F^2 of
+// their rows and columns in the slot's last entry, for the oblique shift of
+// Eq. (finds2B).
+template <int KC, bool OBL>
 __global__ void __launch_bounds__(tc::THREADS + 32, 1)
 tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
                const unsigned long long* __restrict__ colmax, double* __restrict__ partials, int part_stride,
-               DevState* __restrict__ st, int bulk, int pairs, int gd) {
+               DevState* __restrict__ st, int bulk, int pairs, int gd, const double* __restrict__ lt, int64_t blk0) {
   using namespace tc;
   using GK = ChunkGeo<KC>;
   constexpr int CHUNKS = GK::CHUNKS;
@@ -297,6 +370,7 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   const int jr = row & 63;
   const bool upper = row < 64;
   const bool rb_skip = !offd && (qd & 1) == 1 && h == 0;
+  double f2 = 0.0;  // OBL: ||Q||_F^2 of this thread's entries (diagonal-block CTAs)
   // exact digit-sum accumulators of this thread's 32 entries: U (d = 0..3)
   // and T (d = 4..7)
   long long U[CW], T[CW];
@@ -369,19 +443,50 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
         const int E = Esh[col];
         unsigned long long F[8];
         uint32_t sp[4] = {0u, 0u, 0u, 0u};  // sign bits of rows 2p (bit 15) and 2p + 1 (bit 31)
+        if constexpr (!OBL) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int i = ig * 8 + r;
-          double x = 0.0;
-          if (col < n && i < rows) x = bulk ? xs[i * n + col] : src[(row0 + i) * lds + col];
-          uint32_t sgn;
-          if (pairs) {
-            F[r] = tc::fixed56_pair((unsigned long long)__double_as_longlong(x), E, &sgn);
-          } else {
-            F[r] = tc::fixed56(x, E);
-            sgn = (uint32_t)((unsigned long long)__double_as_longlong(x) >> 32) & 0x80000000u;
+          for (int r = 0; r < 8; ++r) {
+            const int i = ig * 8 + r;
+            double x = 0.0;
+            if (col < n && i < rows) x = bulk ? xs[i * n + col] : src[(row0 + i) * lds + col];
+            uint32_t sgn;
+            if (pairs) {
+              F[r] = tc::fixed56_pair((unsigned long long)__double_as_longlong(x), E, &sgn);
+            } else {
+              F[r] = tc::fixed56(x, E);
+              sgn = (uint32_t)((unsigned long long)__double_as_longlong(x) >> 32) & 0x80000000u;
+            }
+            sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
           }
-          sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
+        } else {
+          double xv[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int i = ig * 8 + r;
+            xv[r] = 0.0;
+            if (col < n && i < rows) xv[r] = bulk ? xs[i * n + col] : src[(row0 + i) * lds + col];
+          }
+          if (!offd) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) f2 = fma(xv[r], xv[r], f2);
+          }
+          // m is a multiple of bs: the unit's blocks lie wholly before or past the end
+          if (ig * 8 < rows) {
+            const int64_t b = blk0 + (row0 + ig * 8) / P.bs;
+            const int nv = rows - ig * 8 < 8 ? rows - ig * 8 : 8;
+            switch (P.bs) {
+              case 1: tc::apply_lt8<1>(xv, lt, b, nv); break;
+              case 2: tc::apply_lt8<2>(xv, lt, b, nv); break;
+              case 4: tc::apply_lt8<4>(xv, lt, b, nv); break;
+              default: tc::apply_lt8<8>(xv, lt, b, nv); break;
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            F[r] = tc::fixed56(xv[r], E);
+            const uint32_t sgn = (uint32_t)((unsigned long long)__double_as_longlong(xv[r]) >> 32) & 0x80000000u;
+            sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
+          }
         }
         uint8_t* dst = sb + (j >> 6) * GK::BREG + ((j & 63) >> 3) * GK::SBO + ig * LBO + (j & 7) * 16;
         tc::store_plane<KC, 0>(dst, F, sp);
@@ -466,7 +571,19 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
       if (c >= r && !((r >> 6) == cj && (c >> 6) == ck)) part[pk_idx(NPK, r, c)] = 0.0;
     }
   }
-  if (tid == 0) part[pk_size(NPK)] = 0.0;
+  if constexpr (OBL) {
+    __shared__ double f2w[THREADS / 32 + 1];
+    for (int o = 16; o > 0; o >>= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+    if (lane == 0) f2w[warp] = f2;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < THREADS / 32; ++w) t += f2w[w];
+      part[pk_size(NPK)] = t;
+    }
+  } else {
+    if (tid == 0) part[pk_size(NPK)] = 0.0;
+  }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
@@ -475,9 +592,15 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
 // ---- host side ----------------------------------------------------------------------------
 
 cudaError_t tc_setup() {
-  cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_gram_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_gram_kernel<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_gram_kernel<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_gram_kernel<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+  return e;
 }
 
 int tc_groups(int64_t m) { return (int)((m + tc::GROUP - 1) / tc::GROUP); }
@@ -491,22 +614,37 @@ int tc_grid(int64_t m, int np, int sms) {
   return (int)(t < sms ? t : sms);
 }
 
-// Column scales then the tensor-core Gram of rows [0, P.m) of src into `grid` slots.
+// Column scales then the tensor-core Gram of rows [0, P.m) of src into `grid`
+// slots; for an oblique B (P.bs > 0) of Z = L^T Q, with lt the packed L_j^T and
+// row 0 of src in block blk0.
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
-                    unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs) {
+                    unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
+                    const double* lt, int64_t blk0) {
   // the slots hold the packed np x np layout; np = 128 needs a CTA per block
   if ((P.np != 64 && P.np != 128) || part_stride != pk_size(P.np) + 1 || (P.np == 128 && grid < 3)) return;
   cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * tc::NPMAX, s);
   const int rs = P.n > 64 ? 2 : 4;
   const int64_t want = (P.m + rs - 1) / rs;
   const int cg = (int)(want < (int64_t)sms * 8 ? (want < 1 ? 1 : want) : (int64_t)sms * 8);
-  colmax_kernel<<<cg, 256, 0, s>>>(src, lds, P.m, P.n, pass, colmax, st, pairs);
+  if (P.bs > 0) {
+    const int gs = P.n > 64 ? 2 : 4;
+    const int64_t wg = (P.m / 8 + 1 + gs - 1) / gs;
+    const int og = (int)(wg < (int64_t)sms * 8 ? (wg < 1 ? 1 : wg) : (int64_t)sms * 8);
+    colmax_obl_kernel<<<og, 256, 0, s>>>(src, lds, P.m, P.n, pass, colmax, st, lt, P.bs, blk0);
+  } else {
+    colmax_kernel<<<cg, 256, 0, s>>>(src, lds, P.m, P.n, pass, colmax, st, pairs);
+  }
   // bulk copies need contiguous rows, 16-byte aligned, and chunk sizes that are
   // multiples of 16 bytes (m n even)
   const int bulk = (lds == P.n && ((uintptr_t)src & 15) == 0 && ((P.m * P.n) & 1) == 0) ? 1 : 0;
+  const bool obl = P.bs > 0;
   if (P.np == 64) {
-    tc_gram_kernel<64><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials, part_stride,
-                                                                st, bulk, pairs, grid);
+    if (obl)
+      tc_gram_kernel<64, true><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials,
+                                                                        part_stride, st, bulk, pairs, grid, lt, blk0);
+    else
+      tc_gram_kernel<64, false><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials,
+                                                                         part_stride, st, bulk, pairs, grid, lt, blk0);
     return;
   }
   // np = 128: gd CTAs for each diagonal block, the rest (which also cut twice
@@ -514,8 +652,12 @@ void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_
   const int g = tc_groups(P.m);
   int gd = grid >= 3 * g ? g : (3 * grid) / 10;
   if (gd < 1) gd = 1;
-  tc_gram_kernel<32><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials, part_stride, st,
-                                                              bulk, pairs, gd);
+  if (obl)
+    tc_gram_kernel<32, true><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials,
+                                                                      part_stride, st, bulk, pairs, gd, lt, blk0);
+  else
+    tc_gram_kernel<32, false><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials,
+                                                                       part_stride, st, bulk, pairs, gd, lt, blk0);
 }
 
 }  // namespace scqr3

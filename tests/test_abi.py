@@ -80,9 +80,16 @@ def test_argument_errors_are_reported_on_the_host(lib):
             scqr3.E_UNSUPPORTED
         assert lib.scqr3_workspace_bytes(2 ** 31 + 1, 8, None, ctypes.byref(o), ctypes.byref(out)) == \
             scqr3.E_UNSUPPORTED
-        b = scqr3._B(8, ctypes.c_void_p(8), 0.0)
+        b = scqr3._B(16, ctypes.c_void_p(8), 0.0)  # blocks of 16 rows: FP64 only
         assert lib.scqr3_workspace_bytes(800, 16, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out)) == \
             scqr3.E_UNSUPPORTED
+        b = scqr3._B(0, None, 0.0, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), 3000)  # CSR
+        assert lib.scqr3_workspace_bytes(1000, 16, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out)) == \
+            scqr3.E_UNSUPPORTED
+    b = scqr3._B(8, ctypes.c_void_p(8), 0.0)  # the mixed substitution takes no B
+    o = scqr3._Opts(0, scqr3.PREC_MIXED_TC, 0.0)
+    assert lib.scqr3_workspace_bytes(800, 16, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out)) == \
+        scqr3.E_UNSUPPORTED
     # null pointers in scqr3_factor are rejected before any CUDA call
     assert lib.scqr3_factor(None, 10, 2, 2, None, None, 2, None, None, None, 0, None, None,
                             None) == -1

@@ -257,3 +257,71 @@ def test_host_form_alg2_and_small_shift_wide(n):
     Qs, Rs, isv = run(testmat(60000, n, 1e7, seed=6920 + n), shift_scale=500.0)
     assert isv.status == 0
     assert np.linalg.norm(Qs.T @ Qs - np.eye(n), 2) <= 1e-13
+
+
+# ------------------------------------------------------------------ oblique inner product (block-diagonal B)
+
+def orth_b(Q, Bblk):
+    n, bs = Q.shape[1], Bblk.shape[1]
+    BQ = np.einsum("kij,kjn->kin", Bblk, Q.reshape(-1, bs, n)).reshape(Q.shape)
+    return np.linalg.norm(Q.T @ BQ - np.eye(n), 2)
+
+
+@pytest.mark.parametrize("n,bs,kappa,m", [(16, 8, 1e8, 24000), (40, 4, 1e10, 24004), (64, 8, 1e10, 24000),
+                                          (100, 2, 1e6, 24002), (128, 8, 1e10, 24000), (33, 1, 1e4, 24001)])
+def test_oblique_against_oracle(n, bs, kappa, m):
+    """The Gram matrix of Z = L^T Q on the tensor cores (L_j^T applied to each
+    8-row unit before the digit cut, the column scales from the same Z), with
+    ||Q||_F^2 from the diagonal-block CTAs for the oblique shift, and the
+    blocked substitution: B-orthogonality, residual and R against the oracle at
+    the FP64 tolerances. m not a multiple of 8 leaves a last unit with fewer
+    rows than 8 (whole blocks of bs rows)."""
+    from paper_1809_11085_gb300.testmat import block_diag_spd
+
+    Xh = testmat(m, n, kappa, seed=7000 + n + bs)
+    Bh = block_diag_spd(m, bs, seed=7100 + n + bs)
+    Q, R, info = scqr3.factor(torch.from_numpy(Xh).cuda(), torch.from_numpy(Bh).cuda(), precision=TC)
+    torch.cuda.synchronize()
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    Qo, Ro, st, tr = oracle.scqr3(Xh, Bblk=Bh)
+    assert st == 0 and info.status == 0, info
+    assert info.passes == tr["passes"]
+    assert orth_b(Q, Bh) <= 1e-13
+    assert np.linalg.norm(Xh - Q @ R) / np.linalg.norm(Xh) <= 1e-13
+    dR = np.linalg.norm(R - Ro) / np.linalg.norm(Ro)
+    assert dR <= (1e-12 if kappa <= 1e8 else 100 * n * kappa * U), dR
+
+
+def test_oblique_matches_fp64_form_and_host_and_rejections():
+    """At kappa 1e8 the pass decisions are clear and the tensor-core form
+    takes the FP64 form's passes; at kappa 1e10 (with kappa(B) ~ 1e3) the
+    plain Cholesky of the second pass sits at the margin (kappa(Q_1)^2 u near
+    1), where either form may add the breakdown rule's shifted pass, so only
+    the results are compared there."""
+    from paper_1809_11085_gb300.testmat import block_diag_spd
+
+    m, n = 400000, 64
+    Bb = torch.from_numpy(block_diag_spd(m, 8, seed=7201)).cuda()
+    Bh = Bb.cpu().numpy()
+    for kappa, seed in ((1e8, 7200), (1e10, 7202)):
+        Xh = testmat(m, n, kappa, seed=seed)
+        X = torch.from_numpy(Xh).cuda()
+        Qt, Rt, it = scqr3.factor(X, Bb, precision=TC)
+        Qd, Rd, idv = scqr3.factor(X, Bb)
+        torch.cuda.synchronize()
+        assert it.status == 0 and idv.status == 0
+        if kappa <= 1e8:
+            assert it.passes == idv.passes
+            assert (torch.linalg.matrix_norm(Rt - Rd) / torch.linalg.matrix_norm(Rd)).item() < 1e-12
+        assert orth_b(Qt.cpu().numpy(), Bh) <= 1e-13
+        assert (torch.linalg.matrix_norm(X - Qt @ Rt) / torch.linalg.matrix_norm(X)).item() <= 1e-13
+    Xp = torch.empty(Xh.shape, dtype=torch.float64, pin_memory=True)
+    Xp.copy_(torch.from_numpy(Xh))
+    Qh, Rh, ih = scqr3.factor_host(Xp, Bb, precision=TC)
+    assert ih.status == 0
+    assert orth_b(Qh.numpy(), Bh) <= 1e-13
+    # blocks of 16 rows and a CSR B stay on FP64; the mixed substitution takes no B
+    with pytest.raises(scqr3.ScqrError):
+        scqr3.factor(X[:64000], torch.from_numpy(block_diag_spd(64000, 16, seed=1)).cuda(), precision=TC)
+    with pytest.raises(scqr3.ScqrError):
+        scqr3.factor(X[:64000], Bb[:8000], precision=scqr3.PREC_MIXED_TC)
