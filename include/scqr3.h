@@ -80,8 +80,10 @@ extern "C" {
  * FP64 form to rounding. The
  * substitution runs in 32-column blocks of R: the triangular diagonal blocks
  * in FP64, the products with the off-diagonal blocks (x_K -= y_J R_JK) on the
- * tensor cores by the same split. Not in the paper. n <= 128, m <= 2^31 and
- * B = NULL (else SCQR3_E_UNSUPPORTED). */
+ * tensor cores by the same split. Not in the paper. n <= 128, m <= 2^31, and
+ * B either NULL or block-diagonal with blocks of 1, 2, 4 or 8 rows (the Gram
+ * matrix of Z = L^T Q, L_j^T applied to each 8-row unit before the split;
+ * else SCQR3_E_UNSUPPORTED). */
 #define SCQR3_PREC_TC 2
 /* The mixed form's substitution (FP32 pairs) with the Gram matrices of
  * SCQR3_PREC_TC, read directly from the float-pair iterates. n <= 128,
