@@ -46,7 +46,7 @@ PROFILED_BLOCK_BYTES_PER_ROW = 210.3  # pass_kernel<16> on the first 16-column b
 # ncu DRAM bytes per row of the tensor-core kernels at 1048576 x 64 (profiles/tc_solve_kernels_* and
 # profiles/tc_gram_kernel_*; for the substitution, the mean over its two update launch shapes), valid for
 # the sources they were taken on.
-PROFILED_TC = {"tc_solve": ("65ab6d794a4f3532", ("tc_common.cuh", "tc_solve.cu"), 478.7),
+PROFILED_TC = {"tc_solve": ("25eb56420f284aac", ("tc_common.cuh", "tc_solve.cu"), 478.7),
                "tc_gram": ("36e48f579de11899", ("tc_common.cuh", "tc_gram.cu"), 516.4)}
 
 

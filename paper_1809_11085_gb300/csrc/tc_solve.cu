@@ -97,7 +97,7 @@ __device__ __forceinline__ uint64_t desc(uint32_t addr) {
          ((uint64_t)1 << 46);
 }
 
-// The 16 MMAs of a tile: digit s of Y0 (A) against the planes t = 0 .. 7 - s
+// The MMAs of a tile (16 for K = 32, 8 for K = 16): digit s of Y (A) against the planes t = 0 .. 7 - s
 // of R01 side by side (B, N = 32 (8 - s): the planes are contiguous, 32
 // columns each), accumulating at tensor-memory column 32 s, so that the pair
 // (s, t) lands in tile e = s + t; K step kk. Descriptor offsets stay inside
@@ -344,8 +344,8 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[slot])) : "memory");
-      slot_sync(slot);  // Y0 read by every thread of the slot
-      // the tile's x1 rows while the tensor core works
+      slot_sync(slot);  // Y read by every thread of the slot
+      // the tile's rows of x while the tensor core works
       {
         constexpr int IT = ROWS * N / SLOT_THREADS;
         double t[IT];
@@ -359,7 +359,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
         for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) / N) * YLD + c] = t[it];
       }
       const bool ok = tc::wait_parity(smem_u32(&mdone[slot]), j & 1);
-      if (slot_any(slot, !ok)) {  // also: the x1 tile is complete
+      if (slot_any(slot, !ok)) {  // also: the tile of x is complete
         err_sh = 1;
         break;
       }
