@@ -182,7 +182,9 @@ def _b_struct(B, normb):
 
 PREC_FP64 = 0
 PREC_MIXED = 1
-PREC_TC = 2  # FP64 substitution, Gram matrices on the BF16 tensor cores (exact digit split)
+PREC_TC = 2  # FP64-accurate: the Gram matrices and the substitution's off-diagonal blocks on the
+             # BF16 tensor cores (exact digit split), FP64 diagonal blocks; n <= 128, B = I or
+             # block-diagonal with blocks of 1, 2, 4 or 8 rows
 PREC_MIXED_TC = 3  # the mixed form's substitution with the tensor-core Gram matrices
 ALG_ADAPTIVE = 2  # Alg. 2: shift only on breakdown, stop on the orthogonality test
 ALG_SCQR3 = 3     # Alg. 3: shifted pass, then CholeskyQR2
