@@ -241,7 +241,9 @@ int scqr3_factor_host(const double *X, int64_t m, int n, int64_t ldx,
  * capture); then scqr3_factor_batched any number of times -- it only queues
  * memsets and kernels on `stream`, so it can be captured in a CUDA graph and
  * replayed; finally scqr3_batch_plan_destroy. The workspace and all item
- * buffers must stay valid and unmoved while the plan is used. */
+ * buffers must stay valid and unmoved while the plan is used. opts: FP64
+ * precision only; max_passes, shift_scale, algorithm and tol apply to every
+ * matrix as in scqr3_factor (Alg. 2's default tol from each matrix's m, n). */
 typedef struct {
   const double *X;    /* device, m x n row-major, ldx >= n                  */
   double *Q;          /* device, m x n, ldq >= n (may equal X, ldq == ldx)   */

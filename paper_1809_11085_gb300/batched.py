@@ -59,7 +59,8 @@ class BatchedQR:
     """
 
     def __init__(self, Xs, *, tune=None, max_passes: int = 0, keep_rpass: bool = False,
-                 in_place: bool = False, graph: bool = False):
+                 in_place: bool = False, graph: bool = False, shift_scale: float = 0.0,
+                 algorithm: int = 3, tol: float = 0.0):
         import torch
 
         self.Xs = list(Xs)
@@ -82,7 +83,7 @@ class BatchedQR:
                              self.Qs[i].stride(0))
         self.tune = tune or tuning()
         t = _Tuning(self.tune["ctas_per_sm"], (ctypes.c_int * 4)(*self.tune["tile_panels"]))
-        opts = scqr3._Opts(int(max_passes), 0, 0.0)
+        opts = scqr3._Opts(int(max_passes), 0, 0.0, float(shift_scale), int(algorithm), float(tol))
         L = _bind()
         plan = ctypes.c_void_p()
         nbytes = ctypes.c_size_t(0)

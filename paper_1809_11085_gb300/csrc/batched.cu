@@ -154,6 +154,8 @@ using namespace scqr3;
 struct scqr3_batch_plan {
   int count = 0;
   int max_passes = 6;
+  scqr3_opts opts{};      // shift_scale, algorithm and tol apply to every matrix
+  bool has_opts = false;
   int grid = 0;
   int ntiles = 0;
   int np_max = 16;
@@ -182,6 +184,8 @@ extern "C" int scqr3_batch_plan_create(const scqr3_batch_item* items, int count,
   if (opts && opts->max_passes != 0 && (opts->max_passes < 3 || opts->max_passes > SCQR3_MAX_PASSES))
     return -3;
   if (opts && opts->precision != SCQR3_PREC_FP64) return -3;
+  if (opts && opts->algorithm != 0 && opts->algorithm != SCQR3_ALG_SCQR3 && opts->algorithm != SCQR3_ALG_ADAPTIVE)
+    return -3;
   if (!out || !workspace_bytes) return -5;
   for (int i = 0; i < count; ++i) {
     const scqr3_batch_item& a = items[i];
@@ -201,6 +205,10 @@ extern "C" int scqr3_batch_plan_create(const scqr3_batch_item* items, int count,
   if (!p) return SCQR3_E_CUDA;
   p->count = count;
   p->max_passes = (opts && opts->max_passes) ? opts->max_passes : 6;
+  if (opts) {
+    p->opts = *opts;
+    p->has_opts = true;
+  }
   p->src.assign(items, items + count);
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -293,7 +301,7 @@ extern "C" int scqr3_batch_plan_upload(scqr3_batch_plan* p, void* workspace, siz
     b.P.bs = 0;
     b.P.norm_x2 = 0.0;
     b.P.normb_in = 0.0;
-    set_options(&b.P, nullptr);
+    set_options(&b.P, p->has_opts ? &p->opts : nullptr);  // per matrix: Alg. 2's tol depends on m, n
     b.ldx = a.ldx;
     b.ldq = a.ldq;
     b.tile_lo = b.tile_hi = -1;

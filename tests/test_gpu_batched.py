@@ -168,3 +168,31 @@ def test_differentiable_batch_against_central_differences():
             fd = (loss([x + h * d for x, d in zip(Xs, D)]) - loss([x - h * d for x, d in zip(Xs, D)])).item() / (2 * h)
             an = sum((g * d).sum().item() for g, d in zip(grads, D))
             assert abs(fd - an) <= tol * max(1.0, abs(an)), (t, fd, an, tol)
+
+
+def test_batch_options_alg2_and_small_shift():
+    """shift_scale, algorithm and tol reach every matrix of a batch (Alg. 2's
+    default tolerance from each matrix's own m, n): the pass counts of the
+    single calls with the same options, and their results to rounding. The
+    condition numbers keep Alg. 2's stopping test away from its margin: one
+    plain pass leaves ||Q^T Q - I|| ~ kappa^2 u, at least 16 times the
+    tolerance 6 (mn + n(n+1)) u here, so CholeskyQR2 (two passes) stops it."""
+    shapes = [(3000, 16, 1e4), (5000, 32, 1e5), (9000, 64, 1e4), (4000, 100, 1e5), (7000, 128, 1e4)]
+    mats = [testmat(m, n, k, seed=5900 + i) for i, (m, n, k) in enumerate(shapes)]
+    for opts in ({"algorithm": scqr3.ALG_ADAPTIVE}, {"shift_scale": 500.0}):
+        Xs = [torch.from_numpy(x).cuda() for x in mats]
+        b = batched.BatchedQR(Xs, **opts)
+        b.run()
+        torch.cuda.synchronize()
+        for i, (xh, inf, Q, R) in enumerate(zip(mats, b.infos(), b.Qs, b.Rs)):
+            Qs, Rs, isg = scqr3.factor(torch.from_numpy(xh).cuda(), **opts)
+            torch.cuda.synchronize()
+            assert inf.status == 0 and isg.status == 0, (i, inf, isg)
+            assert inf.passes == isg.passes, (opts, i, inf.passes, isg.passes)
+            if "algorithm" in opts:
+                assert inf.passes == 2
+            Rg, Rsn = R.cpu().numpy(), Rs.cpu().numpy()
+            assert np.linalg.norm(Rg - Rsn) / np.linalg.norm(Rsn) <= 1e-12
+            m, n = xh.shape
+            tol = 6 * (m * n + n * (n + 1)) * U if "algorithm" in opts else 1e-13
+            assert orth2(Q.cpu().numpy()) <= tol
