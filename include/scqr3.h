@@ -307,8 +307,11 @@ int scqr3_backward(const double *Q, int64_t m, int n, int64_t ldq,
  * counterpart; this is a deployment convenience.
  *
  * Scratch comes from a fixed array of SCQR3_NOALLOC_SCRATCH_BYTES inside the
- * library, reserved on each device where this entry point is first used and
- * held until the process exits. Problems whose scqr3_workspace_bytes()
+ * library. A device reserves it when the library's module holding it is
+ * loaded there, and holds it until the process exits: on the first call of
+ * this entry point on that device under lazy module loading (CUDA's default),
+ * or when the context is created under CUDA_MODULE_LOADING=EAGER (then every
+ * process using the library reserves it). Problems whose scqr3_workspace_bytes()
  * exceeds it (the scratch grows with n and with the number of CTAs, which
  * is capped by the SM count) are rejected with SCQR3_E_SCRATCH_LIMIT, so
  * scqr3_workspace_bytes() tells in advance whether a problem fits. The first call
@@ -316,7 +319,8 @@ int scqr3_backward(const double *Q, int64_t m, int n, int64_t ldq,
  * capture. All calls share the array, so calls whose GPU work overlaps (other
  * streams or host threads) race; serialize them. The call allocates nothing
  * (no cudaMalloc/cudaFree, no allocating library routine). X, Q, R, info:
- * as for scqr3_factor. */
+ * as for scqr3_factor. A negative argument code -k names argument k of THIS
+ * prototype (X 1, m 2, n 3, ldx 4, Q 5, ldq 6, R 7, info 8). */
 #define SCQR3_NOALLOC_SCRATCH_BYTES (16u << 20)
 int scqr3_factor_noalloc(const double *X, int64_t m, int n, int64_t ldx,
                          double *Q, int64_t ldq, double *R, scqr3_info *info,

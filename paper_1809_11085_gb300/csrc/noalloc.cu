@@ -10,15 +10,18 @@
 // allocator of its own. For them this entry point runs the same kernels with
 // the scratch placed in a fixed array that this library owns.
 //
-// The array lives in this translation unit only, so it is reserved on a
-// device when this file's module is first used there and held until the
-// process exits; processes that never call scqr3_factor_noalloc do not load
-// it. Its device address is looked up once per device (with that device
-// current) on the first call there; make that first call before any stream
-// capture. All calls share the one array: the pass state is cleared at the
-// start of every call and every other scratch entry is written before it is
-// read, but two calls whose work overlaps on the GPU (different streams,
-// different host threads) race on the array.
+// The array lives in this translation unit, so a device reserves it when this
+// module is loaded there and holds it until the process exits. Under lazy
+// module loading (CUDA's default) that happens on the first use of the module
+// on that device; under eager loading (CUDA_MODULE_LOADING=EAGER) it happens
+// when the context is created, so every process that loads the library then
+// reserves the array on each device it uses. Its device address is looked up
+// once per device (with that device current) on the first call there; make
+// that first call before any stream capture. All calls share the one array:
+// the pass state is cleared at the start of every call and every other
+// scratch entry is written before it is read, but two calls whose work
+// overlaps on the GPU (different streams, different host threads) race on the
+// array.
 #include <mutex>
 
 #include "scqr3_internal.cuh"
@@ -48,15 +51,34 @@ int scratch_address(void** out) {
 
 }  // namespace
 
+// scqr3_factor numbers its arguments by its own prototype; this entry point
+// reports them by the positions in its prototype instead (X 1, m 2, n 3,
+// ldx 4, Q 5, ldq 6, R 7, info 8).
+static int own_arg_code(int r) {
+  switch (r) {
+    case -6: return -5;   // Q
+    case -7: return -6;   // ldq
+    case -8: return -7;   // R
+    case -13: return -8;  // info
+    default: return r;    // X, m, n, ldx keep their positions; other codes are not argument codes
+  }
+}
+
 extern "C" int scqr3_factor_noalloc(const double* X, int64_t m, int n, int64_t ldx, double* Q,
                                     int64_t ldq, double* R, scqr3_info* info, void* stream) {
+  if (!X) return -1;
+  if (ldx < n) return -4;
+  if (!Q) return -5;
+  if (ldq < n) return -6;
+  if (!R) return -7;
+  if (!info) return -8;
   size_t need = 0;
   const int r = scqr3_workspace_bytes(m, n, nullptr, nullptr, &need);
-  if (r != SCQR3_OK) return r;
+  if (r != SCQR3_OK) return own_arg_code(r);
   if (need > kScratchBytes) return SCQR3_E_SCRATCH_LIMIT;
   void* ws = nullptr;
   const int a = scratch_address(&ws);
   if (a != SCQR3_OK) return a;
-  return scqr3_factor(X, m, n, ldx, nullptr, Q, ldq, R, nullptr, ws, kScratchBytes, nullptr, info,
-                      stream);
+  return own_arg_code(scqr3_factor(X, m, n, ldx, nullptr, Q, ldq, R, nullptr, ws, kScratchBytes, nullptr,
+                                   info, stream));
 }

@@ -12,7 +12,7 @@ import os
 from dataclasses import dataclass, field
 
 MAX_PASSES = 8
-MAX_N = 128
+MAX_N = 256  # largest n (FP64, B = I); the other forms take n <= 128
 
 OK = 0
 E_NONFINITE = -100
