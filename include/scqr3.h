@@ -361,6 +361,32 @@ int scqr3_timing_begin(int capacity);
  * number of launches recorded (which may exceed capacity). */
 int scqr3_timing_end(scqr3_launch_time *out, int capacity, int *count);
 
+/* ---------------------------------------------------------------------------
+ * Test and tuning hooks (process-wide; not part of the method, and not needed
+ * for normal use). They affect calls queued after they are set.
+ *   SCQR3_DEBUG_WAIT_NS      value: the time limit, in nanoseconds, of the
+ *                            waits by which the warps of a tensor-core kernel
+ *                            hand work to each other (default 2 s; value < 0
+ *                            restores it). A wait that runs out records
+ *                            SCQR3_E_TIMEOUT in scqr3_info; the kernel then
+ *                            waits, always with the default limit, for its own
+ *                            tensor-core operations and copies before it frees
+ *                            its tensor memory, so a short limit is safe. Tests
+ *                            set 0 to drive that path.
+ *   SCQR3_DEBUG_WAIT_SCOPE   value: which kernels the limit above applies to
+ *                            (bit 0: the tensor-core Gram kernel, bit 1: the
+ *                            tensor-core substitution kernels; default 3);
+ *                            the others keep the default limit.
+ *   SCQR3_DEBUG_FUSED_SOLVE  value 1 (default): SCQR3_PREC_TC with
+ *                            16 < n <= 64 runs each pass's substitution in one
+ *                            sweep; 0: in the separate diagonal-block and
+ *                            update launches (for comparison).
+ * Returns SCQR3_OK, -1 for an unknown key, -2 for an invalid value. */
+#define SCQR3_DEBUG_WAIT_NS 1
+#define SCQR3_DEBUG_FUSED_SOLVE 2
+#define SCQR3_DEBUG_WAIT_SCOPE 3
+int scqr3_debug_set(int key, long long value);
+
 #ifdef __cplusplus
 }
 #endif

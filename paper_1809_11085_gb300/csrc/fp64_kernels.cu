@@ -56,6 +56,12 @@ chol_kernel(Params P, int pass, const double* __restrict__ gram, double* __restr
   chol_body<NP>(P, pass, gram, rstack, racc, Rout, Rpass, st, info, sm, sm + pk_size(NP));
 }
 
+// A failure recorded in the device state by a kernel that runs after the last
+// Cholesky (a tensor-core wait that ran out) reaches the call's record.
+__global__ void status_kernel(const DevState* __restrict__ st, scqr3_info* __restrict__ info) {
+  if (threadIdx.x == 0 && st->status != SCQR3_OK && info->status == SCQR3_OK) info->status = st->status;
+}
+
 // -------------------------------------------------------------------------------------------
 // B_j = L_j L_j^T for every diagonal block; stores L_j^T packed (upper, row-
 // major) and the max over j of ||B_j||_F (for ||B||_2 in Eq. finds2B).
@@ -165,6 +171,8 @@ void launch_chol(int np, cudaStream_t s, const Params& P, int pass, const double
     default: break;
   }
 }
+
+void launch_status(cudaStream_t s, const DevState* st, scqr3_info* info) { status_kernel<<<1, 32, 0, s>>>(st, info); }
 
 void launch_bfactor(cudaStream_t s, int bs, const double* B, int64_t nblk, double* lt, DevState* st,
                     int sms) {

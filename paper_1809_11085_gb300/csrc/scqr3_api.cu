@@ -8,6 +8,7 @@
 // capturable in a CUDA graph and free of host round trips.
 #include <cstdint>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "scqr3_internal.cuh"
@@ -54,10 +55,15 @@ void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int w, i
                        double* rdiag);
 void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t ldy, const double* x1,
                       int64_t ldx, double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np,
-                      int r0, int c0, DevState* st);
+                      int r0, int c0, DevState* st, long long wait_ns);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
-                    const double* lt, int64_t blk0);
+                    const double* lt, int64_t blk0, int scan);
+cudaError_t tc_fused_setup();
+bool tc_fused_supported(int n);
+void launch_tc_fused(int sms, cudaStream_t s, const double* X, int64_t ldx, double* Q, int64_t ldq, const Params& P,
+                     int pass, const double* rk, unsigned long long* colmax, DevState* st);
+void launch_status(cudaStream_t s, const DevState* st, scqr3_info* info);
 
 namespace {
 
@@ -122,6 +128,8 @@ cudaError_t device_geo(int np, int* grid_max, PassGeom* geo) {
     e = tc_setup();
     if (e != cudaSuccess) return e;
     e = tc_solve_setup();
+    if (e != cudaSuccess) return e;
+    e = tc_fused_setup();
     if (e != cudaSuccess) return e;
     for (int k = 0; k < 4; ++k)
       if (d.csr_ctas_per_sm[k] < 1) return cudaErrorInvalidConfiguration;
@@ -354,7 +362,18 @@ bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
 
 }  // namespace
 
+// Test and tuning hooks (scqr3_debug_set): the hand-off wait limit of the
+// tensor-core kernels, and whether the tensor-core substitution runs fused.
+constexpr long long kDefaultWaitNs = 2000000000ll;
+std::atomic<long long> g_wait_ns{kDefaultWaitNs};
+std::atomic<int> g_wait_scope{3};  // bit 0: the Gram kernel, bit 1: the substitution kernels
+std::atomic<int> g_fused_solve{1};
+
 void set_options(Params* P, const scqr3_opts* opts) {
+  const long long w = g_wait_ns.load();
+  const int scope = g_wait_scope.load();
+  P->wait_ns = (scope & 2) ? w : kDefaultWaitNs;
+  P->wait_ns_gram = (scope & 1) ? w : kDefaultWaitNs;
   const double u = 1.1102230246251565e-16;
   P->shift_scale = (opts && opts->shift_scale > 0.0) ? opts->shift_scale : 0.0;
   P->algorithm = (opts && opts->algorithm == SCQR3_ALG_ADAPTIVE) ? 2 : 3;
@@ -408,6 +427,7 @@ struct Call {
   int grid = 0;  // pass kernel CTAs (FP64 or mixed)
   PassGeom geo;
   bool mixed = false, csr = false, tc = false;
+  bool fused = false;  // tensor-core substitution in one sweep (tc_fused.cu)
   const scqr3_B* B = nullptr;
   cudaStream_t s = nullptr;
   DevState* st = nullptr;
@@ -461,6 +481,7 @@ int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void*
   P.tc = c->tc ? 1 : 0;
   P.solve_only = (c->csr || c->tc) ? 1 : 0;
   set_options(&P, opts);
+  c->fused = c->tc && !c->mixed && g_fused_solve.load() != 0 && tc_fused_supported(n);
 
   if (cudaMemsetAsync(c->st, 0, sizeof(DevState), s) != cudaSuccess) return SCQR3_E_CUDA;
   if (cudaMemsetAsync(info, 0, sizeof(scqr3_info), s) != cudaSuccess) return SCQR3_E_CUDA;
@@ -491,7 +512,7 @@ int first_gram(Call& c, const double* X, int64_t ldx, int64_t r0, int64_t r1, in
   if (c.tc) {
     const int g = tc_grid(Pc.m, c.P.np, sm_count());
     launch_tc_gram(g, sm_count(), c.s, src, ldx, Pc, -1, c.colmax, part, c.L.part_stride, c.st, 0, c.lt,
-                   c.lt ? r0 / c.P.bs : 0);
+                   c.lt ? r0 / c.P.bs : 0, 1);
     return g;
   }
   if (c.csr) {  // the whole matrix only: rows reach across any split
@@ -539,8 +560,22 @@ int tc_block_width(int n) { return n <= 64 ? 16 : 32; }
 // Y_J R_JK for the later columns, 32 at a time (tensor cores, exact digit
 // split). Block 0 reads the pass's input; every later block is updated and
 // solved in place in the output.
+// The fused substitution (tc_fused.cu: one sweep, column maxima of the result
+// for the next Gram matrix) serves the FP64-accurate tensor-core form for
+// 16 < n <= 64.
+bool use_fused(const Call& c) { return c.fused; }
+
 void tc_solve_rows(Call& c, int k, const double* rk, const double* src, int64_t lds, double* dst, int64_t ldd,
                    const Params& Pc) {
+  if (use_fused(c)) {
+    // B = I: the column maxima go to the next Gram matrix (the oblique one
+    // scans Z = L^T Q itself)
+    unsigned long long* cm = c.lt ? nullptr : c.colmax;
+    if (cm) cudaMemsetAsync(cm, 0, sizeof(unsigned long long) * 128, c.s);
+    tick(c.s, SCQR3_KERNEL_PASS, k);
+    launch_tc_fused(sm_count(), c.s, src, lds, dst, ldd, Pc, k, rk, cm, c.st);
+    return;
+  }
   const int n = Pc.n, w = tc_block_width(n), nb = (n + w - 1) / w;
   tick(c.s, SCQR3_KERNEL_TCUPDATE, k);
   launch_tc_split_r(c.s, rk, c.P.np, n, w, k, c.st, c.tcr);
@@ -561,7 +596,7 @@ void tc_solve_rows(Call& c, int k, const double* rk, const double* src, int64_t 
       const double* x1 = J == 0 ? src + c0 : dst + c0;
       const int64_t ldx1 = J == 0 ? lds : ldd;
       launch_tc_update(sm_count(), c.s, w, dst + w * J, ldd, x1, ldx1, dst + c0, ldd, Pc.m, n1, k, rk, c.P.np,
-                       w * J, c0, c.st);
+                       w * J, c0, c.st, c.P.wait_ns);
     }
   }
 }
@@ -604,7 +639,7 @@ void after_pass(Call& c, int k, const double* Q, int64_t ldq) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     // the mixed form keeps float pairs between passes
     launch_tc_gram(c.L.tc_grid, sm_count(), c.s, Q, ldq, c.P, k, c.colmax, c.partials, c.L.part_stride, c.st,
-                   c.mixed ? 1 : 0, c.lt, 0);
+                   c.mixed ? 1 : 0, c.lt, 0, (use_fused(c) && !c.lt) ? 0 : 1);
   } else if (c.csr) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     launch_csr_gram(c.P.np, c.L.csr_grid, c.s, Q, ldq, c.P, k, c.B, c.partials, c.L.part_stride, c.st);
@@ -659,6 +694,8 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
     tick(c.s, SCQR3_KERNEL_FINISH, -1);
     launch_df_finish(sm_count() * 4, c.s, Q, ldq, m, n, c.P.max_passes, c.st);
   }
+  // a tensor-core kernel after the last Cholesky may have recorded a failure
+  if (c.tc) launch_status(c.s, c.st, c.info);
   tick(c.s, -1, -1);
   if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
   return SCQR3_OK;
@@ -791,6 +828,7 @@ extern "C" int scqr3_factor_host(const double* X, int64_t m, int n, int64_t ldx,
                           cudaMemcpyDeviceToHost, h->copy) != cudaSuccess)
       return SCQR3_E_CUDA;
   }
+  if (c.tc) launch_status(s, c.st, c.info);
   tick(s, -1, -1);
   if (cudaMemcpyAsync(R, c.R, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return SCQR3_E_CUDA;
@@ -800,6 +838,24 @@ extern "C" int scqr3_factor_host(const double* X, int64_t m, int n, int64_t ldx,
   if (cudaStreamSynchronize(h->copy) != cudaSuccess) return SCQR3_E_CUDA;
   if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
   return SCQR3_OK;
+}
+
+extern "C" int scqr3_debug_set(int key, long long value) {
+  switch (key) {
+    case SCQR3_DEBUG_WAIT_NS:
+      g_wait_ns.store(value < 0 ? kDefaultWaitNs : value);
+      return SCQR3_OK;
+    case SCQR3_DEBUG_WAIT_SCOPE:
+      if (value < 0 || value > 3) return -2;
+      g_wait_scope.store((int)value);
+      return SCQR3_OK;
+    case SCQR3_DEBUG_FUSED_SOLVE:
+      if (value != 0 && value != 1) return -2;
+      g_fused_solve.store((int)value);
+      return SCQR3_OK;
+    default:
+      return -1;
+  }
 }
 
 extern "C" int scqr3_timing_begin(int capacity) {

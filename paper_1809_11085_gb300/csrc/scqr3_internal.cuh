@@ -44,6 +44,8 @@ struct Params {
   int csr;             // 1: B in CSR form (csr_gram_kernel forms Q^T B Q)
   int tc;              // 1: Gram matrices on the tensor cores (tc_gram_kernel)
   int solve_only;      // 1: the pass kernel only solves; a separate kernel forms the Gram
+  long long wait_ns;       // limit (ns) of the hand-off waits in the tensor-core substitution kernels
+  long long wait_ns_gram;  // ... and in the tensor-core Gram kernel
 };
 
 // The factorization uses an oblique inner product (block-diagonal or CSR B).

@@ -10,7 +10,12 @@ namespace scqr3 {
 
 namespace tc {
 
-constexpr long long WAIT_LIMIT = 1ll << 26;  // iterations of a bounded mbarrier wait
+// Waits on mbarriers are bounded in time (%globaltimer, nanoseconds). A
+// hand-off wait (one warp waiting for another's work) uses the call's limit,
+// Params::wait_ns (default kWaitNs; a test can shorten it to force the
+// timeout path); a drain wait before tensor memory is freed always uses
+// kWaitNs, so that no MMA or copy of the CTA is still in flight then.
+constexpr long long kWaitNs = 2000000000ll;  // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -19,15 +24,29 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
                :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 
-// Bounded wait for the completion of the phase with parity `parity`.
-__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
-    uint32_t done;
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the completion of the phase with parity `parity`, for at most
+// limit_ns nanoseconds; false if it did not complete in time. The first test
+// never blocks, so a limit of zero returns at once unless the phase is
+// already complete.
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity, long long limit_ns) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  if (done) return true;
+  if (limit_ns <= 0) return false;
+  const unsigned long long t0 = globaltimer();
+  for (;;) {
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                  : "=r"(done) : "r"(bar), "r"(parity) : "memory");
     if (done) return true;
+    if ((long long)(globaltimer() - t0) > limit_ns) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&v)[16]) {
@@ -45,6 +64,11 @@ __device__ __forceinline__ unsigned long long fixed56(double x, int E) {
   if (ex) mant |= 1ull << 52; else ex = 1;
   const int sh = ex - 1019 - E;  // F = mant * 2^sh
   return sh >= 0 ? (sh <= 3 ? (mant << sh) : (1ull << 56) - 1) : (sh > -64 ? (mant >> -sh) : 0ull);
+}
+
+__device__ __forceinline__ void ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(taddr) : "memory");
 }
 
 __device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&v)[8]) {

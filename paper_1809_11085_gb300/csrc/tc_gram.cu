@@ -399,9 +399,9 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
       for (uint32_t k = 0; row0_of(k) >= 0; ++k) {
         const int stg = k & 1;
         const uint32_t q = k % CHUNKS, gi = k / CHUNKS;
-        bool okw = wait_parity(smem_u32(&pfull[stg]), (k >> 1) & 1);  // planes written, staging consumed
+        bool okw = wait_parity(smem_u32(&pfull[stg]), (k >> 1) & 1, P.wait_ns_gram);  // planes written, staging consumed
         if (okw && bulk) stage_in(k + 2);
-        if (okw && q == 0 && gi > 0) okw = wait_parity(smem_u32(&tfree), (gi - 1) & 1);  // tiles read back
+        if (okw && q == 0 && gi > 0) okw = wait_parity(smem_u32(&tfree), (gi - 1) & 1, P.wait_ns_gram);  // tiles read back
         if (!okw || err_sh) {
           err_sh = 1;
           break;
@@ -429,8 +429,8 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
       if (row0 < 0 || err_sh) break;
       const int rows = (int)((m - row0) < KC ? (m - row0) : KC);
       const int stg = chunk & 1;
-      bool w = chunk < 2 || wait_parity(smem_u32(&bar[stg]), ((chunk - 2) >> 1) & 1);  // planes free
-      if (w && bulk) w = wait_parity(smem_u32(&full[stg]), (chunk >> 1) & 1);            // rows staged
+      bool w = chunk < 2 || wait_parity(smem_u32(&bar[stg]), ((chunk - 2) >> 1) & 1, P.wait_ns_gram);  // planes free
+      if (w && bulk) w = wait_parity(smem_u32(&full[stg]), (chunk >> 1) & 1, P.wait_ns_gram);            // rows staged
       if (!w) {
         err_sh = 1;
         break;
@@ -502,7 +502,7 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[stg])) : "memory");
       if (!group_end(chunk)) continue;
       // end of a group: all its MMAs (the last commit covers every earlier one)
-      if (!wait_parity(smem_u32(&bar[stg]), (chunk >> 1) & 1)) {
+      if (!wait_parity(smem_u32(&bar[stg]), (chunk >> 1) & 1, P.wait_ns_gram)) {
         err_sh = 1;
         break;
       }
@@ -540,8 +540,8 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
     atomicCAS(&st->status, SCQR3_OK, SCQR3_E_TIMEOUT);
     // let the MMAs and copies already issued finish (bounded) before the memory goes away
     if (producer && lane == 0) {
-      if (committed > 0) wait_parity(smem_u32(&bar[(committed - 1) & 1]), ((committed - 1) >> 1) & 1);
-      for (uint32_t k = committed; k < issued; ++k) wait_parity(smem_u32(&full[k & 1]), (k >> 1) & 1);
+      if (committed > 0) wait_parity(smem_u32(&bar[(committed - 1) & 1]), ((committed - 1) >> 1) & 1, kWaitNs);
+      for (uint32_t k = committed; k < issued; ++k) wait_parity(smem_u32(&full[k & 1]), (k >> 1) & 1, kWaitNs);
     }
   }
 
@@ -617,16 +617,19 @@ int tc_grid(int64_t m, int np, int sms) {
 // Column scales then the tensor-core Gram of rows [0, P.m) of src into `grid`
 // slots; for an oblique B (P.bs > 0) of Z = L^T Q, with lt the packed L_j^T and
 // row 0 of src in block blk0.
+// scan = 0: colmax already holds the column maxima of src (the fused
+// substitution that wrote it emitted them), so the scan is skipped.
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
-                    const double* lt, int64_t blk0) {
+                    const double* lt, int64_t blk0, int scan) {
   // the slots hold the packed np x np layout; np = 128 needs a CTA per block
   if ((P.np != 64 && P.np != 128) || part_stride != pk_size(P.np) + 1 || (P.np == 128 && grid < 3)) return;
-  cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * tc::NPMAX, s);
+  if (scan) cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * tc::NPMAX, s);
   const int rs = P.n > 64 ? 2 : 4;
   const int64_t want = (P.m + rs - 1) / rs;
   const int cg = (int)(want < (int64_t)sms * 8 ? (want < 1 ? 1 : want) : (int64_t)sms * 8);
-  if (P.bs > 0) {
+  if (!scan) {
+  } else if (P.bs > 0) {
     const int gs = P.n > 64 ? 2 : 4;
     const int64_t wg = (P.m / 8 + 1 + gs - 1) / gs;
     const int og = (int)(wg < (int64_t)sms * 8 ? (wg < 1 ? 1 : wg) : (int64_t)sms * 8);

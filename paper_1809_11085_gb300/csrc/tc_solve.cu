@@ -190,7 +190,7 @@ template <int K, int N>
 __global__ void __launch_bounds__(tcs::THREADS + 32, 1)
 tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, int64_t ldx, double* q1, int64_t ldq,
                  int64_t m, int n1, int pass, const double* __restrict__ rk, int np, int r0, int c0,
-                 DevState* __restrict__ st) {
+                 DevState* __restrict__ st, long long wait_ns) {
   using namespace tcs;
   using tc::smem_u32;
   constexpr uint32_t SBO = UGeo<K>::SBO;
@@ -263,7 +263,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
     if (lane == 0) {
       for (uint32_t k = 0; tile_row0(k) >= 0; ++k) {
         const int g = k & 1;
-        if (!tc::wait_parity(smem_u32(&pfull[g]), (k >> 1) & 1) || err_sh) {
+        if (!tc::wait_parity(smem_u32(&pfull[g]), (k >> 1) & 1, wait_ns) || err_sh) {
           err_sh = 1;
           break;
         }
@@ -358,7 +358,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
 #pragma unroll
         for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) / N) * YLD + c] = t[it];
       }
-      const bool ok = tc::wait_parity(smem_u32(&mdone[slot]), j & 1);
+      const bool ok = tc::wait_parity(smem_u32(&mdone[slot]), j & 1, wait_ns);
       if (slot_any(slot, !ok)) {  // also: the tile of x is complete
         err_sh = 1;
         break;
@@ -411,7 +411,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
     // let the MMAs already issued finish (bounded) before the memory goes away
     if (producer && lane == 0 && committed > 0) {
       const uint32_t k = committed - 1;
-      tc::wait_parity(smem_u32(&mdone[k & 1]), (k >> 1) & 1);
+      tc::wait_parity(smem_u32(&mdone[k & 1]), (k >> 1) & 1, tc::kWaitNs);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -446,12 +446,12 @@ void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int w, i
 // updated; R_JK at (r0, c0) of R_k (packed np).
 void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t ldy, const double* x1,
                       int64_t ldx, double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np,
-                      int r0, int c0, DevState* st) {
+                      int r0, int c0, DevState* st, long long wait_ns) {
   const int64_t tiles = (m + tcs::ROWS - 1) / tcs::ROWS;
   const int grid = (int)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
 #define SCQR3_UPD(KV, NV)                                                                                   \
   tc_update_kernel<KV, NV><<<grid, tcs::THREADS + 32, tcs::UGeo<KV>::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, \
-                                                                             pass, rk, np, r0, c0, st)
+                                                                             pass, rk, np, r0, c0, st, wait_ns)
   if (k == 16) {
     if (n1 <= 16) SCQR3_UPD(16, 16);
     else SCQR3_UPD(16, 32);

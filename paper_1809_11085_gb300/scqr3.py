@@ -146,12 +146,26 @@ def lib():
         L.scqr3_backward_workspace_bytes.restype = i32
         L.scqr3_backward.argtypes = [p, i64, i32, i64, p, i32, p, i64, p, p, i64, p, sz, p]
         L.scqr3_backward.restype = i32
+        L.scqr3_debug_set.argtypes = [i32, ctypes.c_longlong]
+        L.scqr3_debug_set.restype = i32
         L.scqr3_timing_begin.argtypes = [i32]
         L.scqr3_timing_begin.restype = i32
         L.scqr3_timing_end.argtypes = [ctypes.POINTER(_LaunchTime), i32, ctypes.POINTER(i32)]
         L.scqr3_timing_end.restype = i32
         _lib = L
     return _lib
+
+
+DEBUG_WAIT_NS = 1       # hand-off wait limit (ns) of the tensor-core kernels; < 0: default
+DEBUG_FUSED_SOLVE = 2   # 1: one-sweep tensor-core substitution (16 < n <= 64); 0: separate launches
+DEBUG_WAIT_SCOPE = 3    # kernels the wait limit applies to: bit 0 the Gram, bit 1 the substitution
+
+
+def debug_set(key: int, value: int) -> None:
+    """scqr3_debug_set: process-wide test and tuning hooks (see include/scqr3.h)."""
+    r = lib().scqr3_debug_set(int(key), int(value))
+    if r != OK:
+        raise ScqrError(r, "scqr3_debug_set")
 
 
 def _check_mat(t, name):
