@@ -371,8 +371,9 @@ int scqr3_timing_end(scqr3_launch_time *out, int capacity, int *count);
  *                            SCQR3_E_TIMEOUT in scqr3_info; the kernel then
  *                            waits, always with the default limit, for its own
  *                            tensor-core operations and copies before it frees
- *                            its tensor memory, so a short limit is safe. Tests
- *                            set 0 to drive that path.
+ *                            its tensor memory, so a short limit is safe. A
+ *                            limit of 0 gives up at the first such wait; tests
+ *                            set it to drive that path.
  *   SCQR3_DEBUG_WAIT_SCOPE   value: which kernels the limit above applies to
  *                            (bit 0: the tensor-core Gram kernel, bit 1: the
  *                            tensor-core substitution kernels; default 3);
@@ -381,10 +382,14 @@ int scqr3_timing_end(scqr3_launch_time *out, int capacity, int *count);
  *                            16 < n <= 64 runs each pass's substitution in one
  *                            sweep; 0: in the separate diagonal-block and
  *                            update launches (for comparison).
+ *   SCQR3_DEBUG_FUSED_STAGGER_NS  value: the start offset, in nanoseconds,
+ *                            between consecutive row slots of a CTA of the
+ *                            one-sweep substitution (0 .. 1e6; default 6000).
  * Returns SCQR3_OK, -1 for an unknown key, -2 for an invalid value. */
 #define SCQR3_DEBUG_WAIT_NS 1
 #define SCQR3_DEBUG_FUSED_SOLVE 2
 #define SCQR3_DEBUG_WAIT_SCOPE 3
+#define SCQR3_DEBUG_FUSED_STAGGER_NS 4
 int scqr3_debug_set(int key, long long value);
 
 #ifdef __cplusplus

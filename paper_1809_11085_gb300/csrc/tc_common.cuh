@@ -31,15 +31,14 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 
 // Wait for the completion of the phase with parity `parity`, for at most
-// limit_ns nanoseconds; false if it did not complete in time. The first test
-// never blocks, so a limit of zero returns at once unless the phase is
-// already complete.
+// limit_ns nanoseconds; false if it did not complete in time. A limit of zero
+// gives up at once (the test hook that drives the timeout path).
 __device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity, long long limit_ns) {
+  if (limit_ns <= 0) return false;
   uint32_t done;
   asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                : "=r"(done) : "r"(bar), "r"(parity) : "memory");
   if (done) return true;
-  if (limit_ns <= 0) return false;
   const unsigned long long t0 = globaltimer();
   for (;;) {
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"

@@ -48,45 +48,44 @@ namespace scqr3 {
 
 namespace tcf {
 
-constexpr int ROWS = 128;                 // rows per tile = tensor-memory lanes
-constexpr int SLOTS = 2;                  // tiles in flight per CTA
-constexpr int THREADS = ROWS * SLOTS;     // one thread per row of each slot's tile
-constexpr uint32_t LBO = 128;             // K-direction core-matrix stride
-constexpr uint32_t TSLOT = 256;           // tensor-memory columns per slot
-constexpr int SBUF = 65536;               // per slot: a staged tile of 128 x 64 doubles, or 8 digit planes (K <= 32)
-constexpr int BOX = ROWS * 128;           // one 16-column box of a staged tile (16 KB)
+constexpr int ROWS = 128;              // rows per tile = tensor-memory lanes
+constexpr int SLOTS = 3;               // tiles in flight per CTA, 128 threads each
+constexpr int THREADS = ROWS * SLOTS;
+constexpr uint32_t LBO = 128;          // K-direction core-matrix stride
+constexpr uint32_t TSLOT = 128;        // tensor-memory columns per slot: 8 tiles x 16 columns
 
-// Off-diagonal updates x[C0, C0 + N) -= y[K0, K0 + K) R[K0.., C0..]: their B
-// planes at byte BOFF of the B area and column exponents at EOFF.
+// Off-diagonal products x[C0, C0 + 16) -= y[K0, K0 + K) R[K0.., C0..]: B planes
+// at byte BOFF of the B area (8 planes of K x 16 BF16 digits), column
+// exponents at EOFF.
 struct Upd {
-  int k0, K, c0, N, boff, eoff;
+  int k0, K, c0, boff, eoff;
 };
+// NP = 64: U0 = y_0 R_01; U1a, U1b = [y_0 y_1] R_{01,2}, R_{01,3}; U2 = y_2 R_23.
+// NP = 32: U0 only.
 template <int NP> struct Plan;
 template <> struct Plan<32> {
-  static constexpr int NU = 1;
-  static constexpr Upd u[1] = {{0, 16, 16, 16, 0, 0}};
-  static constexpr int BBYTES = 4096, NEB = 16;
+  static constexpr int NU = 1, BBYTES = 4096, NEB = 16;
 };
 template <> struct Plan<64> {
-  static constexpr int NU = 3;
-  static constexpr Upd u[3] = {{0, 16, 16, 16, 0, 0}, {0, 32, 32, 32, 4096, 16}, {32, 16, 48, 16, 20480, 48}};
-  static constexpr int BBYTES = 24576, NEB = 64;
+  static constexpr int NU = 4, BBYTES = 24576, NEB = 64;
 };
+template <int NP, int UI>
+__host__ __device__ constexpr Upd plan() {
+  return UI == 0 ? Upd{0, 16, 16, 0, 0}
+       : UI == 1 ? Upd{0, 32, 32, 4096, 16}
+       : UI == 2 ? Upd{0, 32, 48, 12288, 32}
+                 : Upd{32, 16, 48, 20480, 48};
+}
 
 template <int NP> struct FGeo {
-  static constexpr int NB = NP / 16;  // diagonal blocks
+  static constexpr int NB = NP / 16;                               // diagonal blocks
+  static constexpr int SBUF = NP == 64 ? 65536 : 32768;            // A planes of one update (K <= NP / 2)
   static constexpr size_t OFF_B = (size_t)SLOTS * SBUF;
-  static constexpr size_t OFF_R = OFF_B + Plan<NP>::BBYTES;       // dense 16 x 16 diagonal blocks of R_k
+  static constexpr size_t OFF_R = OFF_B + Plan<NP>::BBYTES;        // dense 16 x 16 diagonal blocks of R_k
   static constexpr size_t OFF_RINV = OFF_R + (size_t)NB * 256 * 8;  // 1 / r_jj
   static constexpr size_t SMEM = OFF_RINV + (size_t)NP * 8 + 1024;  // + alignment slack
-  static_assert(SMEM <= 227 * 1024, "shared memory");
+  static_assert(SMEM + 512 <= 227 * 1024, "shared memory");
 };
-
-// byte offset of (row r, column c) in a staged tile: column box c / 16 (128
-// bytes of each row), its 16-byte units XOR-swizzled by r % 8
-__device__ __forceinline__ uint32_t stage_off(int r, int c) {
-  return (uint32_t)((c >> 4) * BOX + r * 128 + ((((c >> 1) & 7) ^ (r & 7)) << 4) + ((c & 1) << 3));
-}
 
 template <int K>
 __device__ __forceinline__ uint64_t desc(uint32_t addr) {
@@ -94,24 +93,25 @@ __device__ __forceinline__ uint64_t desc(uint32_t addr) {
          ((uint64_t)1 << 46);
 }
 
-// The MMAs of one update: digit s of Y (A: plane s at s * 256 K bytes) against
-// the B planes t = 0 .. 7 - s side by side, N_u (8 - s) columns from tensor
-// column N_u s; K step kk (two core matrices, 256 bytes, per K = 16).
-template <int K, int N, int S, int KK>
+// The MMAs of one product: digit s of Y (A: plane s at s * 256 K bytes)
+// against the B planes t = 0 .. 7 - s side by side, 16 (8 - s) columns from
+// tensor column 16 s, so that the pair (s, t) lands in tile e = s + t; K step
+// kk (two core matrices, 256 bytes, per K = 16).
+template <int K, int S, int KK>
 __device__ __forceinline__ void issue(uint64_t adesc, uint64_t bdesc, uint32_t tmem, uint32_t idesc0) {
-  constexpr uint32_t NS = N * (8 - S);
+  constexpr uint32_t NS = 16 * (8 - S);
   constexpr uint64_t aoff = ((uint32_t)S * (ROWS * K * 2) + KK * 2 * LBO) >> 4;
   constexpr uint64_t boff = (KK * 2 * LBO) >> 4;
-  tc::mma(tmem + N * S, adesc + aoff, bdesc + boff, idesc0 | ((NS >> 3) << 17), (S > 0 || KK > 0) ? 1u : 0u);
+  tc::mma(tmem + 16 * S, adesc + aoff, bdesc + boff, idesc0 | ((NS >> 3) << 17), (S > 0 || KK > 0) ? 1u : 0u);
   if constexpr (KK + 1 < K / 16) {
-    issue<K, N, S, KK + 1>(adesc, bdesc, tmem, idesc0);
+    issue<K, S, KK + 1>(adesc, bdesc, tmem, idesc0);
   } else if constexpr (S < 7) {
-    issue<K, N, S + 1, 0>(adesc, bdesc, tmem, idesc0);
+    issue<K, S + 1, 0>(adesc, bdesc, tmem, idesc0);
   }
 }
 
-// Barrier among the 128 threads of a slot (ids 1, 2); the second form returns
-// whether any of them passed a non-zero `pred` (slot-uniform decisions).
+// Barrier among the 128 threads of a slot (ids 1..SLOTS); the second form
+// returns whether any of them passed a non-zero `pred` (slot-uniform decisions).
 __device__ __forceinline__ void slot_sync(int slot) {
   asm volatile("bar.sync %0, %1;" :: "r"(1 + slot), "r"(ROWS) : "memory");
 }
@@ -124,7 +124,7 @@ __device__ __forceinline__ int slot_any(int slot, int pred) {
 
 // Eight consecutive values as 8 digit planes of one core-matrix row each
 // (16 bytes: 8 BF16 digits), at dst + s * plane; |x| < 2^E.
-__device__ __forceinline__ void cut8(const double (&x)[8], int E, uint8_t* dst, uint32_t plane) {
+__device__ __forceinline__ void cut8(const double* x, int E, uint8_t* dst, uint32_t plane) {
   unsigned long long F[8];
   uint32_t sp[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
@@ -133,23 +133,18 @@ __device__ __forceinline__ void cut8(const double (&x)[8], int E, uint8_t* dst, 
     const uint32_t sgn = (uint32_t)((unsigned long long)__double_as_longlong(x[r]) >> 32) & 0x80000000u;
     sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
   }
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    uint4 w;
-    switch (s) {  // digit_pair takes the digit as a template argument
-#define SCQR3_CUTS(S)                                 \
-  case S:                                             \
-    w.x = tc::digit_pair<S>(F[0], F[1], sp[0]);       \
-    w.y = tc::digit_pair<S>(F[2], F[3], sp[1]);       \
-    w.z = tc::digit_pair<S>(F[4], F[5], sp[2]);       \
-    w.w = tc::digit_pair<S>(F[6], F[7], sp[3]);       \
-    break;
-      SCQR3_CUTS(0) SCQR3_CUTS(1) SCQR3_CUTS(2) SCQR3_CUTS(3) SCQR3_CUTS(4) SCQR3_CUTS(5) SCQR3_CUTS(6)
-      SCQR3_CUTS(7)
-#undef SCQR3_CUTS
-    }
-    *(uint4*)(dst + s * plane) = w;
+#define SCQR3_CUTS(S)                               \
+  {                                                 \
+    uint4 w;                                        \
+    w.x = tc::digit_pair<S>(F[0], F[1], sp[0]);     \
+    w.y = tc::digit_pair<S>(F[2], F[3], sp[1]);     \
+    w.z = tc::digit_pair<S>(F[4], F[5], sp[2]);     \
+    w.w = tc::digit_pair<S>(F[6], F[7], sp[3]);     \
+    *(uint4*)(dst + (S) * plane) = w;               \
   }
+  SCQR3_CUTS(0) SCQR3_CUTS(1) SCQR3_CUTS(2) SCQR3_CUTS(3) SCQR3_CUTS(4) SCQR3_CUTS(5) SCQR3_CUTS(6)
+  SCQR3_CUTS(7)
+#undef SCQR3_CUTS
 }
 
 // W 2^e2 as a double from the bits of W (integer operations only): W's
@@ -172,95 +167,32 @@ __device__ __forceinline__ int scale_exp(unsigned long long mx) {
   return (ex ? ex : 1) - 1023 + 1;
 }
 
-// The row of a thread lives in a register array x[NP]; the code that works on
-// it is written once and reached with a runtime block index. These switches
-// move 8, 16 or 4 values between x and small arrays with compile-time indices
-// in every case, so x stays in registers while the tile's code stays small
-// (a fully unrolled tile does not fit the instruction cache).
-#define SCQR3_CASES8(M) M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7)
-#define SCQR3_CASES16(M) SCQR3_CASES8(M) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15)
-template <int NP>
-__device__ __forceinline__ void get8(const double (&x)[NP], int g, double (&v)[8]) {
-  switch (g) {
-#define SCQR3_G8(I)                                           \
-  case I:                                                     \
-    if constexpr (8 * I < NP) {                               \
-      _Pragma("unroll") for (int q = 0; q < 8; ++q) v[q] = x[8 * I + q]; \
-    }                                                         \
-    break;
-    SCQR3_CASES8(SCQR3_G8)
-#undef SCQR3_G8
-    default: break;
-  }
-}
-template <int NP>
-__device__ __forceinline__ void get16(const double (&x)[NP], int J, double (&t)[16]) {
-  switch (J) {
-#define SCQR3_G16(I)                                            \
-  case I:                                                       \
-    if constexpr (16 * I < NP) {                                \
-      _Pragma("unroll") for (int q = 0; q < 16; ++q) t[q] = x[16 * I + q]; \
-    }                                                           \
-    break;
-    SCQR3_G16(0) SCQR3_G16(1) SCQR3_G16(2) SCQR3_G16(3)
-#undef SCQR3_G16
-    default: break;
-  }
-}
-template <int NP>
-__device__ __forceinline__ void put16(double (&x)[NP], int J, const double (&t)[16]) {
-  switch (J) {
-#define SCQR3_P16(I)                                            \
-  case I:                                                       \
-    if constexpr (16 * I < NP) {                                \
-      _Pragma("unroll") for (int q = 0; q < 16; ++q) x[16 * I + q] = t[q]; \
-    }                                                           \
-    break;
-    SCQR3_P16(0) SCQR3_P16(1) SCQR3_P16(2) SCQR3_P16(3)
-#undef SCQR3_P16
-    default: break;
-  }
-}
-// x[4 g + q] -= upd[q] (NaN for a row whose scale is not finite)
-template <int NP>
-__device__ __forceinline__ void sub4(double (&x)[NP], int g, const double (&upd)[4], bool finite) {
-  switch (g) {
-#define SCQR3_S4(I)                                                                          \
-  case I:                                                                                    \
-    if constexpr (4 * I < NP) {                                                              \
-      _Pragma("unroll") for (int q = 0; q < 4; ++q) x[4 * I + q] = finite ? x[4 * I + q] - upd[q] : (double)NAN; \
-    }                                                                                        \
-    break;
-    SCQR3_CASES16(SCQR3_S4)
-#undef SCQR3_S4
-    default: break;
-  }
-}
-
-// y = t R_JJ^{-1} in place for one 16-column diagonal block: forward
-// substitution over its columns (multiply by the rounded reciprocal of r_jj).
-__device__ __forceinline__ void solve16(double (&t)[16], const double* __restrict__ rb,
+// y = h[OFF, OFF + 16) R_JJ^{-1} in place: forward substitution over the
+// block's columns (multiply by the rounded reciprocal of r_jj); rb = the dense
+// 16 x 16 block, ri = its 16 reciprocals (shared memory).
+template <int OFF>
+__device__ __forceinline__ void solve16(double (&h)[32], const double* __restrict__ rb,
                                         const double* __restrict__ ri) {
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
     double rc;
     asm volatile("ld.shared.f64 %0, [%1];" : "=d"(rc) : "r"(tc::smem_u32(ri + c)));
-    const double y = t[c] * rc;
-    t[c] = y;
+    const double y = h[OFF + c] * rc;
+    h[OFF + c] = y;
 #pragma unroll
     for (int c2 = c + 1; c2 < 16; ++c2) {
-      // an explicit shared load: left to itself the compiler hoists all of
-      // the block's R values into registers, which the resident row needs
+      // an explicit shared load: left to itself the compiler hoists the
+      // block's R values into registers ahead of their use
       double rv;
       asm volatile("ld.shared.f64 %0, [%1];" : "=d"(rv) : "r"(tc::smem_u32(rb + c * 16 + c2)));
-      t[c2] = fma(-y, rv, t[c2]);
+      h[OFF + c2] = fma(-y, rv, h[OFF + c2]);
     }
   }
 }
 
 // Per-slot state of the update pipeline.
 struct SlotCtx {
-  uint8_t* sbuf;     // the slot's buffer (staged rows, A planes)
+  uint8_t* sbuf;     // the slot's A planes
   uint8_t* bb;       // B planes of the off-diagonal blocks
   const int* Eb;     // their column exponents
   uint32_t tmem;     // the slot's first tensor-memory column (lane 0)
@@ -271,74 +203,63 @@ struct SlotCtx {
   long long wait_ns;
 };
 
-template <int NP>
-__device__ __forceinline__ Upd plan_of(int ui) {
-  if constexpr (NP == 32) {
-    return Upd{0, 16, 16, 16, 0, 0};
-  } else {
-    return ui == 0 ? Upd{0, 16, 16, 16, 0, 0} : ui == 1 ? Upd{0, 32, 32, 32, 4096, 16} : Upd{32, 16, 48, 16, 20480, 48};
-  }
-}
-
-// Update ui of Plan<NP> on this thread's row: x[C0, C0 + N) -= y[K0, K0 + K)
-// R[K0.., C0..] on the tensor cores. Returns false (slot-uniformly) if the
-// wait for the MMAs ran out.
-template <int NP>
-__device__ __forceinline__ bool update(double (&x)[NP], int ui, const SlotCtx& c, uint32_t& phase,
-                                       uint32_t& commits) {
-  const Upd U = plan_of<NP>(ui);
-  // the row's scale over its K values
+// The scale exponent of h[0, K) and its digit planes (A operand, K-major) in
+// the slot's buffer. Returns false for a non-finite row.
+template <int K>
+__device__ __forceinline__ bool cut_rows(const double (&h)[32], const SlotCtx& c, int& E) {
   unsigned long long mx = 0;
-#pragma unroll 1
-  for (int g = U.k0 / 8; g < (U.k0 + U.K) / 8; ++g) {
-    double v[8];
-    get8(x, g, v);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(v[q]) & 0x7FFFFFFFFFFFFFFFull;
-      mx = mx > b ? mx : b;
-    }
+  for (int k = 0; k < K; ++k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(h[k]) & 0x7FFFFFFFFFFFFFFFull;
+    mx = mx > b ? mx : b;
   }
   const bool finite = (mx >> 52) != 0x7FF;
-  const int E = finite ? scale_exp(mx) : 0;
-  slot_sync(c.slot);  // every warp of the slot is done with the buffer (staged rows, earlier planes)
-  {
-    uint8_t* ar = c.sbuf + (c.r >> 3) * (16 * U.K) + (c.r & 7) * 16;
-    const uint32_t plane = ROWS * U.K * 2;
-#pragma unroll 1
-    for (int kg = 0; kg < U.K / 8; ++kg) {
-      double v[8];
-      get8(x, U.k0 / 8 + kg, v);
-      cut8(v, E, ar + kg * LBO, plane);
-    }
-  }
+  E = finite ? scale_exp(mx) : 0;
+  slot_sync(c.slot);  // the slot's previous planes are consumed (its MMAs have completed)
+  uint8_t* ar = c.sbuf + (c.r >> 3) * (16 * K) + (c.r & 7) * 16;
+#pragma unroll
+  for (int kg = 0; kg < K / 8; ++kg) cut8(&h[8 * kg], E, ar + kg * LBO, ROWS * K * 2);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  slot_sync(c.slot);
-  bool ok = true;
+  return finite;
+}
+
+// Thread 0 of the slot issues product UI's MMAs (after the slot's barrier) and
+// commits them to the slot's mbarrier.
+template <int NP, int UI>
+__device__ __forceinline__ void mma_product(const SlotCtx& c, uint32_t& commits) {
+  constexpr Upd U = plan<NP, UI>();
+  slot_sync(c.slot);  // planes written; the tensor-memory sums of the previous product read back
   if (c.r == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (U.K == 16)
-      issue<16, 16, 0, 0>(desc<16>(tc::smem_u32(c.sbuf)), desc<16>(tc::smem_u32(c.bb + U.boff)), c.tmem, c.idesc0);
-    else
-      issue<32, 32, 0, 0>(desc<32>(tc::smem_u32(c.sbuf)), desc<32>(tc::smem_u32(c.bb + U.boff)), c.tmem, c.idesc0);
+    issue<U.K, 0, 0>(desc<U.K>(tc::smem_u32(c.sbuf)), desc<U.K>(tc::smem_u32(c.bb + U.boff)), c.tmem, c.idesc0);
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(c.mbar)
                  : "memory");
     ++commits;
-    // one thread waits; the barrier below releases the slot
-    ok = tc::wait_parity(c.mbar, phase & 1, c.wait_ns);
   }
+}
+
+// Thread 0 waits for the slot's last commit; the barrier releases the slot.
+// False (slot-uniformly) if the wait ran out.
+__device__ __forceinline__ bool mma_wait(const SlotCtx& c, uint32_t& phase) {
+  bool ok = true;
+  if (c.r == 0) ok = tc::wait_parity(c.mbar, phase & 1, c.wait_ns);
   ++phase;
   if (slot_any(c.slot, !ok)) return false;
   asm volatile("tcgen05.fence::after_thread_sync;");
-  // read back the 8 tile sums of each updated column and apply them
+  return true;
+}
+
+// h[OFF, OFF + 16) -= the product just read back: per column, the 8 tile sums
+// folded exactly into int64 and assembled as sigma_i tau_l 2^-56 W.
+template <int OFF>
+__device__ __forceinline__ void fold16(double (&h)[32], const SlotCtx& c, int E, bool finite, const int* eb) {
   constexpr unsigned long long BIAS = 0x4B400000ull * ((1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
-#pragma unroll 1
-  for (int c4 = 0; c4 < U.N; c4 += 4) {
+#pragma unroll
+  for (int c4 = 0; c4 < 16; c4 += 4) {
     uint32_t v[8][4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) tc::ld4(c.tq + U.N * e + c4, v[e]);
+    for (int e = 0; e < 8; ++e) tc::ld4(c.tq + 16 * e + c4, v[e]);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    double upd[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       // |D_e| < 2^22: D_e + 1.5 2^23 is exact, with bit pattern 0x4B400000 + D_e
@@ -354,19 +275,64 @@ __device__ __forceinline__ bool update(double (&x)[NP], int ui, const SlotCtx& c
       }
       const long long Us = (long long)(Uu - BIAS), Ts = (long long)(Tt - BIAS);
       const long long W = (Us << 21) + (Ts >> 7);  // 2^56 (y r) / (sigma tau), truncated
-      upd[q] = scaled_int(W, E + c.Eb[U.eoff + c4 + q] - 56);
+      const double upd = scaled_int(W, E + eb[c4 + q] - 56);
+      h[OFF + c4 + q] = finite ? h[OFF + c4 + q] - upd : (double)NAN;
     }
-    sub4(x, (U.c0 + c4) / 4, upd, finite);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
-  return true;
 }
 
-// Column exponents of update UI's block of R_k (tau_l = 2^Eb > max_k |r_kl|).
+// 32 columns [c0, c0 + 32) of the row into h (zeros past m and past n). vec:
+// the half lies within n and starts on a 32-byte boundary (X 32-byte aligned,
+// ldx a multiple of 4), so it moves as eight 256-bit loads.
+__device__ __forceinline__ void load_half(double (&h)[32], const double* X, int64_t ldx, int64_t g, int64_t m,
+                                          int c0, int n, bool vec) {
+  const double* src = X + g * ldx + c0;
+  if (g >= m) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) h[c] = 0.0;
+  } else if (vec) {
+#pragma unroll
+    for (int c = 0; c < 32; c += 4)
+      asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+                   : "=d"(h[c]), "=d"(h[c + 1]), "=d"(h[c + 2]), "=d"(h[c + 3]) : "l"(src + c) : "memory");
+  } else {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) h[c] = c0 + c < n ? src[c] : 0.0;
+  }
+}
+
+// h -> columns [c0, c0 + 32) of the row (256-bit stores when vec); the warp's
+// largest |q| per column (the high word of its bit pattern) joins lane c's
+// running maximum cm.
+__device__ __forceinline__ void store_half(const double (&h)[32], double* Q, int64_t ldq, int64_t g, int64_t m,
+                                           int c0, int n, bool vec, int lane, uint32_t& cm) {
+  double* dst = Q + g * ldq + c0;
+  if (g < m) {
+    if (vec) {
+#pragma unroll
+      for (int c = 0; c < 32; c += 4)
+        asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};"
+                     :: "l"(dst + c), "d"(h[c]), "d"(h[c + 1]), "d"(h[c + 2]), "d"(h[c + 3]) : "memory");
+    } else {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c0 + c < n) dst[c] = h[c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const uint32_t hi = (uint32_t)((unsigned long long)__double_as_longlong(h[c]) >> 32) & 0x7FFFFFFFu;
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == c) cm = cm > wm ? cm : wm;
+  }
+}
+
+// Column exponents of product UI's block of R_k (tau_l = 2^Eb > max_k |r_kl|).
 template <int NP, int UI>
 __device__ __forceinline__ void setup_eb(const double* __restrict__ rk, int np, int* Eb) {
-  constexpr Upd U = Plan<NP>::u[UI];
-  for (int l = threadIdx.x; l < U.N; l += THREADS) {
+  constexpr Upd U = plan<NP, UI>();
+  for (int l = threadIdx.x; l < 16; l += THREADS) {
     unsigned long long mx = 0;
     for (int k = 0; k < U.K; ++k) {
       const unsigned long long b =
@@ -377,17 +343,17 @@ __device__ __forceinline__ void setup_eb(const double* __restrict__ rk, int np, 
   }
 }
 
-// Digit planes of update UI's block of R_k (B operand: N columns, K-major;
-// plane t at t * 2 K N bytes), units (column l, K group kg).
+// Digit planes of product UI's block of R_k (B operand: 16 columns, K-major;
+// plane t at t * 32 K bytes), units (column l, K group kg).
 template <int NP, int UI>
 __device__ __forceinline__ void setup_b(const double* __restrict__ rk, int np, const int* Eb, uint8_t* bb) {
-  constexpr Upd U = Plan<NP>::u[UI];
-  for (int u = threadIdx.x; u < U.N * (U.K / 8); u += THREADS) {
-    const int l = u % U.N, kg = u / U.N;
+  constexpr Upd U = plan<NP, UI>();
+  for (int u = threadIdx.x; u < 16 * (U.K / 8); u += THREADS) {
+    const int l = u % 16, kg = u / 16;
     double v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = rk[pk_idx(np, U.k0 + 8 * kg + q, U.c0 + l)];
-    cut8(v, Eb[U.eoff + l], bb + U.boff + (l >> 3) * (16 * U.K) + kg * LBO + (l & 7) * 16, 2 * U.K * U.N);
+    cut8(v, Eb[U.eoff + l], bb + U.boff + (l >> 3) * (16 * U.K) + kg * LBO + (l & 7) * 16, 32 * U.K);
   }
 }
 
@@ -395,12 +361,13 @@ __device__ __forceinline__ void setup_b(const double* __restrict__ rk, int np, c
 
 // X: rows [0, P.m) of the pass's input (ldx), Q: its output (ldq; may be X
 // itself). rk: R_k packed P.np x P.np. colmax (may be null): receives, by
-// atomicMax, the bit pattern of max |q_ij| per column j < n.
+// atomicMax, a bit pattern with the exponent of max |q_ij| per column j < n
+// (the high word of the pattern; the low word zero).
 template <int NP>
 __global__ void __launch_bounds__(tcf::THREADS, 1)
 tc_fused_solve_kernel(const double* X, int64_t ldx, double* Q, int64_t ldq, Params P, int pass,
                       const double* __restrict__ rk, unsigned long long* __restrict__ colmax,
-                      DevState* __restrict__ st) {
+                      DevState* __restrict__ st, int stagger_ns) {
   using namespace tcf;
   using tc::smem_u32;
   using G = FGeo<NP>;
@@ -419,19 +386,19 @@ tc_fused_solve_kernel(const double* X, int64_t ldx, double* Q, int64_t ldq, Para
   const int slot = tid >> 7, r = tid & (ROWS - 1), ws = warp & 3;
   const int n = P.n, np = P.np;
   const int64_t m = P.m;
-  uint8_t* sbuf = base + slot * SBUF;
 
   // R_k: the diagonal blocks (dense 16 x 16, upper part), 1 / r_jj, and the
-  // column exponents of the off-diagonal blocks
+  // digit planes of the off-diagonal blocks with their column exponents
   for (int e = tid; e < G::NB * 256; e += THREADS) {
     const int J = e >> 8, c = (e >> 4) & 15, c2 = e & 15;
     rdb[e] = c2 >= c ? rk[pk_idx(np, 16 * J + c, 16 * J + c2)] : 0.0;
   }
   for (int j = tid; j < NP; j += THREADS) rinv[j] = 1.0 / rk[pk_idx(np, j, j)];
   setup_eb<NP, 0>(rk, np, Eb);
-  if constexpr (PL::NU > 1) {
+  if constexpr (NP == 64) {
     setup_eb<NP, 1>(rk, np, Eb);
     setup_eb<NP, 2>(rk, np, Eb);
+    setup_eb<NP, 3>(rk, np, Eb);
   }
   if (tid < SLOTS) err_sh[tid] = 0;
   if (tid == 0) {
@@ -445,9 +412,10 @@ tc_fused_solve_kernel(const double* X, int64_t ldx, double* Q, int64_t ldq, Para
   }
   __syncthreads();
   setup_b<NP, 0>(rk, np, Eb, bb);
-  if constexpr (PL::NU > 1) {
+  if constexpr (NP == 64) {
     setup_b<NP, 1>(rk, np, Eb, bb);
     setup_b<NP, 2>(rk, np, Eb, bb);
+    setup_b<NP, 3>(rk, np, Eb, bb);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -455,7 +423,7 @@ tc_fused_solve_kernel(const double* X, int64_t ldx, double* Q, int64_t ldq, Para
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
   SlotCtx ctx;
-  ctx.sbuf = sbuf;
+  ctx.sbuf = base + slot * G::SBUF;
   ctx.bb = bb;
   ctx.Eb = Eb;
   ctx.tmem = tmem + slot * TSLOT;
@@ -467,9 +435,18 @@ tc_fused_solve_kernel(const double* X, int64_t ldx, double* Q, int64_t ldq, Para
   ctx.r = r;
   ctx.wait_ns = P.wait_ns;
 
-  unsigned long long cmax[NP / 32];  // max |q| bit patterns of columns 32 h + lane (store phase)
+  // 256-bit row accesses for halves that lie within n, 32-byte aligned
+  const bool vx0 = n >= 32 && ((uintptr_t)X & 31) == 0 && (ldx & 3) == 0;
+  const bool vq0 = n >= 32 && ((uintptr_t)Q & 31) == 0 && (ldq & 3) == 0;
+  const bool vx1 = vx0 && n >= 64, vq1 = vq0 && n >= 64;
+
+  // The slots start apart, so that one slot's integer and tensor-core phases
+  // meet the others' FP64 phases rather than their own.
+  for (int t = 0; t < slot; ++t) __nanosleep(stagger_ns);
+
+  uint32_t cm[NP / 32];  // lane c: the largest |q| high word of column 32 h + c
 #pragma unroll
-  for (int h = 0; h < NP / 32; ++h) cmax[h] = 0;
+  for (int h = 0; h < NP / 32; ++h) cm[h] = 0;
   uint32_t phase = 0;    // completed waits on mdone[slot]
   uint32_t commits = 0;  // commits to mdone[slot] (thread 0 of the slot)
   bool failed = false;
@@ -477,63 +454,54 @@ tc_fused_solve_kernel(const double* X, int64_t ldx, double* Q, int64_t ldq, Para
   for (int64_t it = 0;; ++it) {
     const int64_t row0 = ((it * gridDim.x + blockIdx.x) * SLOTS + slot) * (int64_t)ROWS;
     if (row0 >= m) break;  // uniform in the slot
-    // ---- the warp's 32 rows into the buffer (zeros past m and past n)
-#pragma unroll 2
-    for (int rr = 0; rr < 32; ++rr) {
-      const int row = 32 * ws + rr;
-      const int64_t g = row0 + row;
-#pragma unroll
-      for (int h = 0; h < NP / 32; ++h) {
-        const int c = 32 * h + lane;
-        const bool ok = g < m && c < n;
-        const double* src = ok ? X + g * ldx + c : X;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
-                     :: "r"(smem_u32(sbuf + stage_off(row, c))), "l"(src), "r"(ok ? 8 : 0) : "memory");
-      }
+    const int64_t g = row0 + r;
+    double h[32];
+    int E;
+    bool fin;
+    load_half(h, X, ldx, g, m, 0, n, vx0);
+    solve16<0>(h, rdb, rinv);
+    // U0: x_1 -= y_0 R_01
+    fin = cut_rows<16>(h, ctx, E);
+    mma_product<NP, 0>(ctx, commits);
+    if (!mma_wait(ctx, phase)) {
+      failed = true;
+      break;
     }
-    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-    __syncwarp();
-    double x[NP];
-#pragma unroll
-    for (int c = 0; c < NP; c += 2) {
-      const double2 v = *(const double2*)(sbuf + stage_off(r, c));
-      x[c] = v.x;
-      x[c + 1] = v.y;
-    }
-    // ---- diagonal blocks and off-diagonal updates (update J follows block J)
-#pragma unroll 1
-    for (int J = 0; J < G::NB; ++J) {
-      double t[16];
-      get16(x, J, t);
-      solve16(t, rdb + J * 256, rinv + 16 * J);
-      put16(x, J, t);
-      if (J + 1 < G::NB && !update(x, J, ctx, phase, commits)) {
+    fold16<16>(h, ctx, E, fin, Eb + plan<NP, 0>().eoff);
+    solve16<16>(h, rdb + 256, rinv + 16);
+    if constexpr (NP == 64) {
+      // U1: [x_2 x_3] -= [y_0 y_1] R_{01,23}, as two 16-column products on
+      // the same digit planes; the first runs while y_0, y_1 go out and
+      // x_2, x_3 come in
+      fin = cut_rows<32>(h, ctx, E);
+      mma_product<NP, 1>(ctx, commits);
+      store_half(h, Q, ldq, g, m, 0, n, vq0, lane, cm[0]);
+      load_half(h, X, ldx, g, m, 32, n, vx1);
+      if (!mma_wait(ctx, phase)) {
         failed = true;
         break;
       }
-    }
-    if (failed) break;
-    // ---- the rows out through the buffer (the last MMAs have completed)
-    __syncwarp();
-#pragma unroll
-    for (int c = 0; c < NP; c += 2) *(double2*)(sbuf + stage_off(r, c)) = make_double2(x[c], x[c + 1]);
-    __syncwarp();
-#pragma unroll 4
-    for (int rr = 0; rr < 32; ++rr) {
-      const int row = 32 * ws + rr;
-      const int64_t g = row0 + row;
-#pragma unroll
-      for (int h = 0; h < NP / 32; ++h) {
-        const int c = 32 * h + lane;
-        if (g < m && c < n) {
-          const double v = *(const double*)(sbuf + stage_off(row, c));
-          Q[g * ldq + c] = v;
-          const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-          cmax[h] = cmax[h] > b ? cmax[h] : b;
-        }
+      fold16<0>(h, ctx, E, fin, Eb + plan<NP, 1>().eoff);
+      mma_product<NP, 2>(ctx, commits);
+      if (!mma_wait(ctx, phase)) {
+        failed = true;
+        break;
       }
+      fold16<16>(h, ctx, E, fin, Eb + plan<NP, 2>().eoff);
+      solve16<0>(h, rdb + 512, rinv + 32);
+      // U2: x_3 -= y_2 R_23
+      fin = cut_rows<16>(h, ctx, E);
+      mma_product<NP, 3>(ctx, commits);
+      if (!mma_wait(ctx, phase)) {
+        failed = true;
+        break;
+      }
+      fold16<16>(h, ctx, E, fin, Eb + plan<NP, 3>().eoff);
+      solve16<16>(h, rdb + 768, rinv + 48);
+      store_half(h, Q, ldq, g, m, 32, n, vq1, lane, cm[1]);
+    } else {
+      store_half(h, Q, ldq, g, m, 0, n, vq0, lane, cm[0]);
     }
-    __syncwarp();
   }
   if (failed && r == 0) err_sh[slot] = 1;
   __syncthreads();
@@ -543,10 +511,10 @@ tc_fused_solve_kernel(const double* X, int64_t ldx, double* Q, int64_t ldq, Para
       // the slot's last MMAs finish (bounded) before the tensor memory is freed
       if (commits > 0) tc::wait_parity(ctx.mbar, (commits - 1) & 1, tc::kWaitNs);
     }
-  } else if (colmax) {
+  } else if (colmax && st->gram_after[pass]) {
 #pragma unroll
     for (int h = 0; h < NP / 32; ++h)
-      if (32 * h + lane < n && cmax[h]) atomicMax(&colmax[32 * h + lane], cmax[h]);
+      if (32 * h + lane < n && cm[h]) atomicMax(&colmax[32 * h + lane], (unsigned long long)cm[h] << 32);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -571,14 +539,16 @@ bool tc_fused_supported(int n) { return n > 16 && n <= 64; }
 // Pass k's substitution over rows [0, P.m) of X into Q; colmax (or null)
 // receives the column maxima of Q for the next Gram matrix.
 void launch_tc_fused(int sms, cudaStream_t s, const double* X, int64_t ldx, double* Q, int64_t ldq, const Params& P,
-                     int pass, const double* rk, unsigned long long* colmax, DevState* st) {
+                     int pass, const double* rk, unsigned long long* colmax, DevState* st, int stagger_ns) {
   const int64_t tiles = (P.m + tcf::ROWS - 1) / tcf::ROWS;
   const int64_t want = (tiles + tcf::SLOTS - 1) / tcf::SLOTS;
   const int grid = (int)(want < sms ? (want < 1 ? 1 : want) : sms);
   if (P.n <= 32)
-    tc_fused_solve_kernel<32><<<grid, tcf::THREADS, tcf::FGeo<32>::SMEM, s>>>(X, ldx, Q, ldq, P, pass, rk, colmax, st);
+    tc_fused_solve_kernel<32><<<grid, tcf::THREADS, tcf::FGeo<32>::SMEM, s>>>(X, ldx, Q, ldq, P, pass, rk, colmax, st,
+                                                                              stagger_ns);
   else
-    tc_fused_solve_kernel<64><<<grid, tcf::THREADS, tcf::FGeo<64>::SMEM, s>>>(X, ldx, Q, ldq, P, pass, rk, colmax, st);
+    tc_fused_solve_kernel<64><<<grid, tcf::THREADS, tcf::FGeo<64>::SMEM, s>>>(X, ldx, Q, ldq, P, pass, rk, colmax, st,
+                                                                              stagger_ns);
 }
 
 }  // namespace scqr3
