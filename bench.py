@@ -7,13 +7,20 @@ ABI (scqr3_factor) of a 16,777,216 x 64 matrix X = U diag(sigma) V^T
 larger than the 129 MB L2, so no flush is needed between steps).
 
 Prints one JSON line (rank 0). Also reports:
-  * roofline of the dominant kernel (pass_kernel), timed live per launch with
-    CUDA events recorded by the library on its stream, against the FP64 peak
+  * roofline of the dominant kernel (the one-sweep tensor-core substitution
+    for the headline form, else pass_kernel), timed live per launch with CUDA
+    events recorded by the library on its stream, against the FP64 peak
     derived from unit counts and clocks (152 SMs x 2 DFMA/clk x 2 flop x
     2.07 GHz = 1258.6 GFLOP/s); a cuBLAS DGEMM measurement is given beside it;
+  * path: the step time against the design's own floor (its FP64-pipe work
+    at the FP64 peak plus its Gram MMAs at the sustained BF16 peak);
+  * accuracy at full size: R against the exact R factor of diag(sigma) V^T
+    (m-independent), and against the CPU oracle run once on the same X in a
+    background thread while the GPU legs run;
   * e2e: the same metric with X copied from pinned host memory and Q, R
     copied back inside every timed step;
-  * cpu_baseline: the CPU oracle timed on a bounded sample of the workload;
+  * cpu_baseline: the CPU oracle, as it stands, timed on a bounded sample of
+    the workload, one single-threaded factorization per host core at once;
   * kappa_sweep: one timed factorization per kappa of the scale-up sweep.
 
 `--impl reference` times the CPU oracle instead (no GPU), on a bounded
@@ -47,7 +54,8 @@ PROFILED_BLOCK_BYTES_PER_ROW = 210.3  # pass_kernel<16> on the first 16-column b
 # profiles/tc_gram_kernel_*; for the substitution, the mean over its two update launch shapes), valid for
 # the sources they were taken on.
 PROFILED_TC = {"tc_solve": ("25eb56420f284aac", ("tc_common.cuh", "tc_solve.cu"), 478.7),
-               "tc_gram": ("36e48f579de11899", ("tc_common.cuh", "tc_gram.cu"), 516.4)}
+               "tc_gram": ("36e48f579de11899", ("tc_common.cuh", "tc_gram.cu"), 516.4),
+               "tc_fused": (None, ("tc_common.cuh", "tc_fused.cu"), None)}
 
 
 def profiled_tc_traffic(kind, m, n):
@@ -55,6 +63,8 @@ def profiled_tc_traffic(kind, m, n):
     import hashlib
 
     sha, files, per_row = PROFILED_TC[kind]
+    if sha is None:
+        return None
     h = hashlib.sha256()
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_1809_11085_gb300", "csrc", f), "rb").read())
@@ -167,6 +177,37 @@ def pass_kernel_flops(m, n, kernel, pass_idx, passes, gram_in_pass=True, block=N
     return 0
 
 
+def fused_used(prec, n):
+    """The library runs the one-sweep substitution for the tensor-core form at 16 < n <= 64."""
+    from paper_1809_11085_gb300 import scqr3
+
+    return prec == scqr3.PREC_TC and 16 < n <= 64
+
+
+def fused_fp64_ops(n):
+    """FP64-pipe operations per row of one one-sweep substitution: per 16-column
+    diagonal block 120 FMAs + 16 multiplies, plus one subtraction per entry an
+    off-diagonal product updates (NP = 32: 16 entries; NP = 64: 4 x 16)."""
+    np_ = 32 if n <= 32 else 64
+    return (np_ // 16) * (16 * 15 // 2 + 16) + (16 if np_ == 32 else 64)
+
+
+def exact_r(s, V):
+    """R factor (positive diagonal) of diag(s) V^T: the exact R of
+    X = U diag(s) V^T for orthonormal U, whatever m (numpy Householder QR of an
+    n x n matrix)."""
+    import numpy as np
+
+    _, Re = np.linalg.qr(np.diag(s) @ V.T)
+    return Re * np.sign(np.diag(Re))[:, None]
+
+
+def rel_fro(A, B):
+    import numpy as np
+
+    return float(np.linalg.norm(A - B) / np.linalg.norm(B))
+
+
 def tc_solve_used(prec, n):
     from paper_1809_11085_gb300 import scqr3
 
@@ -263,12 +304,25 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle legs
 
-def oracle_rows_per_s(n, kappa, target_s, seed=77, max_rows=1 << 21):
-    """Time the CPU oracle (single thread, as it stands) on a sample sized for
-    about target_s seconds; returns (rows/s, rows, seconds)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_rows_per_s(n, kappa, target_s, seed=77, max_rows=1 << 21, cores=None):
+    """Time the CPU oracle (as it stands: single-threaded) on the host's cores:
+    `cores` factorizations of one sample at once, one per thread (the oracle's
+    C call releases the interpreter lock), the sample sized for about target_s
+    seconds each. Returns (rows/s over all cores, rows per factorization,
+    seconds, passes, cores)."""
+    import concurrent.futures
+
     import oracle
     from paper_1809_11085_gb300.testmat import testmat
 
+    cores = cores or host_cores()
     m0 = 32768
     X = testmat(m0, n, kappa, seed=seed)
     t0 = time.perf_counter()
@@ -277,19 +331,25 @@ def oracle_rows_per_s(n, kappa, target_s, seed=77, max_rows=1 << 21):
     rows = int(min(max_rows, max(m0, m0 * target_s / max(t_small, 1e-6))))
     rows = max(n, (rows // 1024) * 1024)
     X = testmat(rows, n, kappa, seed=seed + 1)
-    t0 = time.perf_counter()
-    _, _, st, tr = oracle.scqr3(X)
-    t = time.perf_counter() - t0
-    return rows / t, rows, t, tr["passes"]
+    with concurrent.futures.ThreadPoolExecutor(cores) as ex:
+        t0 = time.perf_counter()
+        res = list(ex.map(lambda _: oracle.scqr3(X), range(cores)))
+        t = time.perf_counter() - t0
+    return cores * rows / t, rows, t, res[0][3]["passes"], cores
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    import concurrent.futures
+
     import oracle
     from paper_1809_11085_gb300.testmat import testmat
 
-    # size each step so that warmup + steps stay within a few minutes
+    # one step = one single-threaded oracle factorization per host core, all
+    # at once, of a row sample sized so that warmup + steps stay within a few
+    # minutes
+    cores = host_cores()
     per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
     m0 = 32768
     X = testmat(m0, args.n, args.kappa, seed=91)
@@ -299,23 +359,25 @@ def run_reference(args, rank, world):
     rows = int(min(1 << 21, max(m0, m0 * per_step / max(t_small, 1e-6))))
     rows = max(args.n, (rows // 1024) * 1024)
     X = testmat(rows, args.n, args.kappa, seed=92)
-    for _ in range(args.warmup):
-        oracle.scqr3(X)
-    ts = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.scqr3(X)
-        ts.append(time.perf_counter() - t0)
+    with concurrent.futures.ThreadPoolExecutor(cores) as ex:
+        step = lambda: list(ex.map(lambda _: oracle.scqr3(X), range(cores)))  # noqa: E731
+        for _ in range(args.warmup):
+            step()
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            step()
+            ts.append(time.perf_counter() - t0)
     t = sum(ts) / len(ts)
-    v = rows / t
-    sample = "%d x %d rows of the same U diag(sigma) V^T construction (kappa=%g), one factorization per step" % (
-        rows, args.n, args.kappa)
+    v = cores * rows / t
+    sample = ("%d x %d rows of the same U diag(sigma) V^T construction (kappa=%g); each step %d single-threaded "
+              "factorizations of it at once, one per host core" % (rows, args.n, args.kappa, cores))
     out = {"metric": METRIC, "value": v, "unit": "rows/s", "impl": "reference", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "sCQR3 FP64 on a bounded row sample of the %d x %d workload" % (args.m, args.n),
-                      "m_sample": rows, "n": args.n, "kappa": args.kappa},
-           "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": sample},
+                      "m_sample": rows, "n": args.n, "kappa": args.kappa, "cores": cores},
+           "cpu_baseline": {"value": v, "unit": "rows/s", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -354,7 +416,8 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     m, n, kappa = args.m, args.n, args.kappa
-    X, _, _ = testmat_torch(m, n, kappa, seed=1000 + 100 * 1 + rank, device=dev)
+    X, sig_t, V_t = testmat_torch(m, n, kappa, seed=1000 + 100 * 1 + rank, device=dev)
+    Rex = exact_r(sig_t.cpu().numpy(), V_t.cpu().numpy())
     Q = torch.empty_like(X)
     ws = scqr3.Workspace(m, n, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -374,6 +437,8 @@ def run_gpu(args, rank, world, local_rank):
     orth = torch.linalg.matrix_norm(G, 2).item()
     resid = (torch.linalg.matrix_norm(X - Q @ R) / torch.linalg.matrix_norm(X)).item()
     del G
+    Rh_main = R.cpu().numpy()
+    dR_exact = rel_fro(Rh_main, Rex)
 
     clocks = ClockSampler(local_rank)
     if dist:
@@ -403,7 +468,9 @@ def run_gpu(args, rank, world, local_rank):
     share = {}
     tc_gram_ms, tc_upd_ms = [], []
     tc_path = prec in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC)
-    tcs = tc_solve_used(prec, n)
+    fused = fused_used(prec, n)
+    tcs = tc_solve_used(prec, n) and not fused
+    fused_ms = []
     seen = {}  # (kernel, pass) -> records so far in the current factorization
     for kernel, p, t in recs:
         name = scqr3.KERNEL_NAMES.get(kernel, str(kernel))
@@ -416,6 +483,10 @@ def run_gpu(args, rank, world, local_rank):
             name = "tc_gram_kernel (+ colmax_kernel)"
             if p <= passes - 1:
                 tc_gram_ms.append(t)
+        if fused and kernel == scqr3.KERNEL_PASS:
+            name = "tc_fused_solve_kernel"
+            if p < passes:
+                fused_ms.append(t)
         if tcs and kernel == scqr3.KERNEL_PASS:
             block = j % ((n + tc_block_width(n) - 1) // tc_block_width(n))
             name = "pass_kernel<32|16> (FP64 diagonal blocks)"
@@ -426,8 +497,12 @@ def run_gpu(args, rank, world, local_rank):
             if jj > 0 and p < passes:
                 tc_upd_ms.append((t, ucols[jj - 1]))
         share[name] = share.get(name, 0.0) + t
-        f = pass_kernel_flops(m, n, kernel, p, passes,
-                              gram_in_pass=prec not in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC), block=block)
+        if fused:
+            # DFMA-equivalent flops of the FP64-pipe operations the one-sweep substitution issues
+            f = 2 * fused_fp64_ops(n) * m if (kernel == scqr3.KERNEL_PASS and p < passes) else 0
+        else:
+            f = pass_kernel_flops(m, n, kernel, p, passes,
+                                  gram_in_pass=prec not in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC), block=block)
         if f > 0:
             kflops += f
             kms += t
@@ -444,6 +519,7 @@ def run_gpu(args, rank, world, local_rank):
 
     # the other forms on the same X, one step each (after a warm-up)
     forms = {}
+    form_R = {pname: Rh_main}
     if args.legs != "none":
         Rref = R.clone()
         for fname, fp in (("fp64", scqr3.PREC_FP64), ("tc", scqr3.PREC_TC), ("mixed", scqr3.PREC_MIXED),
@@ -453,12 +529,42 @@ def run_gpu(args, rank, world, local_rank):
             fms = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, workspace=ws, read_info=False, precision=fp),
                         reps=2)
             _, Rf, finf = scqr3.factor(X, Q=Q, workspace=ws, precision=fp)
+            form_R[fname] = Rf.cpu().numpy()
             forms[fname] = {"ms": round(fms, 2), "rows_per_s": m / (fms * 1e-3), "passes": finf.passes,
                             "orth": _orth(torch, Q),
                             "resid": (torch.linalg.matrix_norm(X - Q @ Rf) / torch.linalg.matrix_norm(X)).item(),
                             "dR_vs_headline": (torch.linalg.matrix_norm(Rf - Rref) /
-                                               torch.linalg.matrix_norm(Rref)).item()}
+                                               torch.linalg.matrix_norm(Rref)).item(),
+                            "dR_vs_exact": rel_fro(form_R[fname], Rex)}
         # restore the headline's Q for nothing else: the e2e leg has its own buffers
+
+    cpu = None
+    if not args.no_cpu:
+        v, rows, t, p, cores = oracle_rows_per_s(n, kappa, args.cpu_seconds)
+        cpu = {"value": v, "unit": "rows/s", "cores": cores, "kind": "oracle",
+               "sample": "%d x %d X = U diag(sigma) V^T, kappa=%g; %d single-threaded factorizations (%d passes) "
+                         "at once, one per host core, in %.1f s" % (rows, n, kappa, cores, p, t)}
+
+    # the CPU oracle on the headline X itself, once, in a background thread
+    # (its C call releases the interpreter lock) while the other legs run
+    oracle_job = None
+    if not args.no_cpu:
+        import threading
+
+        import oracle
+
+        Xnp = X.cpu().numpy()
+        oracle_job = {"t0": time.perf_counter()}
+
+        def _run_oracle():
+            try:
+                _, Ro, st, tr = oracle.scqr3(Xnp)
+                oracle_job.update(R=Ro, status=st, passes=tr["passes"], s=time.perf_counter() - oracle_job["t0"])
+            except Exception as exc:  # reported in the line, never fatal to the GPU legs
+                oracle_job["error"] = repr(exc)
+
+        oracle_job["thread"] = threading.Thread(target=_run_oracle, daemon=True)
+        oracle_job["thread"].start()
 
     # e2e: pinned host X -> device, factorization, Q and R -> pinned host, every step
     e2e = None
@@ -515,8 +621,9 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         for kk in (1e2, 1e6, 1e10, 1e14, 1e15, "repeated"):
             sig = repeated_small_sigma(n, 8, 1e-14, 1e7) if kk == "repeated" else None
-            Xs, _, _ = testmat_torch(m, n, 0.0 if sig is not None else kk, seed=1150 + len(sweep),
-                                     device=dev, sigma=sig)
+            Xs, sg, Vs = testmat_torch(m, n, 0.0 if sig is not None else kk, seed=1150 + len(sweep),
+                                       device=dev, sigma=sig)
+            Rex_s = exact_r(sg.cpu().numpy(), Vs.cpu().numpy())
             scqr3.factor(Xs, Q=Q, workspace=ws, read_info=False, precision=prec)
             torch.cuda.synchronize(dev)
             g0, g1 = torch.cuda.Event(True), torch.cuda.Event(True)
@@ -529,22 +636,53 @@ def run_gpu(args, rank, world, local_rank):
             Gs -= torch.eye(n, dtype=torch.float64, device=dev)
             o = torch.linalg.matrix_norm(Gs, 2).item()
             sweep[str(kk)] = {"ms": round(g0.elapsed_time(g1), 2), "passes": inf.passes,
-                              "shifted": inf.shifted, "status": inf.status, "orth": o}
+                              "shifted": inf.shifted, "status": inf.status, "orth": o,
+                              "dR_vs_exact": rel_fro(Rs.cpu().numpy(), Rex_s)}
             del Xs, Gs
             torch.cuda.empty_cache()
-
-    cpu = None
-    if not args.no_cpu:
-        v, rows, t, p = oracle_rows_per_s(n, kappa, args.cpu_seconds)
-        cpu = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
-               "sample": "%d x %d X = U diag(sigma) V^T, kappa=%g, one factorization (%d passes) in %.1f s"
-                         % (rows, n, kappa, p, t)}
 
     legs = {}
     if args.legs == "all":
         legs = extra_legs(torch, dev, stream, args)
     elif args.legs == "csr":
         legs = {"oblique_csr": csr_leg(torch, dev, stream, args.csr_grid)}
+
+    accuracy = {"dR_vs_exact": dR_exact,
+                "exact_note": "||R - R_exact||_F / ||R_exact||_F, R_exact = R factor of diag(sigma) V^T "
+                              "(exact for X = U diag(sigma) V^T, U orthonormal to ~1e-15), headline form",
+                "forms_dR_vs_exact": {k: v.get("dR_vs_exact") for k, v in forms.items()}}
+    if oracle_job is not None:
+        oracle_job["thread"].join()
+    if oracle_job is not None and "R" in oracle_job:
+        Ro = oracle_job["R"]
+        accuracy.update({"oracle": "CPU oracle on the same %d x %d X (one run, single-threaded, %.0f s, %d passes, "
+                                   "status %d)" % (m, n, oracle_job["s"], oracle_job["passes"],
+                                                   oracle_job["status"]),
+                         "dR_vs_oracle": {k: rel_fro(v, Ro) for k, v in form_R.items()},
+                         "oracle_dR_vs_exact": rel_fro(Ro, Rex)})
+    elif oracle_job is not None:
+        accuracy["oracle"] = "failed: %s" % oracle_job.get("error")
+
+    # the design's floor: its FP64-pipe work at the FP64 peak plus its Gram MMAs
+    # at the sustained BF16 peak (the kernels run one after another)
+    path = None
+    if fused:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        fp64_ms = passes * fused_fp64_ops(n) * m / (FP64_PEAK_DERIVED_TFLOPS * 1e12 / 2) * 1e3
+        grams = passes  # the Gram of X and one after each pass but the last
+        tensor_ms = grams * ((m + 63) // 64) * 104 * 2 * 128 * 64 * 16 / (bf16 * 1e12) * 1e3
+        byts = m * n * 8 * (1 + 2 * passes + (passes - 1) + 1)  # scan of X, each pass r/w, Gram reads
+        hbm_ms = byts / (hbm * 1e9) * 1e3
+        floor = fp64_ms + tensor_ms
+        path = {"floor_ms": floor, "frac": floor / ms, "fp64_pipe_ms": fp64_ms, "gram_tensor_ms": tensor_ms,
+                "hbm_ms_overlapped": hbm_ms, "fp64_ops_per_row_per_pass": fused_fp64_ops(n),
+                "note": "floor = the substitution's FP64-pipe operations at 1258.6 GFLOP/s (DFMA rate) + the "
+                        "tensor-core Gram MMAs (104 per 64 rows) at the measured sustained BF16 peak; HBM time "
+                        "(every byte moved once per kernel) overlaps both; per-kernel fractions below",
+                "fp64_6mn2_roofline_ms": 6 * m * n * n / (FP64_PEAK_DERIVED_TFLOPS * 1e12) * 1e3}
 
     fl = flops_of(m, n, passes)
     out = {
@@ -562,15 +700,19 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "inputs (%.1f GB) larger than the 129 MB L2; no flush" % (m * n * 8 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu",
-                     "kernel": ("pass_kernel<32|16> (FP64 DFMA substitution of the 32-column diagonal blocks; "
+                     "kernel": ("tc_fused_solve_kernel (one sweep per pass: FP64 16-column diagonal blocks, "
+                                "off-diagonal blocks on the tensor cores; achieved counts its FP64-pipe operations "
+                                "as DFMA-equivalent flops, %d per row)" % (2 * fused_fp64_ops(n))) if fused else
+                               ("pass_kernel<32|16> (FP64 DFMA substitution of the 32-column diagonal blocks; "
                                 "the off-diagonal blocks on the tensor cores)") if tcs else
                                "pass_kernel<64> (FP64 DFMA%s)" % (", substitution only" if tc_path else ""),
                      "achieved": achieved, "peak": FP64_PEAK_DERIVED_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_DERIVED_TFLOPS) if achieved else None,
-                     "traffic": profiled_traffic(m, n, solve_only=tc_path, tcs=tcs), "traffic_note":
+                     "traffic": (profiled_tc_traffic("tc_fused", m, n) if fused else
+                                 profiled_traffic(m, n, solve_only=tc_path, tcs=tcs)), "traffic_note":
                          "DRAM bytes of one %s launch (ncu at 1048576 rows, scaled by rows)"
-                         % ("32-column diagonal-block" if tcs else "substitution-only" if tc_path
-                            else "fused solve+Gram"),
+                         % ("one-sweep substitution" if fused else "32-column diagonal-block" if tcs else
+                            "substitution-only" if tc_path else "fused solve+Gram"),
                      "launches_timed": kl,
                      "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; cuBLAS DGEMM measured beside it",
                      "cublas_dgemm_tflops": dgemm},
@@ -581,6 +723,8 @@ def run_gpu(args, rank, world, local_rank):
         "path_tflops": fl / (ms * 1e-3) / 1e12,
         "gflops_6mn2": 6 * m * n * n / (ms * 1e-3) / 1e9,
         "kernel_share": {k: round(v / tot, 4) for k, v in share.items()},
+        "path": path,
+        "accuracy": accuracy,
         "orth": orth, "resid": resid,
         "gpu_launches": launches,
         "clocks": clk,

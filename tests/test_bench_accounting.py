@@ -61,3 +61,45 @@ def test_update_roofline_bytes():
     # mean bytes per launch: (16 + 64) * 8 and (16 + 32) * 8 per row
     assert r["bytes_per_launch"] == (1 << 20) * 8 * (80 + 48) / 2
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+
+
+def fused_ops_restated(n):
+    """FP64-pipe operations per row of the one-sweep substitution, counted from
+    its structure: NP / 16 diagonal blocks of 16 columns (16 * 15 / 2 FMAs and 16
+    multiplies each) and one subtraction per entry an off-diagonal product
+    updates (NP = 64: x_1 by y_0, x_2 and x_3 by [y_0 y_1], x_3 by y_2)."""
+    np_ = 32 if n <= 32 else 64
+    blocks = np_ // 16
+    updated = {32: [16], 64: [16, 16, 16, 16]}[np_]
+    return blocks * (16 * 15 // 2 + 16) + sum(updated)
+
+
+@pytest.mark.parametrize("n", [17, 32, 33, 64])
+def test_fused_fp64_ops(n):
+    assert bench.fused_fp64_ops(n) == fused_ops_restated(n)
+    assert bench.fused_fp64_ops(64) == 608
+    # a quarter-plus of the unblocked substitution's n^2 FP64 flops per row
+    assert bench.fused_fp64_ops(64) < 64 * 64 // 6
+
+
+def test_fused_used_range():
+    from paper_1809_11085_gb300 import scqr3
+
+    assert [n for n in (16, 17, 64, 65) if bench.fused_used(scqr3.PREC_TC, n)] == [17, 64]
+    assert not bench.fused_used(scqr3.PREC_FP64, 64) and not bench.fused_used(scqr3.PREC_MIXED_TC, 64)
+
+
+def test_exact_r_of_the_generator():
+    """exact_r(s, V) is the R factor of X = U diag(s) V^T for any orthonormal U:
+    it matches numpy's Householder R of such an X (signs fixed) to rounding."""
+    import numpy as np
+
+    from paper_1809_11085_gb300.testmat import testmat_factors
+
+    U, s, V = testmat_factors(3000, 12, 1e6, seed=5)
+    X = (U * s) @ V.T
+    _, Rn = np.linalg.qr(X)
+    Rn = Rn * np.sign(np.diag(Rn))[:, None]
+    Re = bench.exact_r(s, V)
+    assert np.all(np.diag(Re) > 0) and np.allclose(np.tril(Re, -1), 0)
+    assert np.linalg.norm(Re - Rn) / np.linalg.norm(Rn) < 1e-12
