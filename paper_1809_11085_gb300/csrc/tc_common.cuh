@@ -1,6 +1,6 @@
 // tc_common.cuh -- device helpers shared by the tensor-core kernels: tcgen05
-// issue and read-back, bounded mbarrier waits, and the exact fixed-point digit
-// split of FP64 values into 7-bit BF16 digits.
+// issue and read-back, bounded mbarrier waits, and the balanced fixed-point
+// digit split of FP64 values into signed 7-bit BF16 digits.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -55,14 +55,45 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&v)[16]) {
                : "r"(taddr) : "memory");
 }
 
-// |x| / 2^E * 2^56 truncated to an integer (< 2^56 when |x| < 2^E).
-__device__ __forceinline__ unsigned long long fixed56(double x, int E) {
+// The balanced fixed-point split shared by the tensor-core kernels. A value x
+// with |x| < 2^(E-1) becomes N = round(x 2^(56-E)), |N| < 2^55 (half-way cases
+// away from zero: the error is at most 2^(E-57) and symmetric), written as
+// N = sum_s d_s 2^(7 (7 - s)) with digits d_1 .. d_7 in [-64, 63] and d_0 in
+// [-64, 64]. With M = N + BIAS56 (64 in every 7-bit field; 0 <= M < 129 2^49)
+// the digits are the unsigned fields of M less 64: d_s = ((M >> (49 - 7 s)) &
+// 127) - 64 for s >= 1 and d_0 = (M >> 49) - 64. Every digit is exactly a BF16
+// number and a product of two is at most 2^12 in magnitude. The rounding and
+// the signed digits make the error of the split zero-mean, unlike truncation,
+// which biases every |x| low.
+constexpr unsigned long long BIAS56 = 0x0081020408102040ull;  // 64 (1 + 2^7 + ... + 2^49)
+
+// M = round(x 2^(56-E)) + BIAS56 for |x| < 2^(E-1) (integer operations only).
+__device__ __forceinline__ unsigned long long biased56(double x, int E) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   int ex = (int)((bits >> 52) & 0x7FF);
   unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
   if (ex) mant |= 1ull << 52; else ex = 1;
-  const int sh = ex - 1019 - E;  // F = mant * 2^sh
-  return sh >= 0 ? (sh <= 3 ? (mant << sh) : (1ull << 56) - 1) : (sh > -64 ? (mant >> -sh) : 0ull);
+  const int sh = ex - 1019 - E;  // N = mant 2^sh, sh <= 2 when |x| < 2^(E-1)
+  const unsigned long long F =
+      sh >= 0 ? (sh <= 2 ? (mant << sh) : (1ull << 55) - 1) : (sh > -64 ? (mant + (1ull << (-sh - 1))) >> -sh : 0ull);
+  return (long long)bits < 0 ? BIAS56 - F : BIAS56 + F;
+}
+
+// The same for an element held as a float pair (hi, lo), value hi + lo (the
+// mixed form's iterates; hi in the low word): each float is rounded to the
+// fixed point on its own and the two integers are added, so no FP64
+// arithmetic is needed; E must leave |hi| + |lo| < 2^(E-1).
+__device__ __forceinline__ long long fix_float(uint32_t f, int E) {
+  int ex = (int)((f >> 23) & 0xFF);
+  long long mant = (long long)(f & 0x7FFFFFu);
+  if (ex) mant |= 0x800000ll; else ex = 1;
+  const int sh = ex - 94 - E;  // value mant 2^(ex - 150), times 2^(56 - E)
+  const long long F = sh >= 0 ? (sh <= 32 ? (mant << sh) : 0x7FFFFFFFFFFFFFll)
+                              : (sh > -40 ? ((mant + (1ll << (-sh - 1))) >> -sh) : 0ll);
+  return (f & 0x80000000u) ? -F : F;
+}
+__device__ __forceinline__ unsigned long long biased56_pair(unsigned long long bits, int E) {
+  return BIAS56 + (unsigned long long)(fix_float((uint32_t)bits, E) + fix_float((uint32_t)(bits >> 32), E));
 }
 
 __device__ __forceinline__ void ld4(uint32_t taddr, uint32_t (&v)[4]) {
@@ -76,37 +107,47 @@ __device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr) : "memory");
 }
 
-// The same for an element held as a float pair (hi, lo), value hi + lo (the
-// mixed form's iterates; hi in the low word). Each float becomes its own
-// fixed-point integer and the two are added as signed integers, so no FP64
-// arithmetic is needed; E must leave |hi + lo| < 2^E. Returns |F| and sets the
-// sign bit (bit 31) in *sign.
-__device__ __forceinline__ long long fix_float(uint32_t f, int E) {
-  int ex = (int)((f >> 23) & 0xFF);
-  long long mant = (long long)(f & 0x7FFFFFu);
-  if (ex) mant |= 0x800000ll; else ex = 1;
-  const int sh = ex - 94 - E;  // value mant 2^(ex - 150), times 2^(56 - E)
-  const long long F = sh >= 0 ? (sh <= 32 ? (mant << sh) : 0x7FFFFFFFFFFFFFll) : (sh > -40 ? (mant >> -sh) : 0ll);
-  return (f & 0x80000000u) ? -F : F;
-}
-__device__ __forceinline__ unsigned long long fixed56_pair(unsigned long long bits, int E, uint32_t* sign) {
-  const long long S = fix_float((uint32_t)bits, E) + fix_float((uint32_t)(bits >> 32), E);
-  *sign = S < 0 ? 0x80000000u : 0u;
-  return (unsigned long long)(S < 0 ? -S : S);
+// Digit s of two entries (biased M0, M1: rows r and r + 1 of a column) as a
+// BF16 pair: the fields f (< 128; f <= 128 for s = 0) are placed side by side
+// and added to the BF16 pattern of 128 (0x4300), which gives the exact BF16
+// value 128 + f (BF16 resolves units between 128 and 256, and 0x4300 + 128 is
+// the pattern of 256); one exact BF16x2 subtraction of 192 leaves f - 64.
+template <int S>
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long M0, unsigned long long M1) {
+  const uint32_t lo = (uint32_t)(M0 >> (49 - 7 * S)), hi = (uint32_t)(M1 >> (49 - 7 * S));
+  const uint32_t w0 = __byte_perm(lo, hi, 0x5410);
+  uint32_t w = S == 0 ? (w0 & 0x00FF00FFu) + 0x43004300u : (w0 & 0x007F007Fu) | 0x43004300u;
+  __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&w);
+  v = __hsub2(v, __floats2bfloat162_rn(192.0f, 192.0f));
+  return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Digit s of two entries (rows r and r + 1 of a column) as a BF16 pair with
-// their signs (bits 15 and 31 of `signs`). The digits a, b < 128 are placed
-// side by side and ORed into the BF16 pattern of 128 (0x4300): that is the
-// exact BF16 value 128 + a, since BF16 resolves units between 128 and 256;
-// one exact BF16x2 subtraction of 128 leaves a and b.
-template <int S>
-__device__ __forceinline__ uint32_t digit_pair(unsigned long long F0, unsigned long long F1, uint32_t signs) {
-  const uint32_t lo = (uint32_t)(F0 >> (49 - 7 * S)), hi = (uint32_t)(F1 >> (49 - 7 * S));
-  uint32_t w = (__byte_perm(lo, hi, 0x5410) & 0x007F007Fu) | 0x43004300u;
-  __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&w);
-  v = __hsub2(v, __floats2bfloat162_rn(128.0f, 128.0f));
-  return *reinterpret_cast<uint32_t*>(&v) | signs;
+// Eight consecutive values as 8 digit planes of one core-matrix row each (16
+// bytes: 8 BF16 digits), at dst + s * plane; |x| < 2^(E-1).
+__device__ __forceinline__ void cut8(const double* x, int E, uint8_t* dst, uint32_t plane) {
+  unsigned long long M[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) M[r] = biased56(x[r], E);
+#define SCQR3_CUTS(S)                                \
+  {                                                  \
+    uint4 w;                                         \
+    w.x = digit_pair<S>(M[0], M[1]);                 \
+    w.y = digit_pair<S>(M[2], M[3]);                 \
+    w.z = digit_pair<S>(M[4], M[5]);                 \
+    w.w = digit_pair<S>(M[6], M[7]);                 \
+    *(uint4*)(dst + (S) * plane) = w;                \
+  }
+  SCQR3_CUTS(0) SCQR3_CUTS(1) SCQR3_CUTS(2) SCQR3_CUTS(3) SCQR3_CUTS(4) SCQR3_CUTS(5) SCQR3_CUTS(6)
+  SCQR3_CUTS(7)
+#undef SCQR3_CUTS
+}
+
+// Scale exponent of a non-negative bit-pattern maximum for the balanced
+// split: 2^(E-1) > the value (-1000 for zero, so every digit is 0).
+__device__ __forceinline__ int split_exp(unsigned long long mx) {
+  if (mx == 0) return -1000;
+  const int ex = (int)(mx >> 52);
+  return (ex ? ex : 1) - 1023 + 2;
 }
 
 }  // namespace tc

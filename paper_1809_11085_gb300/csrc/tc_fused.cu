@@ -122,31 +122,6 @@ __device__ __forceinline__ int slot_any(int slot, int pred) {
   return r;
 }
 
-// Eight consecutive values as 8 digit planes of one core-matrix row each
-// (16 bytes: 8 BF16 digits), at dst + s * plane; |x| < 2^E.
-__device__ __forceinline__ void cut8(const double* x, int E, uint8_t* dst, uint32_t plane) {
-  unsigned long long F[8];
-  uint32_t sp[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    F[r] = tc::fixed56(x[r], E);
-    const uint32_t sgn = (uint32_t)((unsigned long long)__double_as_longlong(x[r]) >> 32) & 0x80000000u;
-    sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
-  }
-#define SCQR3_CUTS(S)                               \
-  {                                                 \
-    uint4 w;                                        \
-    w.x = tc::digit_pair<S>(F[0], F[1], sp[0]);     \
-    w.y = tc::digit_pair<S>(F[2], F[3], sp[1]);     \
-    w.z = tc::digit_pair<S>(F[4], F[5], sp[2]);     \
-    w.w = tc::digit_pair<S>(F[6], F[7], sp[3]);     \
-    *(uint4*)(dst + (S) * plane) = w;               \
-  }
-  SCQR3_CUTS(0) SCQR3_CUTS(1) SCQR3_CUTS(2) SCQR3_CUTS(3) SCQR3_CUTS(4) SCQR3_CUTS(5) SCQR3_CUTS(6)
-  SCQR3_CUTS(7)
-#undef SCQR3_CUTS
-}
-
 // W 2^e2 as a double from the bits of W (integer operations only): W's
 // leading 53 bits (truncated), zero for W = 0 or below the normal range.
 __device__ __forceinline__ double scaled_int(long long W, int e2) {
@@ -158,13 +133,6 @@ __device__ __forceinline__ double scaled_int(long long W, int e2) {
   unsigned long long bits = sgn | ((unsigned long long)(ex < 2047 ? ex : 2047) << 52);
   if (ex < 2047) bits |= (a >> 11) & 0xFFFFFFFFFFFFFull;
   return (W == 0 || ex <= 0) ? 0.0 : __longlong_as_double((long long)bits);
-}
-
-// 2^E > the non-negative bit-pattern maximum mx (-1000 for zero)
-__device__ __forceinline__ int scale_exp(unsigned long long mx) {
-  if (mx == 0) return -1000;
-  const int ex = (int)(mx >> 52);
-  return (ex ? ex : 1) - 1023 + 1;
 }
 
 // y = h[OFF, OFF + 16) R_JJ^{-1} in place: forward substitution over the
@@ -214,11 +182,11 @@ __device__ __forceinline__ bool cut_rows(const double (&h)[32], const SlotCtx& c
     mx = mx > b ? mx : b;
   }
   const bool finite = (mx >> 52) != 0x7FF;
-  E = finite ? scale_exp(mx) : 0;
+  E = finite ? tc::split_exp(mx) : 0;
   slot_sync(c.slot);  // the slot's previous planes are consumed (its MMAs have completed)
   uint8_t* ar = c.sbuf + (c.r >> 3) * (16 * K) + (c.r & 7) * 16;
 #pragma unroll
-  for (int kg = 0; kg < K / 8; ++kg) cut8(&h[8 * kg], E, ar + kg * LBO, ROWS * K * 2);
+  for (int kg = 0; kg < K / 8; ++kg) tc::cut8(&h[8 * kg], E, ar + kg * LBO, ROWS * K * 2);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   return finite;
 }
@@ -262,7 +230,7 @@ __device__ __forceinline__ void fold16(double (&h)[32], const SlotCtx& c, int E,
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      // |D_e| < 2^22: D_e + 1.5 2^23 is exact, with bit pattern 0x4B400000 + D_e
+      // |D_e| <= 8 * 32 * 64^2 = 2^20: D_e + 1.5 2^23 is exact, with bit pattern 0x4B400000 + D_e
       // (the constant leaves with BIAS). U takes D_0..3 with weights 2^21, 2^14,
       // 2^7, 1; T takes D_4..7 with the same weights.
       unsigned long long Uu = 0, Tt = 0;
@@ -339,7 +307,7 @@ __device__ __forceinline__ void setup_eb(const double* __restrict__ rk, int np, 
           (unsigned long long)__double_as_longlong(rk[pk_idx(np, U.k0 + k, U.c0 + l)]) & 0x7FFFFFFFFFFFFFFFull;
       mx = mx > b ? mx : b;
     }
-    Eb[U.eoff + l] = scale_exp(mx);
+    Eb[U.eoff + l] = tc::split_exp(mx);
   }
 }
 
@@ -353,7 +321,7 @@ __device__ __forceinline__ void setup_b(const double* __restrict__ rk, int np, c
     double v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = rk[pk_idx(np, U.k0 + 8 * kg + q, U.c0 + l)];
-    cut8(v, Eb[U.eoff + l], bb + U.boff + (l >> 3) * (16 * U.K) + kg * LBO + (l & 7) * 16, 32 * U.K);
+    tc::cut8(v, Eb[U.eoff + l], bb + U.boff + (l >> 3) * (16 * U.K) + kg * LBO + (l & 7) * 16, 32 * U.K);
   }
 }
 

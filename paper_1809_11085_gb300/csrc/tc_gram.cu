@@ -5,32 +5,37 @@
 // of a tall-skinny matrix costs as much as the substitution. The tensor cores
 // multiply BF16 exactly into FP32, which allows an exact fixed-point split:
 //
-//  * every column j gets a scale sigma_j = 2^E_j > max_i |q_ij| (colmax_kernel);
-//  * |q_ij| / sigma_j * 2^56 is truncated to an integer F < 2^56 and cut into
-//    eight 7-bit digits a_0 .. a_7 (a_0 most significant), each carrying the
-//    sign of q_ij, so q_ij = sigma_j * sum_s a_s 2^(-7(s+1)) up to less than
-//    sigma_j 2^-56; every digit is exactly a BF16 number;
-//  * a product of two digits is below 2^14 and the tensor core accumulates
-//    it exactly in FP32 as long as a sum stays below 2^24: 256 rows of up to
-//    four digit pairs (4 * 256 * 127^2 < 2^24);
+//  * every column j gets a scale sigma_j = 2^E_j > 2 max_i |q_ij| (the column
+//    maxima come from colmax_kernel, or from the one-sweep substitution that
+//    wrote Q);
+//  * q_ij / sigma_j * 2^56 is rounded to an integer N, |N| < 2^55, and cut
+//    into eight signed digits a_0 .. a_7 (a_0 most significant; a_1 .. a_7 in
+//    [-64, 63], a_0 in [-64, 64]: the balanced split of tc_common.cuh), so
+//    q_ij = sigma_j * sum_s a_s 2^(-7(s+1)) up to at most sigma_j 2^-57, with
+//    an error of zero mean; every digit is exactly a BF16 number;
+//  * a product of two digits is at most 2^12 and the tensor core accumulates
+//    it exactly in FP32 as long as a sum stays within 2^24: 1024 rows of up to
+//    four digit pairs (4 * 1024 * 64^2 = 2^24);
 //  * D_d = sum over digit pairs (s, t) with s + t = d, d = 0 .. 7, is read back
-//    from tensor memory every 256 rows. The digit sums are exact integers, so
+//    from tensor memory every 1024 rows. The digit sums are exact integers, so
 //    U = D_0 2^21 + D_1 2^14 + D_2 2^7 + D_3 and T = D_4 2^21 + ... + D_7
-//    (per row below 2^35 and 2^37.3: all d + 1 pairs of D_d are at most
-//    127^2) are accumulated exactly in int64 over all of a CTA's rows (below
-//    2^63 up to 2^25.7 rows per CTA; a 288 GB device holds at most 2^28 rows
-//    of 128 columns, spread over at least 45 CTAs per block), and only the
-//    final 2^-35 U + 2^-63 T is formed in FP64: the FP64 pipe, the scarce one,
-//    does no work per row. Pairs with s + t > 7 (below 2^-56 relative) are
+//    (per 1024 rows below 2^45.1) are accumulated exactly in int64 over all
+//    of a CTA's rows (below 2^63 up to 2^27.9 rows per CTA; a 288 GB device
+//    holds at most 2^28 rows of 128 columns, spread over at least 45 CTAs per
+//    block), and only the final 2^-35 U + 2^-63 T is formed in FP64: the FP64
+//    pipe, the scarce one, does no work per row. Pairs with s + t > 7 (at
+//    most 7 * 2^12 * 2^-70 < 2^-55 of sigma_j sigma_k per row, zero mean) are
 //    dropped.
 //
-// The result differs from q_j^T q_k by at most m 2^-53 sigma_j sigma_k (each
-// value truncated to 2^-56 of its scale, and the pairs s + t > 7 not formed,
-// below 2^-53.2 sigma_j sigma_k per row). With sigma <= 2 max |q| that is at
-// most about 4.3 m u ||q_j|| ||q_k||, so ||E|| <= 4.3 m n u ||Q||^2: a
-// norm-wise Gram error of the FP64 form's order, inside the
-// 11 (mn + n(n+1)) u ||Q||^2 shift of Eq. (finds2), so the factorization keeps
-// its guarantees.
+// The result differs from q_j^T q_k by at most about m 2^-54 sigma_j sigma_k
+// (each value rounded to 2^-57 of its scale, and the pairs s + t > 7 not
+// formed). With sigma <= 4 max |q| that is at most about 8.5 m u ||q_j||
+// ||q_k||, so ||E|| <= 8.5 m n u ||Q||^2: a norm-wise Gram error of the FP64
+// form's order, inside the 11 (mn + n(n+1)) u ||Q||^2 shift of Eq. (finds2),
+// so the factorization keeps its guarantees. Unlike truncation, the rounding
+// and the signed digits leave the error unbiased: the diagonal does not come
+// out systematically low, which matters where a pass's plain Cholesky decides
+// at the margin (Alg. 2's breakdown rule).
 //
 // Blocks: the columns form operand blocks of 64. For n <= 64 one block, and
 // every CTA computes it; for 64 < n <= 128 the Gram matrix is the blocks
@@ -72,7 +77,7 @@ namespace tc {
 
 constexpr int BW = 64;              // columns of one operand block
 constexpr int NPMAX = 128;          // largest padded n
-constexpr int GROUP = 256;          // rows per read-back group
+constexpr int GROUP = 1024;         // rows per read-back group
 constexpr int THREADS = 256;   // slicer and read-back threads (the producer warp comes on top)
 constexpr uint32_t LBO = 128;       // K-direction core-matrix stride
 constexpr int STAGE = 65536;        // digit planes of one chunk (one or two operand blocks)
@@ -128,12 +133,12 @@ __device__ __forceinline__ void issue_e(uint64_t dbase, uint32_t tmem, uint32_t 
 }
 
 template <int KC, int S>
-__device__ __forceinline__ void store_plane(uint8_t* dst, const unsigned long long (&F)[8], const uint32_t (&sp)[4]) {
+__device__ __forceinline__ void store_plane(uint8_t* dst, const unsigned long long (&M)[8]) {
   uint4 w4;
-  w4.x = digit_pair<S>(F[0], F[1], sp[0]);
-  w4.y = digit_pair<S>(F[2], F[3], sp[1]);
-  w4.z = digit_pair<S>(F[4], F[5], sp[2]);
-  w4.w = digit_pair<S>(F[6], F[7], sp[3]);
+  w4.x = digit_pair<S>(M[0], M[1]);
+  w4.y = digit_pair<S>(M[2], M[3]);
+  w4.z = digit_pair<S>(M[4], M[5]);
+  w4.w = digit_pair<S>(M[6], M[7]);
   *(uint4*)(dst + plane_off<KC>(S)) = w4;
 }
 
@@ -316,7 +321,7 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
         bad = 1;  // non-finite input: the Gram matrix is NaN
       } else if (cm > 0.0) {
         const int ex = (int)((colmax[tid] >> 52) & 0x7FF);
-        E = (ex ? ex : 1) - 1023 + 1 + pairs;  // cm < 2^E (pairs: |hi + lo| < 2^E)
+        E = (ex ? ex : 1) - 1023 + 2 + pairs;  // cm < 2^(E-1) (pairs: |hi| + |lo| < 2^(E-1))
         sg = ldexp(1.0, E);
       }
     }
@@ -371,6 +376,10 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   const bool upper = row < 64;
   const bool rb_skip = !offd && (qd & 1) == 1 && h == 0;
   double f2 = 0.0;  // OBL: ||Q||_F^2 of this thread's entries (diagonal-block CTAs)
+  // diagonal-block CTAs: sum of the squares of digit 4 of this thread's
+  // values (one column, tid % 64), the square pair (4, 4) of d = 8 that the
+  // tiles do not hold; added to the diagonal it keeps the split unbiased there
+  long long s44 = 0;
   // exact digit-sum accumulators of this thread's 32 entries: U (d = 0..3)
   // and T (d = 4..7)
   long long U[CW], T[CW];
@@ -441,22 +450,14 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
         const int j = u & ((1 << lgc) - 1), ig = u >> lgc;
         const int col = j < BW ? colA + j : colB + (j - BW);
         const int E = Esh[col];
-        unsigned long long F[8];
-        uint32_t sp[4] = {0u, 0u, 0u, 0u};  // sign bits of rows 2p (bit 15) and 2p + 1 (bit 31)
+        unsigned long long F[8];  // biased fixed-point values (balanced split)
         if constexpr (!OBL) {
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int i = ig * 8 + r;
             double x = 0.0;
             if (col < n && i < rows) x = bulk ? xs[i * n + col] : src[(row0 + i) * lds + col];
-            uint32_t sgn;
-            if (pairs) {
-              F[r] = tc::fixed56_pair((unsigned long long)__double_as_longlong(x), E, &sgn);
-            } else {
-              F[r] = tc::fixed56(x, E);
-              sgn = (uint32_t)((unsigned long long)__double_as_longlong(x) >> 32) & 0x80000000u;
-            }
-            sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
+            F[r] = pairs ? tc::biased56_pair((unsigned long long)__double_as_longlong(x), E) : tc::biased56(x, E);
           }
         } else {
           double xv[8];
@@ -482,21 +483,24 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
             }
           }
 #pragma unroll
+          for (int r = 0; r < 8; ++r) F[r] = tc::biased56(xv[r], E);
+        }
+        if (!offd) {
+#pragma unroll
           for (int r = 0; r < 8; ++r) {
-            F[r] = tc::fixed56(xv[r], E);
-            const uint32_t sgn = (uint32_t)((unsigned long long)__double_as_longlong(xv[r]) >> 32) & 0x80000000u;
-            sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
+            const int d4 = (int)((F[r] >> 21) & 127) - 64;
+            s44 += d4 * d4;
           }
         }
         uint8_t* dst = sb + (j >> 6) * GK::BREG + ((j & 63) >> 3) * GK::SBO + ig * LBO + (j & 7) * 16;
-        tc::store_plane<KC, 0>(dst, F, sp);
-        tc::store_plane<KC, 1>(dst, F, sp);
-        tc::store_plane<KC, 2>(dst, F, sp);
-        tc::store_plane<KC, 3>(dst, F, sp);
-        tc::store_plane<KC, 4>(dst, F, sp);
-        tc::store_plane<KC, 5>(dst, F, sp);
-        tc::store_plane<KC, 6>(dst, F, sp);
-        tc::store_plane<KC, 7>(dst, F, sp);
+        tc::store_plane<KC, 0>(dst, F);
+        tc::store_plane<KC, 1>(dst, F);
+        tc::store_plane<KC, 2>(dst, F);
+        tc::store_plane<KC, 3>(dst, F);
+        tc::store_plane<KC, 4>(dst, F);
+        tc::store_plane<KC, 5>(dst, F);
+        tc::store_plane<KC, 6>(dst, F);
+        tc::store_plane<KC, 7>(dst, F);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[stg])) : "memory");
@@ -549,10 +553,12 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   long long* xch = (long long*)stages;  // 64 x 64 int64 (32 KB) of stage 0
+  long long* s44sh = xch + BW * BW;     // then the slicers' digit-4 square sums
   if (!producer && !upper) {
 #pragma unroll
     for (int k = 0; k < CW; ++k) xch[jr * BW + CW * h + k] = T[k];
   }
+  if (!producer) s44sh[tid] = s44;
   __syncthreads();
   if (!producer && upper && !rb_skip) {
     const double sj = sig[colA + jr];
@@ -560,7 +566,12 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
     for (int k = 0; k < CW; ++k) {
       const int c = CW * h + k;
       if (offd || c >= jr) {
-        const double a = fma(0x1p-35, (double)U[k], 0x1p-63 * (double)(T[k] + xch[jr * BW + c]));
+        double a = fma(0x1p-35, (double)U[k], 0x1p-63 * (double)(T[k] + xch[jr * BW + c]));
+        if (!offd && c == jr) {  // the diagonal: the square pair (4, 4), weight 2^-70
+          long long q = 0;
+          for (int t = jr; t < THREADS; t += BW) q += s44sh[t];
+          a = fma(0x1p-70, (double)q, a);
+        }
         part[pk_idx(NPK, colA + jr, colB + c)] = a * sj * sig[colB + c];
       }
     }

@@ -10,21 +10,23 @@
 // run here on the BF16 tensor cores (one launch per 32 columns to update;
 // written below as Y = Y_J with k = w columns and R01 = the updated columns
 // of R_JK) through the exact digit split of the Gram kernel:
-//  * row i of Y gets the scale sigma_i = 2^E_i > max_k |y_ik| (its own k
-//    values), column l of R01 the scale tau_l = 2^E_l > max_k |r_kl|;
-//  * both are cut into eight signed 7-bit digits (56 bits); digit products are
-//    exact in FP32, and tile e of tensor memory sums the pairs (s, t) with
-//    s + t = e over the k columns: at most 8 * 32 * 127^2 < 2^24, exact;
+//  * row i of Y gets the scale sigma_i = 2^E_i > 2 max_k |y_ik| (its own k
+//    values), column l of R01 the scale tau_l = 2^E_l > 2 max_k |r_kl|;
+//  * both are rounded to 2^-56 of their scale and cut into eight signed
+//    digits in [-64, 64] (the balanced split of tc_common.cuh); digit products
+//    are exact in FP32, and tile e of tensor memory sums the pairs (s, t) with
+//    s + t = e over the k columns: at most 8 * 32 * 64^2 = 2^20, exact;
 //  * per entry the tile sums fold exactly into int64, U = sum_{e<=3} D_e
-//    2^{7(3-e)} (< 2^40.1) and T = sum_{e>=4} D_e 2^{7(7-e)} (< 2^42.4), then
-//    W = 2^21 U + floor(T / 2^7) (< 2^61.2, truncation below 2^-56 of
-//    sigma_i tau_l); sigma_i tau_l 2^-56 W is assembled as a double from the
-//    bits of W (integer operations), and x'_il = x_il - that, one FP64
-//    subtraction per entry.
+//    2^{7(3-e)} (< 2^41.1) and T = sum_{e>=4} D_e 2^{7(7-e)}, then
+//    W = 2^21 U + floor(T / 2^7) (truncation below 2^-56 of sigma_i tau_l);
+//    sigma_i tau_l 2^-56 W is assembled as a double from the bits of W
+//    (integer operations), and x'_il = x_il - that, one FP64 subtraction per
+//    entry.
 // The computed product differs from y_i^T r_l by less than
-// 2^-56 (sigma_i ||r_l||_1 + tau_l ||y_i||_1) + k 2^-53 sigma_i tau_l (the
-// truncation of each value, and the digit pairs s + t > 7 not formed): at
-// most about 4 k u ||y_i|| ||r_l||, a perturbation of R01 of norm O(u ||R||),
+// 2^-57 (sigma_i ||r_l||_1 + tau_l ||y_i||_1) + k 2^-55 sigma_i tau_l (the
+// rounding of each value, and the digit pairs s + t > 7 not formed, both of
+// zero mean), plus 2^-56 sigma_i tau_l for the fold: at most about
+// 4 k u ||y_i|| ||r_l||, a perturbation of R01 of norm O(u ||R||),
 // the order of the row-wise backward error of FP64 substitution
 // (Eq. backward2) on which the analysis of Sec. 3 rests.
 //
@@ -115,30 +117,6 @@ __device__ __forceinline__ void issue(uint64_t adesc, uint64_t bdesc, uint32_t t
   }
 }
 
-// Eight consecutive values of a row (or column) as 8 digit planes of one
-// core-matrix row each (16 bytes: 8 BF16 digits), at dst + s * plane.
-__device__ __forceinline__ void cut8(const double (&x)[8], int E, uint8_t* dst, uint32_t plane) {
-  unsigned long long F[8];
-  uint32_t sp[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    F[r] = tc::fixed56(x[r], E);
-    const uint32_t sgn = (uint32_t)((unsigned long long)__double_as_longlong(x[r]) >> 32) & 0x80000000u;
-    sp[r >> 1] |= (r & 1) ? sgn : (sgn >> 16);
-  }
-#define SCQR3_CUT(S)                                                                                \
-  {                                                                                                 \
-    uint4 w;                                                                                        \
-    w.x = tc::digit_pair<S>(F[0], F[1], sp[0]);                                                     \
-    w.y = tc::digit_pair<S>(F[2], F[3], sp[1]);                                                     \
-    w.z = tc::digit_pair<S>(F[4], F[5], sp[2]);                                                     \
-    w.w = tc::digit_pair<S>(F[6], F[7], sp[3]);                                                     \
-    *(uint4*)(dst + (S) * plane) = w;                                                               \
-  }
-  SCQR3_CUT(0) SCQR3_CUT(1) SCQR3_CUT(2) SCQR3_CUT(3) SCQR3_CUT(4) SCQR3_CUT(5) SCQR3_CUT(6) SCQR3_CUT(7)
-#undef SCQR3_CUT
-}
-
 // W 2^e2 as a double, built from the bits of W with integer operations (the
 // FP64 pipe, the scarce one, is left for the update itself): W's leading 53
 // bits (truncated: relative error below 2^-52), exponent 63 - clz(|W|) + e2.
@@ -153,14 +131,6 @@ __device__ __forceinline__ double scaled_int(long long W, int e2) {
   unsigned long long bits = sgn | ((unsigned long long)(ex < 2047 ? ex : 2047) << 52);
   if (ex < 2047) bits |= (a >> 11) & 0xFFFFFFFFFFFFFull;
   return (W == 0 || ex <= 0) ? 0.0 : __longlong_as_double((long long)bits);
-}
-
-// Scale exponent of a non-negative bit-pattern maximum: 2^E > the value
-// (-1000 for zero, so every digit is 0).
-__device__ __forceinline__ int scale_exp(unsigned long long mx) {
-  if (mx == 0) return -1000;
-  const int ex = (int)(mx >> 52);
-  return (ex ? ex : 1) - 1023 + 1;
 }
 
 }  // namespace tcs
@@ -221,7 +191,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
             (unsigned long long)__double_as_longlong(rk[pk_idx(np, r0 + k, c0 + tid)]) & 0x7FFFFFFFFFFFFFFFull;
         mx = mx > b ? mx : b;
       }
-    Eb[tid] = scale_exp(mx);
+    Eb[tid] = tc::split_exp(mx);
   }
   if (tid == 0) {
     err_sh = 0;
@@ -242,7 +212,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
     double v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = l < n1 ? rk[pk_idx(np, r0 + 8 * kg + q, c0 + l)] : 0.0;
-    cut8(v, Eb[l], bbuf + (l >> 3) * SBO + kg * LBO + (l & 7) * 16, BPLANE);
+    tc::cut8(v, Eb[l], bbuf + (l >> 3) * SBO + kg * LBO + (l & 7) * 16, BPLANE);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -332,14 +302,14 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
         mx = mx > b ? mx : b;
       }
       const bool finite = (mx >> 52) != 0x7FF;
-      const int E = finite ? scale_exp(mx) : 0;
+      const int E = finite ? tc::split_exp(mx) : 0;
 #pragma unroll
       for (int kh = 0; kh < K / 16; ++kh) {
         const int kg = (K / 16) * hf + kh;
         double v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = yb[r * yld + 8 * kg + q];
-        cut8(v, E, arow + kg * LBO, APLANE);
+        tc::cut8(v, E, arow + kg * LBO, APLANE);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;");

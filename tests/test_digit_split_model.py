@@ -1,18 +1,22 @@
 """CPU model of the exact digit split behind the tensor-core forms.
 
-Readings 20 and 21 claim that cutting each value into eight signed 7-bit
-digits relative to a power-of-two scale (per Gram column, or per row of Y and
-per column of R_JK in the substitution) makes every digit product and every
-tile sum exact in FP32, and that a product of k terms through the split
-differs from the exact one by less than
-    2^-56 (sigma ||r||_1 + tau ||y||_1) + k 2^-53 sigma tau:
-truncating each value to 2^-56 of its scale, plus the digit pairs with
-s + t >= 8 that are not formed (at most 7 127^2 2^-70 < 2^-53.2 of sigma tau
-per term). These tests check those claims with exact integer arithmetic
-(Python ints), independent of any GPU code: the bounds on the tile sums that
-the kernels rely on (worst case, all digits 127), the fold
-W = 2^21 U + floor(T / 2^7), and the error bound on random, badly scaled and
-worst-case inputs.
+Readings 20 to 22 claim that rounding each value to 2^-56 of a power-of-two
+scale (per Gram column, or per row of Y and per column of R_JK in the
+substitution; the scale more than twice the largest value) and cutting it into
+eight signed digits in [-64, 64] (the balanced split) makes every digit
+product and every tile sum exact in FP32, and that a product of k terms
+through the split differs from the exact one by less than
+    2^-57 (sigma ||r||_1 + tau ||y||_1) + k 2^-55 sigma tau + 2^-56 sigma tau:
+rounding each value to half a unit of 2^-56 of its scale, the digit pairs
+with s + t >= 8 that are not formed (at most 7 * 64^2 * 2^-70 of sigma tau per
+term), and the fold's final truncation. The rounding and the signed digits
+make the error zero-mean; the truncating split it replaces biased every |x|
+low, so Gram diagonals came out low on average. These tests check those
+claims with exact integer arithmetic (Python ints), independent of any GPU
+code: the bounds on the tile sums that the kernels rely on (worst case, all
+digits at their largest magnitude), the fold W = 2^21 U + floor(T / 2^7), the
+error bound on random, badly scaled and worst-case inputs, and the absence of
+bias.
 """
 import math
 from fractions import Fraction
@@ -21,22 +25,34 @@ import numpy as np
 import pytest
 
 DIGITS, BITS = 8, 7
+BIAS56 = sum(64 << (7 * s) for s in range(DIGITS))  # 64 in every 7-bit field
 
 
 def scale_exp(vals):
-    """E with 2^E > max |v| (the kernels' rule: one above the max's exponent)."""
+    """E with 2^(E-1) > max |v| (the kernels' rule: two above the max's exponent)."""
     mx = max(abs(v) for v in vals)
     if mx == 0:
         return None
-    return math.frexp(mx)[1]  # mx < 2^E, mx >= 2^(E-1)
+    return math.frexp(mx)[1] + 1  # mx < 2^(E-1), mx >= 2^(E-2)
+
+
+def round_half_away(q):
+    """Nearest integer to the Fraction q, half-way cases away from zero."""
+    a = abs(q)
+    n = math.floor(a + Fraction(1, 2))
+    return n if q >= 0 else -n
 
 
 def digits(v, E):
-    """Signed 7-bit digits a_0 .. a_7 of v relative to 2^E: F = floor(|v| 2^(56-E))."""
-    F = math.floor(Fraction(abs(v)) * Fraction(2) ** (56 - E))
-    assert F < 2 ** 56
-    sgn = -1 if v < 0 else 1
-    return [sgn * ((F >> (49 - 7 * s)) & 127) for s in range(DIGITS)]
+    """Signed digits d_0 .. d_7 of v relative to 2^E: N = round(v 2^(56-E)),
+    M = N + BIAS56, d_s = field s of M less 64 (field 0: the bits above 49)."""
+    N = round_half_away(Fraction(v) * Fraction(2) ** (56 - E))
+    assert abs(N) < 2 ** 55
+    M = N + BIAS56
+    assert 0 <= M < 129 * 2 ** 49
+    ds = [(M >> 49) - 64] + [((M >> (49 - 7 * s)) & 127) - 64 for s in range(1, DIGITS)]
+    assert sum(d << (7 * (DIGITS - 1 - s)) for s, d in enumerate(ds)) == N
+    return ds
 
 
 def value_of(ds, E):
@@ -71,50 +87,66 @@ def model_dot(y, r):
     return Fraction(W) * Fraction(2) ** (Ey + Er - 56), Ey, Er, max(abs(d) for d in D)
 
 
-def test_digits_represent_values_to_2_pow_minus_56():
+def test_digits_represent_values_to_2_pow_minus_57():
     rng = np.random.default_rng(11)
     for _ in range(2000):
         v = float(rng.standard_normal() * 10.0 ** rng.integers(-30, 30))
         E = scale_exp([v, v * 0.5])
-        err = abs(value_of(digits(v, E), E) - Fraction(v))
-        assert err < Fraction(2) ** (E - 56)
-        assert all(abs(d) <= 127 for d in digits(v, E))
+        ds = digits(v, E)
+        err = abs(value_of(ds, E) - Fraction(v))
+        assert err <= Fraction(2) ** (E - 57)
+        assert all(-64 <= d <= 63 for d in ds[1:]) and -64 <= ds[0] <= 64
 
 
-@pytest.mark.parametrize("k,rows_per_tile", [(16, 1), (32, 1), (64, 256)])
-def test_worst_case_tile_sums_below_2_pow_24(k, rows_per_tile):
-    """All digits at 127 (the bound): the substitution's tiles (k = 16, 32 per
-    entry) and the Gram's tiles (64-row chunks read back every 256 rows, at
-    most 4 pairs per tile in each lane half) stay exact in FP32."""
+def test_digit_extremes():
+    """The largest value below the scale's half gives the top digit 64, the
+    most negative -64; a BF16 number represents every digit exactly."""
+    E = 1
+    top = 1.0 - 2.0 ** -53  # < 2^(E-1) = 1
+    assert digits(top, E)[0] == 64 and digits(-top, E)[0] == -64
+    for d in range(-64, 65):
+        assert float(np.float32(d)) == d and (abs(d) < 256)  # 8 significant bits suffice
+
+
+@pytest.mark.parametrize("k,rows_per_tile", [(16, 1), (32, 1), (64, 1024)])
+def test_worst_case_tile_sums_within_2_pow_24(k, rows_per_tile):
+    """All digits at magnitude 64 (the bound): the substitution's tiles (k = 16,
+    32 per entry) stay below 2^22 (the kernels' float-to-integer step needs
+    that), and the Gram's tiles (64-row chunks read back every 1024 rows, at
+    most 4 pairs per tile in each lane half) stay within 2^24, exact in FP32."""
     if rows_per_tile == 1:
-        worst = max((e + 1) * k * 127 * 127 for e in range(DIGITS))
+        worst = max((e + 1) * k * 64 * 64 for e in range(DIGITS))
+        assert worst < 2 ** 22
     else:
-        worst = 4 * rows_per_tile * 127 * 127  # lane-half pairing of the Gram kernel
-    assert worst < 2 ** 24
+        worst = 4 * rows_per_tile * 64 * 64  # lane-half pairing of the Gram kernel
+    assert worst <= 2 ** 24
 
 
 def test_fold_bounds_fit_int64():
     k = 32
-    D = [(e + 1) * k * 127 * 127 for e in range(DIGITS)]
+    D = [(e + 1) * k * 64 * 64 for e in range(DIGITS)]
     U = sum(D[e] * 2 ** (7 * (3 - e)) for e in range(4))
     T = sum(D[e] * 2 ** (7 * (7 - e)) for e in range(4, 8))
-    assert U < 2 ** 40.1 and T < 2 ** 42.4
-    assert abs(fold(D)) < 2 ** 61.2 and abs(fold([-d for d in D])) < 2 ** 61.2 + 1
+    assert U < 2 ** 41.1 and T < 2 ** 43.4
+    assert abs(fold(D)) < 2 ** 62.2 and abs(fold([-d for d in D])) < 2 ** 62.2 + 1
+    # the Gram's per-group sums: 4 pairs of 1024 rows per tile half
+    G = 4 * 1024 * 64 * 64
+    assert G * sum(2 ** (7 * (3 - e)) for e in range(4)) < 2 ** 45.1
 
 
 def split_bound(y, r, Ey, Er):
     sig, tau = Fraction(2) ** Ey, Fraction(2) ** Er
-    return (Fraction(2) ** -56 * (sig * sum(Fraction(abs(float(b))) for b in r)
+    return (Fraction(2) ** -57 * (sig * sum(Fraction(abs(float(b))) for b in r)
                                  + tau * sum(Fraction(abs(float(a))) for a in y))
-            + len(y) * Fraction(2) ** -53 * sig * tau)
+            + (len(y) * Fraction(2) ** -55 + Fraction(2) ** -56) * sig * tau)
 
 
 @pytest.mark.parametrize("k", [16, 32])
 def test_product_error_within_stated_bound(k):
-    """|model - exact| <= 2^-56 (sigma ||r||_1 + tau ||y||_1) + k 2^-53 sigma
-    tau, with sigma, tau the power-of-two scales, on random and badly scaled
-    vectors; in norm terms at most about 4 k u ||y||_2 ||r||_2, the order of
-    the FP64 dot product's gamma_k bound."""
+    """|model - exact| <= 2^-57 (sigma ||r||_1 + tau ||y||_1) + (k 2^-55 +
+    2^-56) sigma tau, with sigma, tau the power-of-two scales, on random and
+    badly scaled vectors; in norm terms at most about 4 k u ||y||_2 ||r||_2,
+    the order of the FP64 dot product's gamma_k bound."""
     rng = np.random.default_rng(100 + k)
     for trial in range(300):
         y = rng.standard_normal(k) * np.exp2(rng.integers(-40, 40, size=k) * (trial % 3 == 0))
@@ -132,27 +164,78 @@ def test_product_error_within_stated_bound(k):
 
 @pytest.mark.parametrize("k", [16, 32])
 def test_worst_case_dropped_pairs_near_the_bound(k):
-    """Every value at the top of its scale (F = 2^56 - 8: every digit 127 but
-    the last, 120):
-    the digit pairs that are not formed make the largest error, and it comes
-    within a factor 2 of the bound's k 2^-53 sigma tau term, so that term is
-    needed and not loose."""
-    v = 1.0 - 2.0 ** -53  # scale 2^0 > v
+    """Values whose digits 1..7 are all -64 (N = 64 2^49 - 64 (2^49 - 1) / 127 * 127 ...,
+    chosen digit by digit): the pairs that are not formed then add up with one
+    sign, and the error comes within a factor 4 of the bound's k 2^-55 sigma tau
+    term, so that term is needed and not loose."""
+    E = 1
+    ds = [64] + [-64] * 7
+    N = sum(d << (7 * (DIGITS - 1 - s)) for s, d in enumerate(ds))
+    v = float(Fraction(N) * Fraction(2) ** (E - 56))
+    assert digits(v, E) == ds
     y, r = [v] * k, [v] * k
     got, Ey, Er, Dmax = model_dot(y, r)
-    assert Ey == 0 and Er == 0 and Dmax < 2 ** 24
+    assert Ey == E and Er == E and Dmax <= 2 ** 22
     exact = sum(Fraction(a) * Fraction(b) for a, b in zip(y, r))
     err = abs(got - exact)
     assert err <= split_bound(y, r, Ey, Er)
-    assert err >= k * Fraction(2) ** -53 * Fraction(1, 2)
+    assert err >= k * Fraction(2) ** -55 * Fraction(2) ** (Ey + Er) / 4
+
+
+def gram_diag_model(q):
+    """A Gram diagonal q . q as the Gram kernel forms it: the tile sums of the
+    pairs s + t <= 7, plus the square pair (4, 4) of e = 8, sum_i d_4(q_i)^2,
+    which the kernel accumulates exactly on the side (weight 2^-70 of
+    sigma^2). The other dropped pairs of a square are products of different
+    digits (zero mean) or squares 2^-14 smaller."""
+    got, E, _, _ = model_dot(q, q)
+    if E is None:
+        return got, E
+    s44 = sum(digits(v, E)[4] ** 2 for v in q)
+    return got + Fraction(s44) * Fraction(2) ** (2 * E - 70), E
+
+
+def test_gram_diagonal_is_unbiased():
+    """Reading 22: the truncating split lowered Gram diagonals by about 3.7 u
+    relative on average. With the balanced split alone, the dropped square
+    pair (4, 4) still lowers them (about -0.7 u here, more where the column
+    scale is far above the typical value); with its exact sum added, the mean
+    error is zero to within sampling noise (below 0.1 u here)."""
+    rng = np.random.default_rng(22)
+    errs, errs_plain = [], []
+    for _ in range(40):
+        q = list(map(float, rng.standard_normal(256)))
+        exact = sum(Fraction(a) * Fraction(a) for a in q)
+        got, _ = gram_diag_model(q)
+        plain, _, _, _ = model_dot(q, q)
+        errs.append(float((got - exact) / exact))
+        errs_plain.append(float((plain - exact) / exact))
+    u = 2.0 ** -53
+    assert np.mean(errs_plain) < -0.3 * u  # the bias the side sum removes
+    assert abs(np.mean(errs)) < 0.1 * u, (np.mean(errs) / u)
+
+
+def test_off_diagonal_products_are_unbiased():
+    """Products of different values (Gram off-diagonals, the substitution's
+    y_J R_JK) have zero-mean error without any correction."""
+    rng = np.random.default_rng(23)
+    errs = []
+    for _ in range(60):
+        y = list(map(float, rng.standard_normal(32)))
+        r = list(map(float, rng.standard_normal(32)))
+        got, _, _, _ = model_dot(y, r)
+        exact = sum(Fraction(a) * Fraction(b) for a, b in zip(y, r))
+        errs.append(float(got - exact) / float(np.linalg.norm(y) * np.linalg.norm(r)))
+    u = 2.0 ** -53
+    assert abs(np.mean(errs)) < 0.2 * u, (np.mean(errs) / u)
 
 
 def test_gram_entry_error_matches_norm_wise_bound():
     """A Gram entry of m rows through the split (scale per column) differs
-    from q_j . q_k by at most m 2^-53 sigma_j sigma_k (the bound above with
-    k = m; the truncation terms are below m 2^-55 sigma_j sigma_k): with
-    sigma <= 2 max |q| this is at most about 4.3 m u ||q_j|| ||q_k||, so
-    ||E|| <= 4.3 m n u ||Q||^2, inside the 11 (mn + n(n+1)) u ||Q||^2 shift of
+    from q_j . q_k by at most m 2^-54 sigma_j sigma_k (the bound above with
+    k = m; the rounding terms are below m 2^-56 sigma_j sigma_k): with
+    sigma <= 4 max |q| this is at most about 8.5 m u ||q_j|| ||q_k||, so
+    ||E|| <= 8.5 m n u ||Q||^2, inside the 11 (mn + n(n+1)) u ||Q||^2 shift of
     Eq. (finds2)."""
     rng = np.random.default_rng(7)
     m = 300
@@ -161,7 +244,7 @@ def test_gram_entry_error_matches_norm_wise_bound():
         qk = rng.standard_normal(m) * 10.0 ** rng.integers(-5, 5)
         got, Ej, Ek, Dmax = model_dot(list(map(float, qj)), list(map(float, qk)))
         exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(qj, qk))
-        assert abs(got - exact) <= m * Fraction(2) ** -53 * Fraction(2) ** (Ej + Ek)
+        assert abs(got - exact) <= m * Fraction(2) ** -54 * Fraction(2) ** (Ej + Ek)
 
 
 def test_exact_for_short_integers():
