@@ -152,6 +152,10 @@ typedef struct {
                                             of pass k broke down, else 0   */
   double s[SCQR3_MAX_PASSES];            /* shift of pass k, 0 if none     */
   double norm2[SCQR3_MAX_PASSES];        /* ||Q_{k-1}||^2 estimate used    */
+  int more;                              /* 1: the device planned another
+                                            pass after pass `passes` (its
+                                            Gram matrix follows the last
+                                            solve); 0 once the call is done */
 } scqr3_info;
 
 /* Bytes of device workspace that scqr3_factor needs for (m, n, B, opts).
@@ -222,6 +226,48 @@ int scqr3_factor_host(const double *X, int64_t m, int n, int64_t ldx,
                       const scqr3_B *B, double *Q, int64_t ldq, double *R,
                       double *Qdev, void *workspace, size_t workspace_bytes,
                       const scqr3_opts *opts, scqr3_info *info, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Row-partitioned form: the data-parallel structure of the method, for a
+ * caller that holds X in row blocks X_r on several devices or processes. The
+ * Gram matrix of X is the sum of its blocks' Gram matrices (Sec. 1: the
+ * Gram matrix is formed "by addition", one reduction of n(n+1)/2 values per
+ * pass; Sec. 7.1, Table 8); the shift, the Cholesky factorization and R are
+ * then the same on every block's holder, and each solves its own rows. Per
+ * rank, with G and G' device vectors of `gram_words` doubles:
+ *
+ *   scqr3_gram_partial(X_r, ..., G)          G = X_r's share of X^T X
+ *   [caller: G := sum of G over the ranks, e.g. an allreduce]
+ *   for pass = 0, 1, ..., max_passes - 1:
+ *     scqr3_apply_pass(pass, G, m, X_r, ..., Q_r, R, G')
+ *         the shift / Cholesky of this pass on G (shift from the global m),
+ *         Q_r := (pass 0: X_r; later: Q_r) R_pass^{-1}, and, if the device
+ *         planned another pass (info->more), G' = Q_r's share of Q^T Q
+ *     [caller: G := sum of G' over the ranks]
+ *
+ * The pass decisions of Alg. 3 / Alg. 2 are taken on the device from G, so
+ * every rank takes the same ones; once a factorization is done the remaining
+ * calls return at once (a fixed sequence is correct; a caller may also stop
+ * after the first call whose info->more is 0). G's entries are partial sums
+ * in an internal packed order: the caller only adds them elementwise. The
+ * workspace carries the state from call to call: one per rank, not shared.
+ * Forms: SCQR3_PREC_FP64 or SCQR3_PREC_TC; B NULL or block-diagonal with
+ * the caller's ||B||_2 in B->norm2 (> 0, the same on every rank) and each
+ * rank's rows whole blocks (m_r % bs == 0); the mixed forms and a CSR B
+ * (whose rows reach across the blocks) are SCQR3_E_UNSUPPORTED. Argument codes
+ * -k name argument k of the function called. */
+int scqr3_shard_sizes(int64_t m_local, int n, const scqr3_B *B,
+                      const scqr3_opts *opts, size_t *workspace_bytes,
+                      size_t *gram_words);
+int scqr3_gram_partial(const double *X, int64_t m_local, int n, int64_t ldx,
+                       const scqr3_B *B, double *G, void *workspace,
+                       size_t workspace_bytes, const scqr3_opts *opts,
+                       scqr3_info *info, void *stream);
+int scqr3_apply_pass(int pass, const double *G, int64_t m_global,
+                     const double *X, int64_t m_local, int n, int64_t ldx,
+                     const scqr3_B *B, double *Q, int64_t ldq, double *R,
+                     double *G_next, void *workspace, size_t workspace_bytes,
+                     const scqr3_opts *opts, scqr3_info *info, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Batched form (FP64, B = I): many independent, uneven factorizations, each

@@ -531,6 +531,7 @@ __device__ __forceinline__ void chol_body(const Params& P, int pass, const doubl
     if (!done && !more) st->status = SCQR3_E_MAXPASS;
     info->status = st->status;
     info->passes = pass + 1;
+    info->more = st->gram_after[pass];
     info->shifted[pass] = shifted_sh;
     info->unshifted_fail[pass] = ufail_sh;
     info->s[pass] = s_sh;

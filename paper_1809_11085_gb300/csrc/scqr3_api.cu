@@ -172,9 +172,9 @@ int sm_count() {
   return (dev >= 0 && dev < kMaxDevices && g_geo[dev].ready) ? g_geo[dev].sms : 1;
 }
 
-int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts) {
+int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, bool shard = false) {
   if (n < 1) return -3;
-  if (m < n) return -2;
+  if (shard ? m < 1 : m < n) return -2;  // a row block of a partitioned X may be shorter than n
   if (B && (B->bs != 0 && B->bs != 1 && B->bs != 2 && B->bs != 4 && B->bs != 8 && B->bs != 16))
     return -5;
   if (B && B->bs > 0 && ((m % B->bs) != 0 || !B->blocks)) return -5;
@@ -442,7 +442,33 @@ struct Call {
 
 // Carves the workspace, fills Params, and queues the state reset and the
 // preparation of B. Arguments were checked by the caller.
+int setup_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void* workspace,
+               size_t workspace_bytes, int host_chunks, double* R, double* Rpass, scqr3_info* info,
+               cudaStream_t s, Call* c);
+
+// Carves the workspace, fills Params, and queues the state reset and the
+// preparation of B. Arguments were checked by the caller.
 int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void* workspace,
+               size_t workspace_bytes, int host_chunks, double* R, double* Rpass, scqr3_info* info,
+               cudaStream_t s, Call* c) {
+  const int r = setup_call(m, n, B, opts, workspace, workspace_bytes, host_chunks, R, Rpass, info, s, c);
+  if (r != SCQR3_OK) return r;
+  if (cudaMemsetAsync(c->st, 0, sizeof(DevState), s) != cudaSuccess) return SCQR3_E_CUDA;
+  if (cudaMemsetAsync(info, 0, sizeof(scqr3_info), s) != cudaSuccess) return SCQR3_E_CUDA;
+  if (B && B->bs > 0) {
+    tick(s, SCQR3_KERNEL_BFACTOR, 0);
+    launch_bfactor(s, B->bs, B->blocks, m / B->bs, c->lt, c->st, sm_count());
+  }
+  if (c->csr) {
+    tick(s, SCQR3_KERNEL_BFACTOR, 0);
+    launch_csr_check(sm_count() * 4, s, m, B, c->st);
+  }
+  return SCQR3_OK;
+}
+
+// The launch context of a call on an existing workspace, without queueing
+// anything (a continuing row-partitioned factorization keeps its state).
+int setup_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void* workspace,
                size_t workspace_bytes, int host_chunks, double* R, double* Rpass, scqr3_info* info,
                cudaStream_t s, Call* c) {
   if (((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
@@ -483,17 +509,6 @@ int begin_call(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, void*
   P.solve_only = (c->csr || c->tc) ? 1 : 0;
   set_options(&P, opts);
   c->fused = c->tc && !c->mixed && g_fused_solve.load() != 0 && tc_fused_supported(n);
-
-  if (cudaMemsetAsync(c->st, 0, sizeof(DevState), s) != cudaSuccess) return SCQR3_E_CUDA;
-  if (cudaMemsetAsync(info, 0, sizeof(scqr3_info), s) != cudaSuccess) return SCQR3_E_CUDA;
-  if (B && B->bs > 0) {
-    tick(s, SCQR3_KERNEL_BFACTOR, 0);
-    launch_bfactor(s, B->bs, B->blocks, m / B->bs, c->lt, c->st, sm_count());
-  }
-  if (c->csr) {
-    tick(s, SCQR3_KERNEL_BFACTOR, 0);
-    launch_csr_check(sm_count() * 4, s, m, B, c->st);
-  }
   return SCQR3_OK;
 }
 
@@ -630,9 +645,17 @@ void solve_rows(Call& c, int k, const double* src, int64_t lds, double* dst, int
   }
 }
 
-// After pass k: the separate Gram kernels (n = 256, CSR B), the fixed-order
-// sum and the Cholesky of pass k + 1.
+// After pass k: the separate Gram kernels (n = 256, tensor cores, CSR B) and
+// the fixed-order sum of the partial Gram matrices into `out`.
+void after_pass_gram(Call& c, int k, const double* Q, int64_t ldq, double* out);
+
+// After pass k: the next Gram matrix and the Cholesky of pass k + 1.
 void after_pass(Call& c, int k, const double* Q, int64_t ldq) {
+  after_pass_gram(c, k, Q, ldq, c.gram);
+  launch_any_chol(c, k + 1);
+}
+
+void after_pass_gram(Call& c, int k, const double* Q, int64_t ldq, double* out) {
   if (c.P.np == 256) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     launch_gram256(c.grid, c.s, Q, ldq, c.P, k, c.partials, c.L.part_stride, c.st);
@@ -646,8 +669,7 @@ void after_pass(Call& c, int k, const double* Q, int64_t ldq) {
     launch_csr_gram(c.P.np, c.L.csr_grid, c.s, Q, ldq, c.P, k, c.B, c.partials, c.L.part_stride, c.st);
   }
   tick(c.s, SCQR3_KERNEL_REDUCE, k + 1);
-  launch_reduce(c.s, c.partials, c.L.n_partials, c.L.part_stride, c.gram, c.st, k);
-  launch_any_chol(c, k + 1);
+  launch_reduce(c.s, c.partials, c.L.n_partials, c.L.part_stride, out, c.st, k);
 }
 
 int check_factor_pointers(const double* X, int64_t m, int n, int64_t ldx, const double* Q, int64_t ldq,
@@ -837,6 +859,116 @@ extern "C" int scqr3_factor_host(const double* X, int64_t m, int n, int64_t ldx,
     return SCQR3_E_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return SCQR3_E_CUDA;
   if (cudaStreamSynchronize(h->copy) != cudaSuccess) return SCQR3_E_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
+  return SCQR3_OK;
+}
+
+// ---- row-partitioned form ------------------------------------------------------------------
+
+namespace {
+// The forms the row-partitioned calls take (see include/scqr3.h); codes in
+// scqr3_factor's numbering.
+int check_shard(int64_t m_local, int n, const scqr3_B* B, const scqr3_opts* opts) {
+  const int a = check_args(m_local, n, B, opts, true);
+  if (a != SCQR3_OK) return a;
+  if (opts && (opts->precision == SCQR3_PREC_MIXED || opts->precision == SCQR3_PREC_MIXED_TC))
+    return SCQR3_E_UNSUPPORTED;
+  if (B && B->bs == 0) return SCQR3_E_UNSUPPORTED;
+  if (B && !(B->norm2 > 0.0)) return -5;
+  return SCQR3_OK;
+}
+
+// scqr3_factor's argument codes (m -2, n -3, B -5, opts -12) in another
+// prototype's positions.
+int remap(int r, int m_pos, int n_pos, int b_pos, int o_pos) {
+  switch (r) {
+    case -2: return -m_pos;
+    case -3: return -n_pos;
+    case -5: return -b_pos;
+    case -12: return -o_pos;
+    default: return r;
+  }
+}
+}  // namespace
+
+extern "C" int scqr3_shard_sizes(int64_t m_local, int n, const scqr3_B* B, const scqr3_opts* opts,
+                                 size_t* workspace_bytes, size_t* gram_words) {
+  if (!workspace_bytes) return -5;
+  if (!gram_words) return -6;
+  const int a = check_shard(m_local, n, B, opts);
+  if (a != SCQR3_OK) return remap(a, 1, 2, 3, 4);
+  Layout L;
+  int grid;
+  PassGeom geo;
+  const int prec = opts ? opts->precision : SCQR3_PREC_FP64;
+  const int r = make_layout(m_local, n, B, prec, 0, &L, &grid, &geo);
+  if (r != SCQR3_OK) return r;
+  *workspace_bytes = L.total;
+  *gram_words = (size_t)L.part_stride;
+  return SCQR3_OK;
+}
+
+extern "C" int scqr3_gram_partial(const double* X, int64_t m_local, int n, int64_t ldx, const scqr3_B* B,
+                                  double* G, void* workspace, size_t workspace_bytes, const scqr3_opts* opts,
+                                  scqr3_info* info, void* stream) {
+  int a = check_shard(m_local, n, B, opts);
+  if (a != SCQR3_OK) return remap(a, 2, 3, 5, 9);
+  if (!X) return -1;
+  if (ldx < n) return -4;
+  if (!G) return -6;
+  if (!workspace) return -7;
+  if (!info) return -10;
+  Call c;
+  a = begin_call(m_local, n, B, opts, workspace, workspace_bytes, 0, nullptr, nullptr, info, (cudaStream_t)stream,
+                 &c);
+  if (a != SCQR3_OK) return a;
+  const int slots = first_gram(c, X, ldx, 0, m_local, 0);
+  tick(c.s, SCQR3_KERNEL_REDUCE, 0);
+  launch_reduce(c.s, c.partials, slots, c.L.part_stride, G, c.st, -1);
+  tick(c.s, -1, -1);
+  if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
+  return SCQR3_OK;
+}
+
+extern "C" int scqr3_apply_pass(int pass, const double* G, int64_t m_global, const double* X, int64_t m_local,
+                                int n, int64_t ldx, const scqr3_B* B, double* Q, int64_t ldq, double* R,
+                                double* G_next, void* workspace, size_t workspace_bytes, const scqr3_opts* opts,
+                                scqr3_info* info, void* stream) {
+  int a = check_shard(m_local, n, B, opts);
+  if (a != SCQR3_OK) return remap(a, 5, 6, 8, 15);
+  const int max_passes = (opts && opts->max_passes) ? opts->max_passes : 6;
+  if (pass < 0 || pass >= max_passes) return -1;
+  if (!G) return -2;
+  if (m_global < n || m_global < m_local) return -3;
+  if (!X) return -4;
+  if (ldx < n) return -7;
+  if (!Q) return -9;
+  if (ldq < n) return -10;
+  if (!R) return -11;
+  if (!G_next && pass + 1 < max_passes) return -12;
+  if (!workspace) return -13;
+  if (!info) return -16;
+  const size_t xbytes = sizeof(double) * (size_t)((m_local - 1) * ldx + n);
+  const size_t qbytes = sizeof(double) * (size_t)((m_local - 1) * ldq + n);
+  if ((const void*)Q != (const void*)X && overlaps(X, xbytes, Q, qbytes)) return -9;
+  if ((const void*)Q == (const void*)X && ldq != ldx) return -10;
+  Call c;
+  a = setup_call(m_local, n, B, opts, workspace, workspace_bytes, 0, R, nullptr, info, (cudaStream_t)stream, &c);
+  if (a != SCQR3_OK) return a;
+  // the shift, Alg. 2's tolerance and the pass decisions are those of the
+  // whole X: the Cholesky kernel sees the global m
+  Params Pg = c.P;
+  Pg.m = m_global;
+  set_options(&Pg, opts);
+  tick(c.s, SCQR3_KERNEL_CHOL, pass);
+  if (c.P.np == 256)
+    launch_chol256(c.s, Pg, pass, G, c.rstack, c.racc, c.R, nullptr, c.st, c.info, c.S, c.Ra);
+  else
+    launch_chol(c.P.np, c.s, Pg, pass, G, c.rstack, c.racc, c.R, nullptr, c.st, c.info);
+  solve_rows(c, pass, pass == 0 ? X : Q, pass == 0 ? ldx : ldq, Q, ldq, 0, m_local);
+  if (pass + 1 < max_passes) after_pass_gram(c, pass, Q, ldq, G_next);
+  if (c.tc) launch_status(c.s, c.st, c.info);
+  tick(c.s, -1, -1);
   if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
   return SCQR3_OK;
 }

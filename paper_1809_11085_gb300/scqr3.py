@@ -86,7 +86,8 @@ class _Info(ctypes.Structure):
                 ("shifted", ctypes.c_int * MAX_PASSES),
                 ("unshifted_fail", ctypes.c_int * MAX_PASSES),
                 ("s", ctypes.c_double * MAX_PASSES),
-                ("norm2", ctypes.c_double * MAX_PASSES)]
+                ("norm2", ctypes.c_double * MAX_PASSES),
+                ("more", ctypes.c_int)]
 
 
 INFO_BYTES = ctypes.sizeof(_Info)
@@ -110,13 +111,14 @@ class Info:
     unshifted_fail: list = field(default_factory=list)
     s: list = field(default_factory=list)
     norm2: list = field(default_factory=list)
+    more: int = 0
 
     @staticmethod
     def from_bytes(buf: bytes) -> "Info":
         c = _Info.from_buffer_copy(buf)
         k = max(0, min(c.passes, MAX_PASSES))
         return Info(c.status, c.passes, list(c.shifted[:k]), list(c.unshifted_fail[:k]),
-                    list(c.s[:k]), list(c.norm2[:k]))
+                    list(c.s[:k]), list(c.norm2[:k]), c.more)
 
 
 _lib = None
@@ -146,6 +148,14 @@ def lib():
         L.scqr3_backward_workspace_bytes.restype = i32
         L.scqr3_backward.argtypes = [p, i64, i32, i64, p, i32, p, i64, p, p, i64, p, sz, p]
         L.scqr3_backward.restype = i32
+        L.scqr3_shard_sizes.argtypes = [i64, i32, ctypes.POINTER(_B), ctypes.POINTER(_Opts), ctypes.POINTER(sz),
+                                        ctypes.POINTER(sz)]
+        L.scqr3_shard_sizes.restype = i32
+        L.scqr3_gram_partial.argtypes = [p, i64, i32, i64, ctypes.POINTER(_B), p, p, sz, ctypes.POINTER(_Opts), p, p]
+        L.scqr3_gram_partial.restype = i32
+        L.scqr3_apply_pass.argtypes = [i32, p, i64, p, i64, i32, i64, ctypes.POINTER(_B), p, i64, p, p, p, sz,
+                                       ctypes.POINTER(_Opts), p, p]
+        L.scqr3_apply_pass.restype = i32
         L.scqr3_debug_set.argtypes = [i32, ctypes.c_longlong]
         L.scqr3_debug_set.restype = i32
         L.scqr3_timing_begin.argtypes = [i32]
@@ -438,3 +448,96 @@ def qr(X, max_passes: int = 0):
     if _SCQR3 is None:
         _SCQR3 = _autograd_function()
     return _SCQR3.apply(X, max_passes)
+
+
+# ----------------------------------------------------------------------------- row-partitioned form
+
+class ShardWorkspace:
+    """One rank's device state for the row-partitioned calls: the workspace,
+    the Gram vectors G (summed over ranks) and G' (this rank's next share), and
+    the per-call record."""
+
+    def __init__(self, m_local, n, B=None, normb=0.0, precision=PREC_FP64, max_passes=0, device=None):
+        import torch
+
+        _, bp = _b_struct(B, normb)
+        _, op = _opts(max_passes, 0.0, precision)
+        wb, gw = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        r = lib().scqr3_shard_sizes(int(m_local), int(n), bp, op, ctypes.byref(wb), ctypes.byref(gw))
+        if r != OK:
+            raise ScqrError(r, "scqr3_shard_sizes")
+        dev = device or "cuda"
+        self.bytes = wb.value
+        self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=dev)
+        self.ptr = (self.buf.data_ptr() + 255) & ~255
+        self.G = torch.zeros(gw.value, dtype=torch.float64, device=dev)
+        self.G_next = torch.zeros(gw.value, dtype=torch.float64, device=dev)
+        self.info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=dev)
+
+
+def gram_partial(X, ws: ShardWorkspace, B=None, *, normb=0.0, precision=PREC_FP64, max_passes=0,
+                 shift_scale=0.0, algorithm=ALG_SCQR3, tol=0.0, stream=None):
+    """scqr3_gram_partial: start a row-partitioned factorization on this rank
+    and write its rows' share of X^T X (or X^T B X) into ws.G."""
+    import torch
+
+    _check_mat(X, "X")
+    m, n = X.shape
+    b, bp = _b_struct(B, normb)
+    o, op = _opts(max_passes, 0.0, precision, shift_scale, algorithm, tol)
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device).cuda_stream
+    r = lib().scqr3_gram_partial(X.data_ptr(), m, n, X.stride(0), bp, ws.G.data_ptr(), ws.ptr, ws.bytes, op,
+                                 ws.info.data_ptr(), ctypes.c_void_p(stream))
+    if r != OK:
+        raise ScqrError(r, "scqr3_gram_partial")
+
+
+def apply_pass(k, m_global, X, Q, R, ws: ShardWorkspace, B=None, *, normb=0.0, precision=PREC_FP64,
+               max_passes=0, shift_scale=0.0, algorithm=ALG_SCQR3, tol=0.0, stream=None):
+    """scqr3_apply_pass: pass k on this rank from the summed ws.G; writes
+    ws.G_next (this rank's share of the next Gram) when another pass follows."""
+    import torch
+
+    _check_mat(X, "X")
+    _check_mat(Q, "Q")
+    m, n = X.shape
+    b, bp = _b_struct(B, normb)
+    o, op = _opts(max_passes, 0.0, precision, shift_scale, algorithm, tol)
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device).cuda_stream
+    r = lib().scqr3_apply_pass(int(k), ws.G.data_ptr(), int(m_global), X.data_ptr(), m, n, X.stride(0), bp,
+                               Q.data_ptr(), Q.stride(0), R.data_ptr(), ws.G_next.data_ptr(), ws.ptr, ws.bytes,
+                               op, ws.info.data_ptr(), ctypes.c_void_p(stream))
+    if r != OK:
+        raise ScqrError(r, "scqr3_apply_pass")
+
+
+def factor_sharded(X, m_global, allreduce, B=None, *, normb=0.0, Q=None, R=None, precision=PREC_FP64,
+                   max_passes=0, shift_scale=0.0, algorithm=ALG_SCQR3, tol=0.0, workspace=None):
+    """This rank's part of a row-partitioned factorization of an m_global x n
+    X whose rows [r0, r0 + m_local) are X here. allreduce(t) must replace the
+    float64 CUDA tensor t by its sum over the ranks (e.g.
+    torch.distributed.all_reduce with NCCL; with gloo, through a CPU copy).
+    Every rank takes the same pass decisions from the same sums, so all of
+    them make the same number of allreduce calls. Returns (Q_local, R, info)."""
+    import torch
+
+    m, n = X.shape
+    if Q is None:
+        Q = torch.empty_like(X)
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=X.device)
+    ws = workspace or ShardWorkspace(m, n, B, normb, precision, max_passes, device=X.device)
+    kw = dict(normb=normb, precision=precision, max_passes=max_passes, shift_scale=shift_scale,
+              algorithm=algorithm, tol=tol)
+    gram_partial(X, ws, B, **kw)
+    allreduce(ws.G)
+    for k in range(max_passes or 6):
+        apply_pass(k, m_global, X, Q, R, ws, B, **kw)
+        info = Info.from_bytes(ws.info.cpu().numpy().tobytes())
+        if not info.more:
+            break
+        allreduce(ws.G_next)
+        ws.G, ws.G_next = ws.G_next, ws.G
+    return Q, R, info

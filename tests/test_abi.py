@@ -42,8 +42,11 @@ def test_library_exports_every_declared_symbol(lib):
 def test_info_struct_layout_matches_header():
     from paper_1809_11085_gb300 import scqr3
 
-    # 2 ints + 2 x MAX_PASSES ints + 2 x MAX_PASSES doubles
-    assert scqr3.INFO_BYTES == 8 + 8 * scqr3.MAX_PASSES + 16 * scqr3.MAX_PASSES
+    # 2 ints + 2 x MAX_PASSES ints + 2 x MAX_PASSES doubles + the `more` int,
+    # padded to the doubles' 8-byte alignment
+    raw = 8 + 8 * scqr3.MAX_PASSES + 16 * scqr3.MAX_PASSES + 4
+    assert scqr3.INFO_BYTES == (raw + 7) // 8 * 8
+    assert scqr3._Info.more.offset == 8 + 8 * scqr3.MAX_PASSES + 16 * scqr3.MAX_PASSES
 
 
 def test_argument_errors_are_reported_on_the_host(lib):
@@ -93,3 +96,30 @@ def test_argument_errors_are_reported_on_the_host(lib):
     # null pointers in scqr3_factor are rejected before any CUDA call
     assert lib.scqr3_factor(None, 10, 2, 2, None, None, 2, None, None, None, 0, None, None,
                             None) == -1
+
+
+def test_shard_argument_errors_are_reported_on_the_host(lib):
+    """The row-partitioned calls number their argument codes by their own
+    prototypes and reject the forms they do not take before any CUDA call."""
+    import ctypes
+
+    from paper_1809_11085_gb300 import scqr3
+
+    wb, gw = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    o = scqr3._Opts(0, scqr3.PREC_MIXED, 0.0, 0.0, 3, 0.0)
+    assert lib.scqr3_shard_sizes(1000, 16, None, ctypes.byref(o), ctypes.byref(wb), ctypes.byref(gw)) == \
+        scqr3.E_UNSUPPORTED
+    assert lib.scqr3_shard_sizes(1000, 0, None, None, ctypes.byref(wb), ctypes.byref(gw)) == -2
+    assert lib.scqr3_shard_sizes(0, 16, None, None, ctypes.byref(wb), ctypes.byref(gw)) == -1
+    assert lib.scqr3_shard_sizes(1000, 16, None, None, None, ctypes.byref(gw)) == -5
+    # a block shorter than n is allowed (m_local >= 1); a B without ||B||_2 is not
+    b = scqr3._B(8, ctypes.c_void_p(8), 0.0)
+    assert lib.scqr3_gram_partial(None, 1000, 16, 16, ctypes.byref(b), None, None, 0, None, None, None) == -5
+    csr = scqr3._B(0, None, 1.0, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), 5000)
+    assert lib.scqr3_gram_partial(None, 1000, 16, 16, ctypes.byref(csr), None, None, 0, None, None, None) == \
+        scqr3.E_UNSUPPORTED
+    assert lib.scqr3_gram_partial(None, 1000, 16, 16, None, None, None, 0, None, None, None) == -1
+    assert lib.scqr3_apply_pass(-1, None, 1000, None, 1000, 16, 16, None, None, 16, None, None, None, 0, None,
+                                None, None) == -1
+    assert lib.scqr3_apply_pass(0, None, 1000, None, 1000, 16, 16, None, None, 16, None, None, None, 0, None,
+                                None, None) == -2
