@@ -50,12 +50,12 @@ PROFILED_KERNEL_SHA = "b447e14d15d0797f"
 PROFILED_BYTES_PER_ROW = 992.3
 PROFILED_SOLVE_BYTES_PER_ROW = 968.7
 PROFILED_BLOCK_BYTES_PER_ROW = 210.3  # pass_kernel<16> on the first 16-column block of a 64-column X
-# ncu DRAM bytes per row of the tensor-core kernels at 1048576 x 64 (profiles/tc_solve_kernels_* and
-# profiles/tc_gram_kernel_*; for the substitution, the mean over its two update launch shapes), valid for
-# the sources they were taken on.
+# ncu DRAM bytes per row of the tensor-core kernels at 1048576 x 64 (profiles/tc_fused_solve_kernel_*,
+# profiles/tc_gram_kernel_* and profiles/tc_solve_kernels_*; for the separate-launch substitution, the mean
+# over its two update launch shapes), valid for the sources they were taken on.
 PROFILED_TC = {"tc_solve": ("25eb56420f284aac", ("tc_common.cuh", "tc_solve.cu"), 478.7),
-               "tc_gram": ("36e48f579de11899", ("tc_common.cuh", "tc_gram.cu"), 516.4),
-               "tc_fused": (None, ("tc_common.cuh", "tc_fused.cu"), None)}
+               "tc_gram": ("df6dd0a802f892f6", ("tc_common.cuh", "tc_gram.cu"), 526.6),
+               "tc_fused": ("5fcf8610f1eec0dc", ("tc_common.cuh", "tc_fused.cu"), 982.2)}
 
 
 def profiled_tc_traffic(kind, m, n):
