@@ -49,7 +49,8 @@ extern "C" {
                                      CholeskyQR passes followed the last
                                      shifted one; Q, R are still X = QR   */
 #define SCQR3_E_CUDA (-103)       /* a CUDA launch failed                  */
-#define SCQR3_E_TIMEOUT (-102) /* a wait inside a kernel passed its iteration limit */
+#define SCQR3_E_TIMEOUT (-102) /* a wait inside a tensor-core kernel ran out
+                                     of time (see scqr3_debug_set)         */
 #define SCQR3_E_WORKSPACE (-104)  /* workspace too small or misaligned     */
 #define SCQR3_E_B_NOT_SPD (-105)  /* a diagonal block of B is not SPD      */
 #define SCQR3_E_UNSUPPORTED (-106)/* size not supported by this build      */
@@ -70,20 +71,26 @@ extern "C" {
  * Inputs must lie within the float exponent range. Not in the paper (which
  * uses FP64 throughout, Sec. 6); expected orthogonality ~1e-14. */
 #define SCQR3_PREC_MIXED 1
-/* FP64 substitution; the Gram matrices on the BF16 tensor cores (tcgen05)
- * through an exact fixed-point split: each column is scaled by a power of two
- * above its largest entry and cut into eight 7-bit digits, every digit
- * product is exact, sums of 256 rows are exact in the FP32 accumulator, and
- * the digit-pair sums are combined in int64. The Gram error is below
- * m 2^-53 sigma_j sigma_k (about 4.3 m u ||q_j|| ||q_k||), within the
- * norm-wise bound that the shift of Eq. (finds2) covers, so results match the
- * FP64 form to rounding. The
- * substitution runs in 32-column blocks of R: the triangular diagonal blocks
- * in FP64, the products with the off-diagonal blocks (x_K -= y_J R_JK) on the
- * tensor cores by the same split. Not in the paper. n <= 128, m <= 2^31, and
- * B either NULL or block-diagonal with blocks of 1, 2, 4 or 8 rows (the Gram
- * matrix of Z = L^T Q, L_j^T applied to each 8-row unit before the split;
- * else SCQR3_E_UNSUPPORTED). */
+/* FP64-accurate form with the bulk of the arithmetic on the BF16 tensor cores
+ * (tcgen05). Not in the paper. Every value a tensor core multiplies is
+ * rounded to 2^-56 of a power-of-two scale (per Gram column; per row of Y and
+ * per column of R_JK in the substitution) and cut into eight signed digits in
+ * [-64, 64]: each digit is exactly a BF16 number, every digit product and
+ * every tensor-core sum (at most 2^24 in magnitude) is exact in FP32, and the
+ * digit-pair sums are combined in int64; the error is zero-mean.
+ *  - Gram matrices: below about 8.5 m u ||q_j|| ||q_k|| per entry, within the
+ *    norm-wise bound that the shift of Eq. (finds2) covers; the diagonal adds
+ *    the digit squares the tiles leave out, so it is not biased low.
+ *  - Substitution Q := X R^{-1}: the triangular diagonal blocks of R (16
+ *    columns for n <= 64, 32 above) in FP64, the products with the
+ *    off-diagonal blocks on the tensor cores, a perturbation of R of norm
+ *    O(u ||R||) per row (the form of the row-wise backward error, Eq.
+ *    backward2). For 16 < n <= 64 a pass reads each row once and writes it
+ *    once (one sweep, see scqr3_debug_set).
+ * Results match the FP64 form to rounding. n <= 128, m <= 2^31, and B either
+ * NULL or block-diagonal with blocks of 1, 2, 4 or 8 rows (the Gram matrix of
+ * Z = L^T Q, L_j^T applied to each 8-row unit before the split); other
+ * shapes return SCQR3_E_UNSUPPORTED. */
 #define SCQR3_PREC_TC 2
 /* The mixed form's substitution (FP32 pairs) with the Gram matrices of
  * SCQR3_PREC_TC, read directly from the float-pair iterates. n <= 128,
@@ -97,8 +104,9 @@ extern "C" {
  * library uses its rows as given and does not check symmetry), with int64
  * row offsets and int32 column indices, m < 2^31; n <= 128, FP64 only. */
 typedef struct {
-  int bs;               /* block size, one of 1, 2, 4, 8, 16, m % bs == 0;
-                           0 selects the CSR fields below                   */
+  int bs;               /* block size, m % bs == 0: 1, 2, 4, 8 or 16 (FP64;
+                           the tensor-core form takes 1, 2, 4 or 8); 0 selects
+                           the CSR fields below (FP64 only)                 */
   const double *blocks; /* device: (m/bs) blocks of bs*bs row-major FP64    */
   double norm2;         /* ||B||_2 if > 0; otherwise an upper bound is
                            computed on the device: max_j ||B_j||_F (blocks),
@@ -112,10 +120,16 @@ typedef struct {
 typedef struct {
   int max_passes;  /* total CholeskyQR passes allowed, 3..SCQR3_MAX_PASSES;
                       0 selects 6                                          */
-  int precision;   /* SCQR3_PREC_FP64 or SCQR3_PREC_MIXED                  */
+  int precision;   /* SCQR3_PREC_FP64 (0), SCQR3_PREC_MIXED,
+                      SCQR3_PREC_TC or SCQR3_PREC_MIXED_TC (see above)    */
   double norm_x2;  /* > 0: value of ||X||_2^2 used in the pass-1 shift of
-                      Eq. (finds2)/(finds2B); otherwise ||X||_F^2 (Sec. 4.1
-                      allows this more conservative substitute)             */
+                      Eq. (finds2)/(finds2B); 0: ||Q||_F^2 of each shifted
+                      pass's iterate (Sec. 4.1 allows this more conservative
+                      substitute); SCQR3_NORM_X2_TWO_EST (B = NULL only):
+                      ||Q||_2^2 of each shifted pass's iterate estimated as
+                      lambda_max of its Gram matrix by the power method (the
+                      normest of Sec. 4.1; iterated until the estimate changes
+                      by at most 1e-12 of itself, at most 200 steps)         */
   double shift_scale; /* > 0: a shifted pass first tries the smaller shift
                       s = shift_scale * u * ||Q||^2 (times ||B|| for oblique
                       B) that the remark of Sec. 6.1 and Sec. 8 suggest
@@ -133,6 +147,8 @@ typedef struct {
                       Thm. (maincholqr3) (the printed sqrt(n) u is below the
                       rounding error of a computed Gram matrix)             */
 } scqr3_opts;
+
+#define SCQR3_NORM_X2_TWO_EST (-1.0)
 
 /* scqr3_opts.algorithm. Alg. 3 shifts pass 1 unconditionally and ends after
  * two consecutive unshifted passes. Alg. 2 tries the plain Cholesky in every
@@ -297,7 +313,7 @@ typedef struct {
   double *Rpass;      /* device, SCQR3_MAX_PASSES * n * n, or NULL           */
   scqr3_info *info;   /* device record of this matrix's call                 */
   int64_t m;
-  int n;              /* 1 .. SCQR3_MAX_N                                    */
+  int n;              /* 1 .. 128 (else SCQR3_E_UNSUPPORTED)                  */
   int64_t ldx, ldq;
 } scqr3_batch_item;
 
@@ -336,7 +352,8 @@ void scqr3_batch_plan_destroy(scqr3_batch_plan *plan);
  *  passes  scqr3_info.passes of that call (1..SCQR3_MAX_PASSES).
  *  dQ      m x n cotangent of Q (lddq >= n); dR: n x n cotangent of R or NULL.
  *  dX      m x n output (lddx >= n); may alias dQ exactly.
- * Device pointers; asynchronous on `stream`; n <= SCQR3_MAX_N. */
+ * Device pointers; asynchronous on `stream`; n <= 128 (else
+ * SCQR3_E_UNSUPPORTED). */
 int scqr3_backward_workspace_bytes(int64_t m, int n, size_t *bytes);
 int scqr3_backward(const double *Q, int64_t m, int n, int64_t ldq,
                    const double *Rpass, int passes, const double *dQ,

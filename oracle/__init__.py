@@ -59,6 +59,8 @@ def lib():
         L.orc_gram_oblique.argtypes = [i64, i32, p, i64, i32, p, p, p]
         L.orc_shift.argtypes = [i64, i32, f64]
         L.orc_shift.restype = f64
+        L.orc_normest2.argtypes = [i32, p]
+        L.orc_normest2.restype = f64
         L.orc_shift_oblique.argtypes = [i64, i32, f64, f64]
         L.orc_shift_oblique.restype = f64
         L.orc_chol.argtypes = [i32, p, f64, p]
@@ -116,6 +118,16 @@ def gram_oblique(X: np.ndarray, Bblk: np.ndarray):
 def shift(m: int, n: int, normx2: float) -> float:
     """s of Eq. (finds2)."""
     return lib().orc_shift(m, n, normx2)
+
+
+def normest2(A: np.ndarray) -> float:
+    """lambda_max of a symmetric positive semidefinite A by the power method
+    (the ||Q||_2^2 estimate of the shift, Sec. 4.1)."""
+    A = _c(A)
+    return lib().orc_normest2(A.shape[0], _ptr(A))
+
+
+TWO_NORM_EST = -1.0  # normx2 value selecting the power-method estimate of ||Q||_2^2 in every shifted pass
 
 
 def shift_oblique(m: int, n: int, normx2: float, normb: float) -> float:

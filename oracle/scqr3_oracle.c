@@ -69,6 +69,36 @@ double orc_shift(int64_t m, int n, double normx2) {
   return 11.0 * (mn + nn1) * ORC_U * normx2;
 }
 
+double orc_normest2(int n, const double *A) {
+  /* Power method: v := A v / ||A v|| from v = (1, ..., 1) / sqrt(n); the
+   * estimate is the Rayleigh quotient v^T A v (v of unit length), stopped once
+   * it changes by at most 1e-12 of itself, or after 200 steps. */
+  double *v = (double *)malloc(sizeof(double) * (size_t)n);
+  double *w = (double *)malloc(sizeof(double) * (size_t)n);
+  for (int j = 0; j < n; ++j) v[j] = 1.0 / sqrt((double)n);
+  double lam = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    for (int j = 0; j < n; ++j) {
+      double t = 0.0;
+      for (int k = 0; k < n; ++k) t = t + A[j * n + k] * v[k];
+      w[j] = t;
+    }
+    double q = 0.0, ww = 0.0;
+    for (int j = 0; j < n; ++j) {
+      q = q + v[j] * w[j];
+      ww = ww + w[j] * w[j];
+    }
+    const double nw = sqrt(ww);
+    const int done = it > 0 && fabs(q - lam) <= 1e-12 * q;
+    lam = q;
+    if (done || !(nw > 0.0)) break;
+    for (int j = 0; j < n; ++j) v[j] = w[j] / nw;
+  }
+  free(v);
+  free(w);
+  return lam;
+}
+
 double orc_shift_oblique(int64_t m, int n, double normx2, double normb) {
   /* Eq. (finds2B). */
   const double dm = (double)m;
@@ -229,6 +259,7 @@ static int orc_drive(int64_t m, int n, const double *X, int64_t ldx, const orc_i
    * 6 {mn + n(n+1)} u. */
   if (!(tol > 0.0)) tol = 6.0 * ((double)m * (double)n + (double)n * (double)(n + 1)) * ORC_U;
   const int oblique = B->kind != 0;
+  if (normx2 < 0.0 && oblique) return ORC_E_ARG;  /* the 2-norm estimate: B = I only */
   if (B->kind == 1 && !(normb > 0.0)) normb = orc_normb_bound(m, B->bs, B->Bblk);
   if (B->kind == 2 && !(normb > 0.0)) normb = orc_normb_csr(m, B->row_ptr, B->vals);
 
@@ -263,6 +294,8 @@ static int orc_drive(int64_t m, int n, const double *X, int64_t ldx, const orc_i
       break;
     }
     if (p == 0 && normx2 > 0.0) nrm2 = normx2;
+    /* normx2 < 0: ||Q||_2^2 estimated by the power method (Sec. 4.1: normest) */
+    if (normx2 < 0.0) nrm2 = orc_normest2(n, A);
 
     /* Alg. 2's loop test: stop when the current iterate is orthonormal enough
      * (its Gram matrix A is already at hand). */

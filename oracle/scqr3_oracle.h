@@ -54,6 +54,11 @@ void orc_gram_oblique(int64_t m, int n, const double *X, int64_t ldx, int bs,
 /* Shift s = 11 {mn + n(n+1)} u ||X||_2^2, Eq. (finds2); u = 2^-53. */
 double orc_shift(int64_t m, int n, double normx2);
 
+/* lambda_max(A) of an n x n symmetric positive semidefinite A (row-major) by
+ * the power method: the estimate of ||Q||_2^2 = lambda_max(Q^T Q) that Sec. 4.1
+ * allows in the shift (normest). */
+double orc_normest2(int n, const double *A);
+
 /* Oblique shift s = 11 {2 m sqrt(mn) + n(n+1)} u ||X||_2^2 ||B||_2,
  * Eq. (finds2B). */
 double orc_shift_oblique(int64_t m, int n, double normx2, double normb);
@@ -90,7 +95,9 @@ double orc_normb_csr(int64_t m, const int64_t *row_ptr, const double *vals);
 /* Shifted CholeskyQR3 (Alg. 3; oblique: Alg. 5) with the breakdown rule of
  * Alg. 2: pass 1 is always shifted; a later pass whose plain Cholesky
  * breaks down is redone with the shift; the factorization ends after two
- * consecutive unshifted passes. bs == 0 means B = I. normx2 > 0 replaces
+ * consecutive unshifted passes. bs == 0 means B = I. normx2 < 0 (B = I only)
+ * estimates ||Q||_2^2 of every shifted pass by orc_normest2 of its Gram
+ * matrix. normx2 > 0 replaces
  * ||X||_2^2 in the pass-1 shift (else ||X||_F^2 is used, see Sec. 4.1);
  * normb > 0 is ||B||_2 (else orc_normb_bound). Returns ORC_OK, a positive
  * breakdown column, or a negative ORC_E_* code. Q may alias X. */

@@ -332,6 +332,51 @@ __device__ double dev_from_identity2(const double* S, int n, double* red) {
   return t;
 }
 
+// Sum of one value per thread over the block, in a fixed order, valid in
+// every thread.
+__device__ __forceinline__ double block_sum(double x, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  return t;
+}
+
+// lambda_max of the packed symmetric positive semidefinite S (columns < n) by
+// the power method: the estimate of ||Q||_2^2 = lambda_max(Q^T Q) that
+// Sec. 4.1 allows in the shift (normest). v := S v / ||S v|| from
+// v = (1, ..., 1) / sqrt(n); the estimate is the Rayleigh quotient, stopped
+// once it changes by at most 1e-12 of itself, or after 200 steps. v and w hold
+// n doubles each; the result is valid in every thread.
+template <int NP>
+__device__ double normest2(const double* S, int n, double* v, double* w, double* red) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) v[j] = 1.0 / sqrt((double)n);
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    double q = 0.0, ww = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double t = 0.0;
+      for (int k = 0; k < n; ++k) t = fma(S[k <= j ? pk_idx(NP, k, j) : pk_idx(NP, j, k)], v[k], t);
+      w[j] = t;
+      q = fma(v[j], t, q);
+      ww = fma(t, t, ww);
+    }
+    q = block_sum(q, red);
+    ww = block_sum(ww, red);
+    const double nw = sqrt(ww);
+    const bool done = it > 0 && fabs(q - lam) <= 1e-12 * q;
+    lam = q;
+    if (done || !(nw > 0.0)) break;  // the same in every thread
+    for (int j = threadIdx.x; j < n; j += blockDim.x) v[j] = w[j] / nw;
+    __syncthreads();
+  }
+  return lam;
+}
+
 // Cholesky of the packed matrix S in place (upper factor), columns < n.
 // Returns 0 or the 1-based breakdown column (radicand not positive/finite).
 template <int NP>
@@ -404,6 +449,12 @@ __device__ __forceinline__ void chol_body(const Params& P, int pass, const doubl
     ufail_sh = 0;
   }
   __syncthreads();
+  if (P.norm_x2 < 0.0) {  // SCQR3_NORM_X2_TWO_EST: ||Q||_2^2 of this pass's iterate, estimated
+    __shared__ double pw[2][256];
+    const double e = normest2<NP>(S, n, pw[0], pw[1], red_sh);
+    if (tid == 0) nrm_sh = e;
+    __syncthreads();
+  }
   if (!isfinite(nrm_sh)) {
     if (tid == 0) {
       st->status = SCQR3_E_NONFINITE;

@@ -9,7 +9,10 @@
 #include <cstdint>
 #include <cstring>
 #include <atomic>
+#include <cstdio>
 #include <mutex>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "scqr3_internal.cuh"
 
@@ -195,6 +198,7 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, bool 
   // (they divide the kernel's 8-row units), FP64 substitution only
   if (tcp && B && (B->bs == 0 || B->bs > 8 || opts->precision == SCQR3_PREC_MIXED_TC)) return SCQR3_E_UNSUPPORTED;
   if (opts && opts->precision == SCQR3_PREC_MIXED && B) return -5;  // mixed form: B = I only
+  if (opts && opts->norm_x2 < 0.0 && B) return -12;  // the 2-norm estimate: B = I only
   if (opts && opts->algorithm != 0 && opts->algorithm != SCQR3_ALG_SCQR3 &&
       opts->algorithm != SCQR3_ALG_ADAPTIVE)
     return -12;
@@ -353,6 +357,20 @@ void tick(cudaStream_t s, int kind, int pass) {
   g_timer.pass[g_timer.used] = pass;
   ++g_timer.used;
 }
+
+// Tracing: an NVTX range around each entry point and each pass's launches
+// (host side, header-only NVTX; a no-op unless a profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  NvtxRange(const char* fmt, long long a, long long b) {
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), fmt, a, b);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
   const char* pa = (const char*)a;
@@ -699,17 +717,22 @@ extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, cons
   if (a != SCQR3_OK) return a;
   a = check_factor_pointers(X, m, n, ldx, Q, ldq, R, workspace, info);
   if (a != SCQR3_OK) return a;
+  NvtxRange range("scqr3_factor %lld x %lld", (long long)m, (long long)n);
   Call c;
   a = begin_call(m, n, B, opts, workspace, workspace_bytes, 0, R, Rpass, info, (cudaStream_t)stream, &c);
   if (a != SCQR3_OK) return a;
 
   // Pass 1 of Alg. 3: A = X^T X (or X^T B X), then the fixed sequence of
   // passes whose launches the device skips once they are not needed.
-  const int slots = first_gram(c, X, ldx, 0, m, 0);
-  tick(c.s, SCQR3_KERNEL_REDUCE, 0);
-  launch_reduce(c.s, c.partials, slots, c.L.part_stride, c.gram, c.st, -1);
-  launch_any_chol(c, 0);
+  {
+    NvtxRange g("scqr3 first Gram");
+    const int slots = first_gram(c, X, ldx, 0, m, 0);
+    tick(c.s, SCQR3_KERNEL_REDUCE, 0);
+    launch_reduce(c.s, c.partials, slots, c.L.part_stride, c.gram, c.st, -1);
+    launch_any_chol(c, 0);
+  }
   for (int k = 0; k < c.P.max_passes; ++k) {
+    NvtxRange pr("scqr3 pass %lld of %lld", (long long)k, (long long)c.P.max_passes);
     solve_rows(c, k, k == 0 ? X : Q, k == 0 ? ldx : ldq, Q, ldq, 0, m);
     if (k + 1 < c.P.max_passes) after_pass(c, k, Q, ldq);
   }
@@ -770,6 +793,7 @@ extern "C" int scqr3_factor_host(const double* X, int64_t m, int n, int64_t ldx,
   a = host_res(&h);
   if (a != SCQR3_OK) return a;
   std::lock_guard<std::mutex> lk(h->mu);
+  NvtxRange range("scqr3_factor_host %lld x %lld", (long long)m, (long long)n);
   cudaStream_t s = (cudaStream_t)stream;
   Call c;
   {
@@ -918,6 +942,7 @@ extern "C" int scqr3_gram_partial(const double* X, int64_t m_local, int n, int64
   if (!G) return -6;
   if (!workspace) return -7;
   if (!info) return -10;
+  NvtxRange range("scqr3_gram_partial %lld x %lld", (long long)m_local, (long long)n);
   Call c;
   a = begin_call(m_local, n, B, opts, workspace, workspace_bytes, 0, nullptr, nullptr, info, (cudaStream_t)stream,
                  &c);
@@ -952,6 +977,7 @@ extern "C" int scqr3_apply_pass(int pass, const double* G, int64_t m_global, con
   const size_t qbytes = sizeof(double) * (size_t)((m_local - 1) * ldq + n);
   if ((const void*)Q != (const void*)X && overlaps(X, xbytes, Q, qbytes)) return -9;
   if ((const void*)Q == (const void*)X && ldq != ldx) return -10;
+  NvtxRange range("scqr3_apply_pass %lld, %lld rows", (long long)pass, (long long)m_local);
   Call c;
   a = setup_call(m_local, n, B, opts, workspace, workspace_bytes, 0, R, nullptr, info, (cudaStream_t)stream, &c);
   if (a != SCQR3_OK) return a;

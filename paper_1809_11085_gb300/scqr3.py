@@ -211,6 +211,7 @@ PREC_TC = 2  # FP64-accurate: the Gram matrices and the substitution's off-diago
              # BF16 tensor cores (exact digit split), FP64 diagonal blocks; n <= 128, B = I or
              # block-diagonal with blocks of 1, 2, 4 or 8 rows
 PREC_MIXED_TC = 3  # the mixed form's substitution with the tensor-core Gram matrices
+NORM_X2_TWO_EST = -1.0  # norm_x2 value: ||Q||_2^2 of each shifted pass estimated by the power method
 ALG_ADAPTIVE = 2  # Alg. 2: shift only on breakdown, stop on the orthogonality test
 ALG_SCQR3 = 3     # Alg. 3: shifted pass, then CholeskyQR2
 

@@ -221,3 +221,37 @@ def test_beyond_one_over_u(m, n, algorithm):
     assert np.linalg.norm(Qg.T @ Qg - np.eye(n)) <= 6 * (m * n + n * (n + 1)) * U
     assert np.linalg.norm(Qg @ Rg - Xh) / np.linalg.norm(Xh, 2) <= 15 * n * n * U
     assert (np.diag(Rg) > 0).all()
+
+
+@pytest.mark.parametrize("precision", [scqr3.PREC_FP64, scqr3.PREC_TC])
+@pytest.mark.parametrize("m,n,kappa", [(20000, 32, 1e12), (30011, 64, 1e15), (5000, 100, 1e8)])
+def test_two_norm_estimate_shift(precision, m, n, kappa):
+    """norm_x2 = SCQR3_NORM_X2_TWO_EST: every shifted pass estimates ||Q||_2^2
+    as lambda_max of its Gram matrix by the power method (Sec. 4.1, normest),
+    on the device as in the oracle: the estimates and shifts agree to 1e-10
+    (the Gram matrices differ only by rounding), the first is ||X||_2^2 = 1 of
+    the construction, and the results meet the FP64 tolerances."""
+    Xh = testmat(m, n, kappa, seed=7700 + n)
+    Q, R, info = scqr3.factor(torch.from_numpy(Xh).cuda(), norm_x2=scqr3.NORM_X2_TWO_EST, precision=precision)
+    torch.cuda.synchronize()
+    Qo, Ro, st, tr = oracle.scqr3(Xh, normx2=oracle.TWO_NORM_EST)
+    assert st == 0 and info.status == 0, info
+    assert abs(info.norm2[0] - 1.0) <= 1e-10 and abs(tr["norm2"][0] - 1.0) <= 1e-10
+    for p in range(min(info.passes, tr["passes"])):
+        if info.shifted[p] and tr["shifted"][p]:
+            assert abs(info.s[p] - tr["s"][p]) <= 1e-9 * tr["s"][p], (p, info.s[p], tr["s"][p])
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    assert np.linalg.norm(Q.T @ Q - np.eye(n), 2) <= 1e-13
+    assert np.linalg.norm(Xh - Q @ R) / np.linalg.norm(Xh) <= 1e-13
+    dR = np.linalg.norm(R - Ro) / np.linalg.norm(Ro)
+    assert dR <= (1e-12 if kappa <= 1e8 else 100 * n * kappa * U), dR
+
+
+def test_two_norm_estimate_rejected_with_b():
+    from paper_1809_11085_gb300.testmat import block_diag_spd
+
+    X = torch.zeros((800, 16), dtype=torch.float64, device="cuda")
+    B = torch.from_numpy(block_diag_spd(800, 8, seed=1)).cuda()
+    with pytest.raises(scqr3.ScqrError) as e:
+        scqr3.factor(X, B, norm_x2=scqr3.NORM_X2_TWO_EST)
+    assert e.value.code == -12

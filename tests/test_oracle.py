@@ -596,3 +596,35 @@ def test_csr_random_pattern_bounds():
     assert np.linalg.norm(Q.T @ B @ Q - np.eye(n)) <= 8 * (m * np.sqrt(m * n) * U + n * (n + 1) * U) * kb
     assert 80 * kb * (m * np.sqrt(m * n) * U + n * (n + 1) * U) <= 1
     assert np.linalg.norm(Q @ R - X) <= 16 * n * n * U * kb ** 1.5
+
+
+# ------------------------------------------------------------------ the 2-norm estimate of the shift
+
+def test_normest2_matches_eigvalsh():
+    """The power method's Rayleigh quotient converges to lambda_max (here with
+    a spectral gap of at least 10%: to within 1e-10 of numpy's eigvalsh)."""
+    rng = np.random.default_rng(31)
+    for n in (1, 2, 7, 32, 64):
+        Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = np.sort(rng.uniform(0.0, 0.9, size=n))
+        lam[-1] = 1.0 + rng.uniform(0.0, 5.0)
+        A = (Qm * lam) @ Qm.T
+        A = (A + A.T) / 2
+        est = oracle.normest2(A)
+        assert abs(est - np.linalg.eigvalsh(A).max()) <= 1e-10 * lam[-1]
+
+
+def test_two_norm_estimate_recovers_table1_shift():
+    """With ||X||_2 = 1 (the testmat construction), the estimated ||X||_2^2 is
+    1 to rounding, so the first shift is Eq. (finds2) with ||X||_2 = 1, as when
+    the caller passes norm_x2 = 1, and kappa(Q_1) of Table 1 follows."""
+    m, n, kappa = 1000, 30, 1e12
+    X = testmat(m, n, kappa, seed=1551)
+    _, _, st1, tr1 = oracle.scqr3(X, normx2=1.0)
+    Q, R, st, tr = oracle.scqr3(X, normx2=oracle.TWO_NORM_EST)
+    assert st == 0 and st1 == 0
+    assert abs(tr["norm2"][0] - 1.0) <= 1e-12
+    assert abs(tr["s"][0] - oracle.shift(m, n, 1.0)) <= 1e-12 * tr["s"][0]
+    assert tr["passes"] == tr1["passes"]
+    # every later shifted pass uses its own iterate's estimate; results keep the bounds
+    assert np.linalg.norm(Q.T @ Q - np.eye(n), 2) <= 6 * (m * n + n * (n + 1)) * 2.0 ** -53
