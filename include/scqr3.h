@@ -445,14 +445,10 @@ int scqr3_timing_end(scqr3_launch_time *out, int capacity, int *count);
  *                            16 < n <= 64 runs each pass's substitution in one
  *                            sweep; 0: in the separate diagonal-block and
  *                            update launches (for comparison).
- *   SCQR3_DEBUG_FUSED_STAGGER_NS  value: the start offset, in nanoseconds,
- *                            between consecutive row slots of a CTA of the
- *                            one-sweep substitution (0 .. 1e6; default 6000).
  * Returns SCQR3_OK, -1 for an unknown key, -2 for an invalid value. */
 #define SCQR3_DEBUG_WAIT_NS 1
 #define SCQR3_DEBUG_FUSED_SOLVE 2
 #define SCQR3_DEBUG_WAIT_SCOPE 3
-#define SCQR3_DEBUG_FUSED_STAGGER_NS 4
 int scqr3_debug_set(int key, long long value);
 
 #ifdef __cplusplus

@@ -65,7 +65,7 @@ void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_
 cudaError_t tc_fused_setup();
 bool tc_fused_supported(int n);
 void launch_tc_fused(int sms, cudaStream_t s, const double* X, int64_t ldx, double* Q, int64_t ldq, const Params& P,
-                     int pass, const double* rk, unsigned long long* colmax, DevState* st, int stagger_ns);
+                     int pass, const double* rk, unsigned long long* colmax, DevState* st);
 void launch_status(cudaStream_t s, const DevState* st, scqr3_info* info);
 
 namespace {
@@ -386,7 +386,6 @@ constexpr long long kDefaultWaitNs = 2000000000ll;
 std::atomic<long long> g_wait_ns{kDefaultWaitNs};
 std::atomic<int> g_wait_scope{3};  // bit 0: the Gram kernel, bit 1: the substitution kernels
 std::atomic<int> g_fused_solve{1};
-std::atomic<int> g_fused_stagger_ns{6000};  // start offset between the slots of the fused substitution
 
 void set_options(Params* P, const scqr3_opts* opts) {
   const long long w = g_wait_ns.load();
@@ -607,7 +606,7 @@ void tc_solve_rows(Call& c, int k, const double* rk, const double* src, int64_t 
     unsigned long long* cm = c.lt ? nullptr : c.colmax;
     if (cm) cudaMemsetAsync(cm, 0, sizeof(unsigned long long) * 128, c.s);
     tick(c.s, SCQR3_KERNEL_PASS, k);
-    launch_tc_fused(sm_count(), c.s, src, lds, dst, ldd, Pc, k, rk, cm, c.st, g_fused_stagger_ns.load());
+    launch_tc_fused(sm_count(), c.s, src, lds, dst, ldd, Pc, k, rk, cm, c.st);
     return;
   }
   const int n = Pc.n, w = tc_block_width(n), nb = (n + w - 1) / w;
@@ -1011,10 +1010,6 @@ extern "C" int scqr3_debug_set(int key, long long value) {
     case SCQR3_DEBUG_FUSED_SOLVE:
       if (value != 0 && value != 1) return -2;
       g_fused_solve.store((int)value);
-      return SCQR3_OK;
-    case SCQR3_DEBUG_FUSED_STAGGER_NS:
-      if (value < 0 || value > 1000000) return -2;
-      g_fused_stagger_ns.store((int)value);
       return SCQR3_OK;
     default:
       return -1;

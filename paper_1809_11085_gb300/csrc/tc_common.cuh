@@ -67,15 +67,19 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&v)[16]) {
 // which biases every |x| low.
 constexpr unsigned long long BIAS56 = 0x0081020408102040ull;  // 64 (1 + 2^7 + ... + 2^49)
 
-// M = round(x 2^(56-E)) + BIAS56 for |x| < 2^(E-1) (integer operations only).
+// M = round(x 2^(56-E)) + BIAS56 for |x| < 2^(E-1) (integer operations only):
+// with x = mant 2^(ex - 1075), N = mant 2^(ex - 1019 - E) = (4 mant) / 2^K,
+// K = 1021 + E - ex >= 0, rounded by adding 2^(K-1) before the shift (for
+// K <= 2 that adds less than 4 to a multiple of 4 and changes nothing; K is
+// capped at 63, where N is 0 already).
 __device__ __forceinline__ unsigned long long biased56(double x, int E) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   int ex = (int)((bits >> 52) & 0x7FF);
   unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
   if (ex) mant |= 1ull << 52; else ex = 1;
-  const int sh = ex - 1019 - E;  // N = mant 2^sh, sh <= 2 when |x| < 2^(E-1)
-  const unsigned long long F =
-      sh >= 0 ? (sh <= 2 ? (mant << sh) : (1ull << 55) - 1) : (sh > -64 ? (mant + (1ull << (-sh - 1))) >> -sh : 0ull);
+  int K = 1021 + E - ex;
+  K = K < 0 ? 0 : (K > 63 ? 63 : K);
+  const unsigned long long F = ((mant << 2) + ((1ull << K) >> 1)) >> K;
   return (long long)bits < 0 ? BIAS56 - F : BIAS56 + F;
 }
 
@@ -107,19 +111,34 @@ __device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr) : "memory");
 }
 
-// Digit s of two entries (biased M0, M1: rows r and r + 1 of a column) as a
-// BF16 pair: the fields f (< 128; f <= 128 for s = 0) are placed side by side
-// and added to the BF16 pattern of 128 (0x4300), which gives the exact BF16
-// value 128 + f (BF16 resolves units between 128 and 256, and 0x4300 + 128 is
-// the pattern of 256); one exact BF16x2 subtraction of 192 leaves f - 64.
-template <int S>
-__device__ __forceinline__ uint32_t digit_pair(unsigned long long M0, unsigned long long M1) {
-  const uint32_t lo = (uint32_t)(M0 >> (49 - 7 * S)), hi = (uint32_t)(M1 >> (49 - 7 * S));
-  const uint32_t w0 = __byte_perm(lo, hi, 0x5410);
-  uint32_t w = S == 0 ? (w0 & 0x00FF00FFu) + 0x43004300u : (w0 & 0x007F007Fu) | 0x43004300u;
-  __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&w);
-  v = __hsub2(v, __floats2bfloat162_rn(192.0f, 192.0f));
-  return *reinterpret_cast<uint32_t*>(&v);
+// The 8 digit planes of 8 biased values M[0..7] as BF16 pairs: word p of w[s]
+// holds digit s of M[2p] (low half) and of M[2p + 1] (high half). The fields
+// are taken two digits at a time: chunk j of a value (bits 42 - 14 j up, 14
+// bits; 15 for j = 0, whose top field d_0 + 64 <= 128 has 8) from two values
+// side by side in one word; one shift and one mask give the fields f of digit
+// 2 j, one mask those of digit 2 j + 1. A field f (< 128; <= 128 for s = 0)
+// added to the BF16 pattern of 128 (0x4300) gives the exact BF16 value 128 + f
+// (BF16 resolves units between 128 and 256, and 0x4300 + 128 is the pattern of
+// 256); one exact BF16x2 subtraction of 192 leaves the digit f - 64.
+__device__ __forceinline__ void planes8(const unsigned long long (&M)[8], uint4 (&w)[8]) {
+  uint32_t d[8][4];
+  const __nv_bfloat162 k192 = __floats2bfloat162_rn(192.0f, 192.0f);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t t0 = (uint32_t)(M[2 * p] >> (42 - 14 * j)), t1 = (uint32_t)(M[2 * p + 1] >> (42 - 14 * j));
+      const uint32_t C = __byte_perm(t0, t1, 0x5410);
+      uint32_t ev = j == 0 ? ((C >> 7) & 0x00FF00FFu) + 0x43004300u : ((C >> 7) & 0x007F007Fu) | 0x43004300u;
+      uint32_t od = (C & 0x007F007Fu) | 0x43004300u;
+      __nv_bfloat162 ve = __hsub2(*reinterpret_cast<__nv_bfloat162*>(&ev), k192);
+      __nv_bfloat162 vo = __hsub2(*reinterpret_cast<__nv_bfloat162*>(&od), k192);
+      d[2 * j][p] = *reinterpret_cast<uint32_t*>(&ve);
+      d[2 * j + 1][p] = *reinterpret_cast<uint32_t*>(&vo);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 8; ++s) w[s] = make_uint4(d[s][0], d[s][1], d[s][2], d[s][3]);
 }
 
 // Eight consecutive values as 8 digit planes of one core-matrix row each (16
@@ -128,18 +147,10 @@ __device__ __forceinline__ void cut8(const double* x, int E, uint8_t* dst, uint3
   unsigned long long M[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) M[r] = biased56(x[r], E);
-#define SCQR3_CUTS(S)                                \
-  {                                                  \
-    uint4 w;                                         \
-    w.x = digit_pair<S>(M[0], M[1]);                 \
-    w.y = digit_pair<S>(M[2], M[3]);                 \
-    w.z = digit_pair<S>(M[4], M[5]);                 \
-    w.w = digit_pair<S>(M[6], M[7]);                 \
-    *(uint4*)(dst + (S) * plane) = w;                \
-  }
-  SCQR3_CUTS(0) SCQR3_CUTS(1) SCQR3_CUTS(2) SCQR3_CUTS(3) SCQR3_CUTS(4) SCQR3_CUTS(5) SCQR3_CUTS(6)
-  SCQR3_CUTS(7)
-#undef SCQR3_CUTS
+  uint4 w[8];
+  planes8(M, w);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) *(uint4*)(dst + s * plane) = w[s];
 }
 
 // Scale exponent of a non-negative bit-pattern maximum for the balanced

@@ -132,16 +132,6 @@ __device__ __forceinline__ void issue_e(uint64_t dbase, uint32_t tmem, uint32_t 
   if constexpr (E < 7) issue_e<KC, OFFD, E + 1>(dbase, tmem, idesc, first_chunk);
 }
 
-template <int KC, int S>
-__device__ __forceinline__ void store_plane(uint8_t* dst, const unsigned long long (&M)[8]) {
-  uint4 w4;
-  w4.x = digit_pair<S>(M[0], M[1]);
-  w4.y = digit_pair<S>(M[2], M[3]);
-  w4.z = digit_pair<S>(M[4], M[5]);
-  w4.w = digit_pair<S>(M[6], M[7]);
-  *(uint4*)(dst + plane_off<KC>(S)) = w4;
-}
-
 }  // namespace tc
 
 // Column scales: colmax[j] = max_i |q_ij| (pairs: max_i |hi_ij|) as the bit pattern of a double (the
@@ -493,14 +483,10 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
           }
         }
         uint8_t* dst = sb + (j >> 6) * GK::BREG + ((j & 63) >> 3) * GK::SBO + ig * LBO + (j & 7) * 16;
-        tc::store_plane<KC, 0>(dst, F);
-        tc::store_plane<KC, 1>(dst, F);
-        tc::store_plane<KC, 2>(dst, F);
-        tc::store_plane<KC, 3>(dst, F);
-        tc::store_plane<KC, 4>(dst, F);
-        tc::store_plane<KC, 5>(dst, F);
-        tc::store_plane<KC, 6>(dst, F);
-        tc::store_plane<KC, 7>(dst, F);
+        uint4 w[8];
+        tc::planes8(F, w);
+#pragma unroll
+        for (int sd = 0; sd < 8; ++sd) *(uint4*)(dst + tc::plane_off<KC>(sd)) = w[sd];
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[stg])) : "memory");

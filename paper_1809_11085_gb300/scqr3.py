@@ -169,7 +169,6 @@ def lib():
 DEBUG_WAIT_NS = 1       # hand-off wait limit (ns) of the tensor-core kernels; < 0: default
 DEBUG_FUSED_SOLVE = 2   # 1: one-sweep tensor-core substitution (16 < n <= 64); 0: separate launches
 DEBUG_WAIT_SCOPE = 3    # kernels the wait limit applies to: bit 0 the Gram, bit 1 the substitution
-DEBUG_FUSED_STAGGER_NS = 4  # start offset (ns) between the row slots of the one-sweep substitution
 
 
 def debug_set(key: int, value: int) -> None:

@@ -77,6 +77,27 @@ def test_fused_shape_sweep(n, m_kind):
     assert np.linalg.norm(Rf - Rs) / np.linalg.norm(Rs) <= 1e-12
 
 
+@pytest.mark.parametrize("scale", [0.0, 1e-9, 1e-3])
+def test_rows_with_a_small_leading_block(scale):
+    """The middle product uses one scale per row for y_0 and y_1; the first
+    product's scale, taken with headroom from y_0 alone, serves both unless y_1
+    is larger, and those rows cut y_0 again. Rows whose leading 16 entries are
+    zero or far below the rest take that second path (every 3rd and 7th row
+    here, so that most warps hold both kinds of row)."""
+    m, n, kappa = 60013, 64, 1e6
+    Xh = testmat(m, n, kappa, seed=9400)
+    Xh[::3, :16] *= scale
+    Xh[::7, :16] = 0.0
+    Qf, Rf, inf = run(Xh)
+    Qo, Ro, st, tr = oracle.scqr3(Xh)
+    assert st == 0 and inf.status == 0, (st, inf)
+    assert np.linalg.norm(Qf.T @ Qf - np.eye(n), 2) <= 1e-13
+    assert np.linalg.norm(Xh - Qf @ Rf) / np.linalg.norm(Xh) <= 1e-13
+    kx = np.linalg.cond(Xh)
+    dR = np.linalg.norm(Rf - Ro) / np.linalg.norm(Ro)
+    assert dR <= max(1e-12, 100 * n * kx * U), (dR, kx)
+
+
 @pytest.mark.parametrize("kappa", [1e2, 1e8, 1e12, 1e15])
 @pytest.mark.parametrize("n", [32, 64])
 def test_fused_conditioning(n, kappa):
