@@ -17,7 +17,8 @@
 //    it exactly in FP32 as long as a sum stays within 2^24: 1024 rows of up to
 //    four digit pairs (4 * 1024 * 64^2 = 2^24);
 //  * D_d = sum over digit pairs (s, t) with s + t = d, d = 0 .. 7, is read back
-//    from tensor memory every 1024 rows. The digit sums are exact integers, so
+//    from tensor memory every 1024 rows (in two shares, lanes 0..63 of tile d
+//    and lanes 64..127 of tile d - 1, added at the end). The digit sums are exact integers, so
 //    U = D_0 2^21 + D_1 2^14 + D_2 2^7 + D_3 and T = D_4 2^21 + ... + D_7
 //    (per 1024 rows below 2^45.1) are accumulated exactly in int64 over all
 //    of a CTA's rows (below 2^63 up to 2^27.9 rows per CTA; a 288 GB device
@@ -49,13 +50,14 @@
 // (the chunk rows are the K dimension), no swizzle: core matrices of 8
 // columns x 8 rows (16 bytes per column), the KC / 8 row groups of a column
 // block contiguous (128 bytes apart), column blocks 16 KC bytes apart. A plane
-// of one block is 128 KC bytes; planes are stored in the order 0, 4, 1, 5, 2,
-// 6, 3, 7 so that the A operand of one MMA (M = 128) covers digit s in its rows
-// 0..63 and digit s + 4 in rows 64..127: one instruction computes the pairs
-// (s, t) and (s + 4, t). Tile e of tensor memory (columns 64e .. 64e+63)
-// accumulates, for s = 0 .. min(3, e) and t = e - s, the pairs (s, t) in lanes
-// 0..63 (d = e) and (s + 4, t) in lanes 64..127 (d = e + 4). Eight tiles use all
-// 512 columns.
+// of one block is 128 KC bytes, and the planes lie in digit order, so that
+// one A operand (M = 128) holds digits s and s + 1 of the block's columns and
+// one B operand (N up to 256) the planes t .. t + 3 side by side: tile x of
+// tensor memory (columns 64x .. 64x+63) accumulates the pairs (s, x - s) in
+// lanes 0..63 (d = x) and (s + 1, x - s) in lanes 64..127 (d = x + 1), for
+// s = 0, 2, 4, 6. Eight tiles use all 512 columns; six MMAs per K step cover
+// every pair with s + t <= 7 (the issue of an MMA costs about as much for
+// N = 256 as for N = 64, so wide ones are what keeps the tensor core busy).
 //
 // One CTA of 256 + 32 threads per SM. Two 64 KB digit-plane stages: the threads cut
 // chunk c + 1 while the tensor core works on chunk c. When the rows are
@@ -101,35 +103,45 @@ __device__ __forceinline__ uint64_t desc(uint32_t addr) {
          ((uint64_t)1 << 46);
 }
 
-// byte offset of digit plane s within an operand block's planes
+// byte offset of digit plane s within an operand block's planes (natural
+// order, so that planes s, s + 1 form one A operand of M = 128 and planes
+// t .. t + 3 one B operand of N = 256)
 template <int KC>
 __host__ __device__ constexpr uint32_t plane_off(int s) {
-  return s < 4 ? s * 2 * ChunkGeo<KC>::PLANE : (s - 4) * 2 * ChunkGeo<KC>::PLANE + ChunkGeo<KC>::PLANE;
+  return s * ChunkGeo<KC>::PLANE;
 }
 
-// The MMAs of one chunk: tile e, digit s (and s + 4), digit t = e - s, K step kk.
-// OFFD: the B operand is the second block's planes. The start-address field
-// of a descriptor is its low 14 bits (address / 16); the operands of a stage
-// lie within 64 KB of its base and every stage below 256 KB, so offsets are
-// added to the base descriptor without carrying out of the field.
-template <int KC, bool OFFD, int E, int S, int KK>
+// The MMAs of one chunk. A = digit planes s and s + 1 (M = 128: rows 0..63
+// digit s, rows 64..127 digit s + 1, of the block's 64 columns), B = planes
+// t0 .. t0 + nt - 1 side by side (N = 64 nt), written from tensor column
+// 64 (s + t0): tile x (columns 64 x ..) then accumulates the pairs (s, x - s)
+// in lanes 0..63 (d = x) and (s + 1, x - s) in lanes 64..127 (d = x + 1).
+// For s = 0, 2, 4, 6 and t = 0 .. 7 - s that is every pair with s + t <= 7
+// (and a few with d = 8 in the upper lanes of tile 7, never read), in six
+// MMAs per K step: the cost of an MMA's issue does not grow with N, so few
+// wide ones keep the tensor core busy. Tile x holds at most 4 pairs per lane
+// half; per 1024 rows a sum stays within 4 * 1024 * 64^2 = 2^24, exact in
+// FP32. OFFD: the B operand is the second block's planes. The start-address
+// field of a descriptor is its low 14 bits (address / 16); the operands of a
+// stage lie within 64 KB of its base and every stage below 256 KB, so offsets
+// are added to the base descriptor without carrying out of the field.
+template <int KC, bool OFFD, int S, int T0, int NT, int KK>
 __device__ __forceinline__ void issue_one(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
-  constexpr int T = E - S;
   constexpr uint64_t aoff = (plane_off<KC>(S) + KK * 2 * LBO) >> 4;
-  constexpr uint64_t boff = ((OFFD ? ChunkGeo<KC>::BREG : 0) + plane_off<KC>(T) + KK * 2 * LBO) >> 4;
+  constexpr uint64_t boff = ((OFFD ? ChunkGeo<KC>::BREG : 0) + plane_off<KC>(T0) + KK * 2 * LBO) >> 4;
+  // the s = 0 MMAs of the first K step of a group's first chunk write all 8 tiles
   const uint32_t accum = (!first_chunk || S > 0 || KK > 0) ? 1u : 0u;
-  mma(tmem + 64 * E, dbase + aoff, dbase + boff, idesc, accum);
-  if constexpr (KK + 1 < KC / 16) issue_one<KC, OFFD, E, S, KK + 1>(dbase, tmem, idesc, first_chunk);
+  mma(tmem + 64 * (S + T0), dbase + aoff, dbase + boff, idesc | ((uint32_t)(8 * NT) << 17), accum);
 }
-template <int KC, bool OFFD, int E, int S>
-__device__ __forceinline__ void issue_s(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
-  issue_one<KC, OFFD, E, S, 0>(dbase, tmem, idesc, first_chunk);
-  if constexpr (S < 3 && S < E) issue_s<KC, OFFD, E, S + 1>(dbase, tmem, idesc, first_chunk);
-}
-template <int KC, bool OFFD, int E>
-__device__ __forceinline__ void issue_e(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
-  issue_s<KC, OFFD, E, 0>(dbase, tmem, idesc, first_chunk);
-  if constexpr (E < 7) issue_e<KC, OFFD, E + 1>(dbase, tmem, idesc, first_chunk);
+template <int KC, bool OFFD, int KK>
+__device__ __forceinline__ void issue_k(uint64_t dbase, uint32_t tmem, uint32_t idesc, bool first_chunk) {
+  issue_one<KC, OFFD, 0, 0, 4, KK>(dbase, tmem, idesc, first_chunk);
+  issue_one<KC, OFFD, 0, 4, 4, KK>(dbase, tmem, idesc, first_chunk);
+  issue_one<KC, OFFD, 2, 0, 4, KK>(dbase, tmem, idesc, first_chunk);
+  issue_one<KC, OFFD, 2, 4, 2, KK>(dbase, tmem, idesc, first_chunk);
+  issue_one<KC, OFFD, 4, 0, 4, KK>(dbase, tmem, idesc, first_chunk);
+  issue_one<KC, OFFD, 6, 0, 2, KK>(dbase, tmem, idesc, first_chunk);
+  if constexpr (KK + 1 < KC / 16) issue_k<KC, OFFD, KK + 1>(dbase, tmem, idesc, first_chunk);
 }
 
 }  // namespace tc
@@ -342,8 +354,8 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
   const uint32_t sbase = smem_u32(stages);
-  // D F32, A and B BF16, both K-major, N = 64, M = 128
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+  // D F32, A and B BF16, both K-major, M = 128 (N set per MMA)
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 4) << 24);
 
   // This CTA's chunks in order: ordinal k is chunk k % CHUNKS of its group
   // cta + (k / CHUNKS) ncta; the sequence ends at the first chunk past m
@@ -408,10 +420,10 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint64_t db = desc<KC>(sbase + stg * STAGE);
         if constexpr (KC == 32) {
-          if (offd) tc::issue_e<KC, true, 0>(db, tmem, idesc, q == 0);
-          else tc::issue_e<KC, false, 0>(db, tmem, idesc, q == 0);
+          if (offd) tc::issue_k<KC, true, 0>(db, tmem, idesc, q == 0);
+          else tc::issue_k<KC, false, 0>(db, tmem, idesc, q == 0);
         } else {
-          tc::issue_e<KC, false, 0>(db, tmem, idesc, q == 0);
+          tc::issue_k<KC, false, 0>(db, tmem, idesc, q == 0);
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(smem_u32(&bar[stg])) : "memory");
@@ -501,16 +513,16 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
         const uint32_t tq = tmem + ((uint32_t)(32 * qd) << 16) + CW * h;
 #pragma unroll
         for (int c = 0; c < CW; c += 8) {
-          // upper rows: U from tiles 0..3, T from tiles 4..7; lower rows hold
-          // d = e + 4: T from tiles 0..3 (tiles 4..7 would be d >= 8).
-          // D_d enters with weight 2^(7 (3 - d)) (U) or 2^(7 (7 - d)) (T).
+          // upper rows hold d = e (tiles 0..7), lower rows d = e + 1 (tiles
+          // 0..6; tile 7 would be d = 8). D_d enters U with weight
+          // 2^(7 (3 - d)) (d <= 3) or T with weight 2^(7 (7 - d)).
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            if (!upper && e >= 4) break;
+            if (!upper && e == 7) break;
             uint32_t v[8];
             tc::ld8(tq + 64 * e + c, v);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int d = upper ? e : e + 4;
+            const int d = upper ? e : e + 1;
             const int sh = d < 4 ? 7 * (3 - d) : 7 * (7 - d);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -535,14 +547,18 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
     }
   }
 
-  // rows 64..127 hold the d + 4 share of the same entries: add them to rows 0..63
+  // rows 64..127 hold the d + 1 share of the same entries: add them to rows 0..63
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  long long* xch = (long long*)stages;  // 64 x 64 int64 (32 KB) of stage 0
-  long long* s44sh = xch + BW * BW;     // then the slicers' digit-4 square sums
+  long long* xch = (long long*)stages;  // 64 x 64 int64 T shares (32 KB) of stage 0,
+  long long* xchu = xch + BW * BW;      // then the U shares (32 KB)
+  long long* s44sh = xchu + BW * BW;    // then the slicers' digit-4 square sums
   if (!producer && !upper) {
 #pragma unroll
-    for (int k = 0; k < CW; ++k) xch[jr * BW + CW * h + k] = T[k];
+    for (int k = 0; k < CW; ++k) {
+      xch[jr * BW + CW * h + k] = T[k];
+      xchu[jr * BW + CW * h + k] = U[k];
+    }
   }
   if (!producer) s44sh[tid] = s44;
   __syncthreads();
@@ -552,7 +568,7 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
     for (int k = 0; k < CW; ++k) {
       const int c = CW * h + k;
       if (offd || c >= jr) {
-        double a = fma(0x1p-35, (double)U[k], 0x1p-63 * (double)(T[k] + xch[jr * BW + c]));
+        double a = fma(0x1p-35, (double)(U[k] + xchu[jr * BW + c]), 0x1p-63 * (double)(T[k] + xch[jr * BW + c]));
         if (!offd && c == jr) {  // the diagonal: the square pair (4, 4), weight 2^-70
           long long q = 0;
           for (int t = jr; t < THREADS; t += BW) q += s44sh[t];
