@@ -134,17 +134,26 @@ def flops_of(m, n, passes):
     return passes * m * (n * (n + 1) + n * n)
 
 
+def gram_mma_flops(m, n):
+    """Flops of the MMAs one tensor-core Gram launch issues: per K step of 16
+    rows, six MMAs of M = 128 whose N add up to 1280 (digit planes s, s + 1
+    against up to four planes side by side, s = 0, 2, 4, 6), 2 * 128 * 16 flops
+    per unit of N; n <= 64 one 64-column block over all rows, 64 < n <= 128
+    three blocks (0,0), (1,1), (0,1), each over all rows."""
+    ksteps = (m + 63) // 64 * 4 if n <= 64 else 3 * ((m + 31) // 32) * 2
+    return ksteps * 1280 * 2 * 128 * 16
+
+
 def tc_gram_roofline(m, n, ms_list):
     """Tensor-pipe figures of the tensor-core Gram launches: the MMAs it issues
-    per 64-row chunk (104 of M=128, N=64, K=16: 2*128*64*16 flops each) against
-    the measured sustained BF16 peak (the kernel runs inside a long step)."""
+    (gram_mma_flops) against the measured sustained BF16 peak (the kernel runs
+    inside a long step)."""
     if not ms_list:
         return None
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
-    chunks = (m + 63) // 64
-    issued = chunks * 104 * 2 * 128 * 64 * 16
+    issued = gram_mma_flops(m, n)
     useful = m * 36 * n * n * 2  # the 36 digit pairs with s + t <= 7 of every row's outer product
     t = statistics.median(ms_list) * 1e-3
     return {"bound": "tensor", "kernel": "tc_gram_kernel (+ colmax_kernel in the timing)",
@@ -673,14 +682,14 @@ def run_gpu(args, rank, world, local_rank):
         hbm = peaks.get("hbm_gbs", 6800.0)
         fp64_ms = passes * fused_fp64_ops(n) * m / (FP64_PEAK_DERIVED_TFLOPS * 1e12 / 2) * 1e3
         grams = passes  # the Gram of X and one after each pass but the last
-        tensor_ms = grams * ((m + 63) // 64) * 104 * 2 * 128 * 64 * 16 / (bf16 * 1e12) * 1e3
+        tensor_ms = grams * gram_mma_flops(m, n) / (bf16 * 1e12) * 1e3
         byts = m * n * 8 * (1 + 2 * passes + (passes - 1) + 1)  # scan of X, each pass r/w, Gram reads
         hbm_ms = byts / (hbm * 1e9) * 1e3
         floor = fp64_ms + tensor_ms
         path = {"floor_ms": floor, "frac": floor / ms, "fp64_pipe_ms": fp64_ms, "gram_tensor_ms": tensor_ms,
                 "hbm_ms_overlapped": hbm_ms, "fp64_ops_per_row_per_pass": fused_fp64_ops(n),
                 "note": "floor = the substitution's FP64-pipe operations at 1258.6 GFLOP/s (DFMA rate) + the "
-                        "tensor-core Gram MMAs (104 per 64 rows) at the measured sustained BF16 peak; HBM time "
+                        "tensor-core Gram MMAs (gram_mma_flops) at the measured sustained BF16 peak; HBM time "
                         "(every byte moved once per kernel) overlaps both; per-kernel fractions below",
                 "fp64_6mn2_roofline_ms": 6 * m * n * n / (FP64_PEAK_DERIVED_TFLOPS * 1e12) * 1e3}
 

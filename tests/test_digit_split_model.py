@@ -300,3 +300,111 @@ def test_blocked_substitution_backward_error(n, w, kappa):
         ez = np.linalg.norm(x0 - z @ R) / (np.linalg.norm(z) * normR)
         assert eb <= 4 * n * u and ez <= 4 * n * u, (trial, eb, ez)
         assert eb <= 16 * max(ez, u), (trial, eb, ez)
+
+
+def test_fixed_point_shift_form():
+    """The kernels form N = round(x 2^(56-E)) from the bit pattern as
+    (4 mant + 2^(K-1)) >> K with K = 1021 + E - ex capped to [0, 63] (mant the
+    53-bit significand, ex the biased exponent): the same integer as rounding
+    half away from zero, for normal and subnormal x and every scale the
+    kernels' rule gives (|x| < 2^(E-1))."""
+    rng = np.random.default_rng(21)
+    vals = [float(v) for v in rng.standard_normal(3000) * 10.0 ** rng.integers(-300, 300, 3000)]
+    vals += [5e-324, 2.2250738585072014e-308, 1.0 - 2.0 ** -53, 0.75, 2.0 ** -1074 * 3]
+    for v in vals:
+        if v == 0.0 or not math.isfinite(v):
+            continue
+        bits = int(np.float64(abs(v)).view(np.uint64))
+        for extra in (0, 1, 2, 40, 80):
+            # the kernels' scale rule: (exponent field, 1 for subnormals) - 1021,
+            # which keeps K >= 0 for subnormal values as well
+            E = max((bits >> 52) & 0x7FF, 1) - 1021 + extra  # |v| < 2^(E-1)
+            ex = (bits >> 52) & 0x7FF
+            mant = bits & ((1 << 52) - 1)
+            if ex:
+                mant |= 1 << 52
+            else:
+                ex = 1
+            K = min(max(1021 + E - ex, 0), 63)
+            N = ((mant << 2) + ((1 << K) >> 1)) >> K
+            assert N == abs(round_half_away(Fraction(v) * Fraction(2) ** (56 - E))), (v, E)
+
+
+def test_digit_fields_from_14_bit_chunks():
+    """The kernels take the 7-bit fields two at a time: chunk j = bits
+    42 - 14 j up of M (two values side by side in one 32-bit word, low 16 bits
+    each), field 2 j = (chunk >> 7) & 127 (& 255 for j = 0: the top field
+    holds up to 128), field 2 j + 1 = chunk & 127; the same fields as
+    (M >> (49 - 7 s)) & 127."""
+    rng = np.random.default_rng(22)
+    for _ in range(3000):
+        N = int(rng.integers(-(2 ** 55) + 1, 2 ** 55))
+        M0 = N + BIAS56
+        M1 = int(rng.integers(-(2 ** 55) + 1, 2 ** 55)) + BIAS56
+        for j in range(4):
+            t0 = (M0 >> (42 - 14 * j)) & 0xFFFFFFFF
+            t1 = (M1 >> (42 - 14 * j)) & 0xFFFFFFFF
+            C = (t0 & 0xFFFF) | ((t1 & 0xFFFF) << 16)  # byte_perm(t0, t1, 0x5410)
+            ev = (C >> 7) & (0x00FF00FF if j == 0 else 0x007F007F)
+            od = C & 0x007F007F
+            for M, sh in ((M0, 0), (M1, 16)):
+                f_even = (M >> 49) if j == 0 else (M >> (49 - 7 * (2 * j))) & 127
+                f_odd = (M >> (49 - 7 * (2 * j + 1))) & 127
+                assert (ev >> sh) & 0xFFFF == f_even and (od >> sh) & 0xFFFF == f_odd
+
+
+def test_pairwise_fold_in_32_bits():
+    """The one-sweep substitution folds tile sums |D_e| <= 2^20 as
+    b_e = 0x4B400000 + D_e (the float bits of D_e + 1.5 2^23), pairs
+    P = b_e 2^7 + b_(e+1) - 129 * 0x4B400000 in 32-bit wrap-around arithmetic
+    (the true value below 2^28), and W = P01 2^35 + P23 2^21 + P45 2^7 +
+    floor(P67 / 2^7): the same W as the int64 fold."""
+    rng = np.random.default_rng(23)
+    C129 = (0x4B400000 * 129) & 0xFFFFFFFF
+    cases = [[2 ** 20] * 8, [-(2 ** 20)] * 8, [0] * 8, [2 ** 20, -(2 ** 20)] * 4]
+    cases += [list(rng.integers(-(2 ** 20), 2 ** 20 + 1, 8)) for _ in range(5000)]
+    for D in cases:
+        D = [int(d) for d in D]
+        assert float(np.float32(D[0] + 1.5 * 2 ** 23)) == D[0] + 1.5 * 2 ** 23
+        b = [(0x4B400000 + d) & 0xFFFFFFFF for d in D]
+
+        def pair(x, y):
+            p = (x * 128 + y - C129) & 0xFFFFFFFF
+            return p - (1 << 32) if p >= 1 << 31 else p
+
+        p01, p23, p45, p67 = pair(b[0], b[1]), pair(b[2], b[3]), pair(b[4], b[5]), pair(b[6], b[7])
+        assert p01 == D[0] * 128 + D[1] and abs(p01) < 2 ** 28
+        W = (p01 << 35) + (p23 << 21) + (p45 << 7) + (p67 >> 7)
+        assert W == fold(D) and abs(W) < 2 ** 63
+
+
+def test_gram_mma_program_covers_each_pair_once():
+    """The Gram kernel's six MMAs per K step: A = digit planes s (lanes 0..63)
+    and s + 1 (lanes 64..127), B = planes t0 .. t0 + nt - 1 side by side, from
+    tensor column 64 (s + t0). The read-back takes d = x from lanes 0..63 of
+    tile x and d = x + 1 from lanes 64..127 of tiles 0..6. Every pair with
+    s + t <= 7 lands in exactly one cell that is read, with d = s + t; each
+    lane half of a tile holds at most 4 pairs (the 2^24 bound); the columns
+    stay within the 512 of tensor memory; N <= 256 per MMA."""
+    program = [(0, 0, 4), (0, 4, 4), (2, 0, 4), (2, 4, 2), (4, 0, 4), (6, 0, 2)]
+    cells = {}
+    for s, t0, nt in program:
+        assert 64 * (s + t0) + 64 * nt <= 512 and 64 * nt <= 256
+        for i in range(nt):
+            t = t0 + i
+            tile = s + t
+            cells.setdefault((tile, "lo"), []).append((s, t))
+            cells.setdefault((tile, "hi"), []).append((s + 1, t))
+    read = {}
+    for (tile, half), pairs in cells.items():
+        assert len(pairs) <= 4
+        d = tile if half == "lo" else tile + 1
+        if d > 7:
+            continue  # never read back
+        for s, t in pairs:
+            assert s + t == d
+            read[(s, t)] = read.get((s, t), 0) + 1
+    want = {(s, t) for s in range(8) for t in range(8) if s + t <= 7}
+    assert set(read) == want and all(c == 1 for c in read.values())
+    # the bench's flop count: N adds up to 1280 per K step
+    assert sum(64 * nt for _, _, nt in program) == 1280
