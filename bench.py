@@ -819,12 +819,24 @@ def extra_legs(torch, dev, stream, args):
         ws = scqr3.Workspace(m, n, device=dev)
         ms = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, workspace=ws, read_info=False))
         inf = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
-        sweep[str(kk)] = {"ms": round(ms, 2), "rows_per_s": m / (ms * 1e-3), "passes": inf.passes,
-                          "status": inf.status, "orth": _orth(torch, Q),
-                          "tflops": flops_of(m, n, inf.passes) / (ms * 1e-3) / 1e12}
-        del X, Q, ws
+        R64 = None
+        row = {"ms": round(ms, 2), "rows_per_s": m / (ms * 1e-3), "passes": inf.passes,
+               "status": inf.status, "orth": _orth(torch, Q),
+               "tflops": flops_of(m, n, inf.passes) / (ms * 1e-3) / 1e12}
+        _, R64, _ = scqr3.factor(X, workspace=ws)
+        # the FP64-accurate tensor-core form of the same X (n <= 256, B = I)
+        mst = _time(torch, stream, lambda: scqr3.factor(X, Q=Q, workspace=ws, precision=scqr3.PREC_TC,
+                                                        read_info=False))
+        inft = scqr3.Info.from_bytes(ws.info.cpu().numpy().tobytes())
+        _, Rt, _ = scqr3.factor(X, workspace=ws, precision=scqr3.PREC_TC)
+        row["tc"] = {"ms": round(mst, 2), "rows_per_s": m / (mst * 1e-3), "speedup": ms / mst,
+                     "passes": inft.passes, "status": inft.status, "orth": _orth(torch, Q),
+                     "dR_vs_fp64": float(torch.linalg.norm(Rt - R64) / torch.linalg.norm(R64))}
+        sweep[str(kk)] = row
+        del X, Q, ws, R64, Rt
         free()
-    legs["scaleup_n256"] = {"workload": "FP64 sCQR3, X = U diag(sigma) V^T, 1048576 x 256", "kappa": sweep}
+    legs["scaleup_n256"] = {"workload": "sCQR3, X = U diag(sigma) V^T, 1048576 x 256: FP64 and the "
+                                        "FP64-accurate tensor-core form (tc)", "kappa": sweep}
 
     # mixed and tensor-core forms vs FP64 on the same matrices
     mixed = {}

@@ -35,8 +35,9 @@ extern "C" {
 #endif
 
 #define SCQR3_MAX_PASSES 8   /* upper limit of opts.max_passes            */
-#define SCQR3_MAX_N 256      /* largest n (FP64, B = I); the oblique, mixed,
-                                batched and adjoint forms take n <= 128    */
+#define SCQR3_MAX_N 256      /* largest n (FP64 and SCQR3_PREC_TC, B = I);
+                                the oblique, mixed, batched and adjoint
+                                forms take n <= 128                        */
 
 /* Status codes (return values and scqr3_info.status).
  *   > 0  : the SHIFTED Cholesky broke down at this 1-based column, i.e.
@@ -87,10 +88,11 @@ extern "C" {
  *    O(u ||R||) per row (the form of the row-wise backward error, Eq.
  *    backward2). For 16 < n <= 64 a pass reads each row once and writes it
  *    once (one sweep, see scqr3_debug_set).
- * Results match the FP64 form to rounding. n <= 128, m <= 2^31, and B either
- * NULL or block-diagonal with blocks of 1, 2, 4 or 8 rows (the Gram matrix of
- * Z = L^T Q, L_j^T applied to each 8-row unit before the split); other
- * shapes return SCQR3_E_UNSUPPORTED. */
+ * Results match the FP64 form to rounding. m <= 2^31; n <= 256 with
+ * B = NULL (for 128 < n <= 256 the Gram matrix is ten 64-column block pairs),
+ * or n <= 128 with B block-diagonal with blocks of 1, 2, 4 or 8 rows (the
+ * Gram matrix of Z = L^T Q, L_j^T applied to each 8-row unit before the
+ * split); other shapes return SCQR3_E_UNSUPPORTED. */
 #define SCQR3_PREC_TC 2
 /* The mixed form's substitution (FP32 pairs) with the Gram matrices of
  * SCQR3_PREC_TC, read directly from the float-pair iterates. n <= 128,

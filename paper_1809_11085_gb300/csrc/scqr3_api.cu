@@ -71,7 +71,7 @@ void launch_status(cudaStream_t s, const DevState* st, scqr3_info* info);
 namespace {
 
 // The tensor-core Gram works on blocks of 64 columns.
-int tc_np(int n) { return n <= 64 ? 64 : 128; }
+int tc_np(int n) { return n <= 64 ? 64 : n <= 128 ? 128 : 256; }
 
 int padded_n(int n) {
   if (n <= 16) return 16;
@@ -191,9 +191,10 @@ int check_args(int64_t m, int n, const scqr3_B* B, const scqr3_opts* opts, bool 
       opts->precision != SCQR3_PREC_TC && opts->precision != SCQR3_PREC_MIXED_TC)
     return -12;
   const bool tcp = opts && (opts->precision == SCQR3_PREC_TC || opts->precision == SCQR3_PREC_MIXED_TC);
-  // tensor-core Gram: n <= 128, B = I, and at most 2^31 rows (its exact int64
-  // digit-sum accumulators)
-  if (tcp && (n > 128 || m > ((int64_t)1 << 31))) return SCQR3_E_UNSUPPORTED;
+  // tensor-core Gram: at most 2^31 rows (its exact int64 digit-sum
+  // accumulators); n <= 128, or n <= 256 for the FP64-accurate form with B = I
+  if (tcp && (n > 256 || m > ((int64_t)1 << 31))) return SCQR3_E_UNSUPPORTED;
+  if (tcp && n > 128 && (B || opts->precision != SCQR3_PREC_TC)) return SCQR3_E_UNSUPPORTED;
   // tensor-core forms with B: block-diagonal with blocks of 1, 2, 4 or 8 rows
   // (they divide the kernel's 8-row units), FP64 substitution only
   if (tcp && B && (B->bs == 0 || B->bs > 8 || opts->precision == SCQR3_PREC_MIXED_TC)) return SCQR3_E_UNSUPPORTED;
@@ -257,7 +258,7 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
   // the tensor-core Gram's slots and column scales are always reserved, so
   // one workspace serves every precision of a shape
   {
-    L->tc_grid = tc_grid(m, np <= 64 ? 64 : 128, sms);
+    L->tc_grid = tc_grid(m, tcg ? np : (np <= 64 ? 64 : 128), sms);
     if (L->tc_grid > slots_alloc) slots_alloc = L->tc_grid;
     if (tcg) L->n_partials = L->tc_grid;
   }
@@ -279,7 +280,7 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
     const int64_t cr = host_chunk_rows(m);
     for (int64_t r0 = 0; r0 < m; r0 += cr) {
       const int64_t rows = (m - r0) < cr ? (m - r0) : cr;
-      ftc += tc_grid(rows, np <= 64 ? 64 : 128, sms);
+      ftc += tc_grid(rows, tcg ? np : (np <= 64 ? 64 : 128), sms);
       if (np == 256) {
         f64 += grid64;
       } else {
@@ -300,7 +301,7 @@ int make_layout_one(int64_t m, int n, const scqr3_B* B, int prec, int host_chunk
     off = align256(off + sizeof(scqr3_info));
   }
   L->colmax = off;
-  off = align256(off + sizeof(unsigned long long) * 128);
+  off = align256(off + sizeof(unsigned long long) * 256);
   L->tcr = off;
   off = align256(off + sizeof(double) * 8 * pk_size(32));
   L->lt = off;
@@ -321,7 +322,8 @@ int make_layout(int64_t m, int n, const scqr3_B* B, int prec, int host_chunks, L
   const int r = make_layout_one(m, n, B, prec, host_chunks, L, grid, geo);
   if (r != SCQR3_OK) return r;
   for (int p : {SCQR3_PREC_FP64, SCQR3_PREC_TC, SCQR3_PREC_MIXED_TC}) {
-    const bool tc_ok = n <= 128 && (!B || (p == SCQR3_PREC_TC && B->bs > 0 && B->bs <= 8));
+    const bool tc_ok = n <= 128 ? (!B || (p == SCQR3_PREC_TC && B->bs > 0 && B->bs <= 8))
+                                : (n <= 256 && !B && p == SCQR3_PREC_TC);
     if (p == prec || (p != SCQR3_PREC_FP64 && !tc_ok)) continue;
     Layout L2;
     int g2;
@@ -538,15 +540,15 @@ int first_gram(Call& c, const double* X, int64_t ldx, int64_t r0, int64_t r1, in
   const double* src = X + r0 * ldx;
   double* part = c.partials + (int64_t)slot0 * c.L.part_stride;
   tick(c.s, SCQR3_KERNEL_GRAM, 0);
-  if (c.P.np == 256) {
-    launch_gram256(c.grid, c.s, src, ldx, Pc, -1, part, c.L.part_stride, c.st);
-    return c.grid;
-  }
   if (c.tc) {
     const int g = tc_grid(Pc.m, c.P.np, sm_count());
     launch_tc_gram(g, sm_count(), c.s, src, ldx, Pc, -1, c.colmax, part, c.L.part_stride, c.st, 0, c.lt,
                    c.lt ? r0 / c.P.bs : 0, 1);
     return g;
+  }
+  if (c.P.np == 256) {
+    launch_gram256(c.grid, c.s, src, ldx, Pc, -1, part, c.L.part_stride, c.st);
+    return c.grid;
   }
   if (c.csr) {  // the whole matrix only: rows reach across any split
     launch_csr_gram(c.P.np, c.L.csr_grid, c.s, src, ldx, c.P, -1, c.B, part, c.L.part_stride, c.st);
@@ -588,7 +590,7 @@ int pass_grid(int np, int64_t m) {
 // halve the FP64 work again but multiply the tensor-core updates.
 int tc_block_width(int n) { return n <= 64 ? 16 : 32; }
 
-// The tensor-core form's substitution (n <= 128) in blocks of w columns: for
+// The tensor-core form's substitution (n <= 256) in blocks of w columns: for
 // J = 0, 1, ..: Y_J = X_J R_JJ^{-1} (FP64 pass kernel), then X_K := X_K -
 // Y_J R_JK for the later columns, 32 at a time (tensor cores, exact digit
 // split). Block 0 reads the pass's input; every later block is updated and
@@ -604,7 +606,7 @@ void tc_solve_rows(Call& c, int k, const double* rk, const double* src, int64_t 
     // B = I: the column maxima go to the next Gram matrix (the oblique one
     // scans Z = L^T Q itself)
     unsigned long long* cm = c.lt ? nullptr : c.colmax;
-    if (cm) cudaMemsetAsync(cm, 0, sizeof(unsigned long long) * 128, c.s);
+    if (cm) cudaMemsetAsync(cm, 0, sizeof(unsigned long long) * 256, c.s);
     tick(c.s, SCQR3_KERNEL_PASS, k);
     launch_tc_fused(sm_count(), c.s, src, lds, dst, ldd, Pc, k, rk, cm, c.st);
     return;
@@ -673,14 +675,14 @@ void after_pass(Call& c, int k, const double* Q, int64_t ldq) {
 }
 
 void after_pass_gram(Call& c, int k, const double* Q, int64_t ldq, double* out) {
-  if (c.P.np == 256) {
-    tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
-    launch_gram256(c.grid, c.s, Q, ldq, c.P, k, c.partials, c.L.part_stride, c.st);
-  } else if (c.tc) {
+  if (c.tc) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     // the mixed form keeps float pairs between passes
     launch_tc_gram(c.L.tc_grid, sm_count(), c.s, Q, ldq, c.P, k, c.colmax, c.partials, c.L.part_stride, c.st,
                    c.mixed ? 1 : 0, c.lt, 0, (use_fused(c) && !c.lt) ? 0 : 1);
+  } else if (c.P.np == 256) {
+    tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
+    launch_gram256(c.grid, c.s, Q, ldq, c.P, k, c.partials, c.L.part_stride, c.st);
   } else if (c.csr) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     launch_csr_gram(c.P.np, c.L.csr_grid, c.s, Q, ldq, c.P, k, c.B, c.partials, c.L.part_stride, c.st);

@@ -78,7 +78,7 @@ namespace scqr3 {
 namespace tc {
 
 constexpr int BW = 64;              // columns of one operand block
-constexpr int NPMAX = 128;          // largest padded n
+constexpr int NPMAX = 256;          // largest padded n
 constexpr int GROUP = 1024;         // rows per read-back group
 constexpr int THREADS = 256;   // slicer and read-back threads (the producer warp comes on top)
 constexpr uint32_t LBO = 128;       // K-direction core-matrix stride
@@ -95,7 +95,7 @@ struct ChunkGeo {
   static constexpr int BREG = 8 * PLANE;       // the B operand's planes (off-diagonal block)
 };
 static_assert(8 * ChunkGeo<64>::PLANE == STAGE && 16 * ChunkGeo<32>::PLANE == STAGE, "stage size");
-static_assert(32 * NPMAX * 8 == XSTAGE && 64 * 64 * 8 == XSTAGE, "staging size");
+static_assert(32 * 128 * 8 == XSTAGE && 64 * 64 * 8 == XSTAGE, "staging size (bulk copies for n <= 128)");
 
 template <int KC>
 __device__ __forceinline__ uint64_t desc(uint32_t addr) {
@@ -150,15 +150,15 @@ __device__ __forceinline__ void issue_k(uint64_t dbase, uint32_t tmem, uint32_t 
 // patterns of non-negative doubles order like the numbers; an Inf or NaN
 // entry, exponent field all ones, orders above every finite one, so
 // colmax[j] is then non-finite) over rows [0, m) of src. Integer operations
-// only: the FP64 pipe is the slow one. Thread t serves column t % nc (nc = 64
-// or 128 >= n) and row t / nc of each group of 256 / nc rows.
+// only: the FP64 pipe is the slow one. Thread t serves column t % nc (nc = 64,
+// 128 or 256 >= n) and row t / nc of each group of 256 / nc rows.
 __global__ void __launch_bounds__(256)
 colmax_kernel(const double* __restrict__ src, int64_t lds, int64_t m, int n, int pass,
               unsigned long long* __restrict__ colmax, const DevState* __restrict__ st, int pairs) {
   if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
   __shared__ unsigned long long red[256];
   const int tid = threadIdx.x;
-  const int nc = n > 64 ? 128 : 64, rs = 256 / nc;
+  const int nc = n > 128 ? 256 : n > 64 ? 128 : 64, rs = 256 / nc;
   const int j = tid % nc, r0 = tid / nc;
   const unsigned long long* s64 = reinterpret_cast<const unsigned long long*>(src);
   // pairs: the max of |hi| (the float's pattern in the low word; the Gram
@@ -278,7 +278,7 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   using namespace tc;
   using GK = ChunkGeo<KC>;
   constexpr int CHUNKS = GK::CHUNKS;
-  constexpr int NPK = KC == 64 ? 64 : 128;  // packed layout of the slots
+  const int NPK = KC == 64 ? 64 : P.np;  // packed layout of the slots (64, 128 or 256)
   if (pass >= 0 && !(st->run_trsm[pass] && st->gram_after[pass])) return;
   extern __shared__ uint8_t dsm[];
   uint8_t* stages = (uint8_t*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
@@ -297,17 +297,31 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   const int64_t m = P.m;
   double* part = partials + (int64_t)blockIdx.x * part_stride;
 
-  // this CTA's block (cj, ck), its ordinal among the CTAs of the block, and their count
+  // this CTA's block (cj, ck), its ordinal among the CTAs of the block, and
+  // their count: nd = NPK / 64 diagonal blocks of gd CTAs each, then the
+  // nd (nd - 1) / 2 off-diagonal blocks (0,1), (0,2), .., (1,2), .. sharing
+  // the rest evenly (the last one takes the remainder)
   int cj = 0, ck = 0, cta = blockIdx.x, ncta = gridDim.x;
   if (KC == 32) {
-    ncta = gd;
-    if (blockIdx.x >= 2 * gd) {
-      ck = 1;
-      cta = blockIdx.x - 2 * gd;
-      ncta = gridDim.x - 2 * gd;
-    } else if (blockIdx.x >= gd) {
-      cj = ck = 1;
-      cta = blockIdx.x - gd;
+    const int nd = NPK / BW, no = nd * (nd - 1) / 2;
+    if ((int)blockIdx.x < nd * gd) {
+      cj = ck = blockIdx.x / gd;
+      cta = blockIdx.x % gd;
+      ncta = gd;
+    } else {
+      const int r = blockIdx.x - nd * gd, rest = gridDim.x - nd * gd, go = rest / no;
+      int p = go > 0 ? r / go : no - 1;
+      if (p > no - 1) p = no - 1;
+      cta = r - p * go;
+      ncta = p == no - 1 ? rest - p * go : go;
+      for (int a = 0, q = p; a < nd; ++a) {
+        if (q < nd - 1 - a) {
+          cj = a;
+          ck = a + 1 + q;
+          break;
+        }
+        q -= nd - 1 - a;
+      }
     }
   }
   const bool offd = cj != ck;
@@ -619,11 +633,11 @@ cudaError_t tc_setup() {
 int tc_groups(int64_t m) { return (int)((m + tc::GROUP - 1) / tc::GROUP); }
 
 // CTAs of the tensor-core Gram of m rows (np = 64: one block; np = 128: three
-// blocks, at least one CTA each).
+// blocks, np = 256: ten, at least one CTA each).
 int tc_grid(int64_t m, int np, int sms) {
   const int64_t g = tc_groups(m);
   if (np <= 64) return (int)(g < sms ? (g < 1 ? 1 : g) : sms);
-  const int64_t t = 3 * (g < 1 ? 1 : g);
+  const int64_t t = (np <= 128 ? 3 : 10) * (g < 1 ? 1 : g);
   return (int)(t < sms ? t : sms);
 }
 
@@ -635,10 +649,12 @@ int tc_grid(int64_t m, int np, int sms) {
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
                     const double* lt, int64_t blk0, int scan) {
-  // the slots hold the packed np x np layout; np = 128 needs a CTA per block
-  if ((P.np != 64 && P.np != 128) || part_stride != pk_size(P.np) + 1 || (P.np == 128 && grid < 3)) return;
+  // the slots hold the packed np x np layout; np = 128 and 256 need a CTA per
+  // block (3 and 10 blocks)
+  const int nblk = P.np == 256 ? 10 : P.np == 128 ? 3 : 1;
+  if ((P.np != 64 && P.np != 128 && P.np != 256) || part_stride != pk_size(P.np) + 1 || grid < nblk) return;
   if (scan) cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * tc::NPMAX, s);
-  const int rs = P.n > 64 ? 2 : 4;
+  const int rs = P.n > 128 ? 1 : P.n > 64 ? 2 : 4;
   const int64_t want = (P.m + rs - 1) / rs;
   const int cg = (int)(want < (int64_t)sms * 8 ? (want < 1 ? 1 : want) : (int64_t)sms * 8);
   if (!scan) {
@@ -652,7 +668,7 @@ void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_
   }
   // bulk copies need contiguous rows, 16-byte aligned, and chunk sizes that are
   // multiples of 16 bytes (m n even)
-  const int bulk = (lds == P.n && ((uintptr_t)src & 15) == 0 && ((P.m * P.n) & 1) == 0) ? 1 : 0;
+  const int bulk = (P.n <= 128 && lds == P.n && ((uintptr_t)src & 15) == 0 && ((P.m * P.n) & 1) == 0) ? 1 : 0;
   const bool obl = P.bs > 0;
   if (P.np == 64) {
     if (obl)
@@ -663,11 +679,13 @@ void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_
                                                                          part_stride, st, bulk, pairs, grid, lt, blk0);
     return;
   }
-  // np = 128: gd CTAs for each diagonal block, the rest (which also cut twice
-  // the columns) for the off-diagonal one
+  // np = 128 (256): gd CTAs for each of the 2 (4) diagonal blocks, the rest
+  // (which also cut twice the columns) for the 1 (6) off-diagonal ones
   const int g = tc_groups(P.m);
-  int gd = grid >= 3 * g ? g : (3 * grid) / 10;
+  const int nd = P.np / 64, no = nd * (nd - 1) / 2;
+  int gd = grid >= (nd + no) * g ? g : (10 * grid) / (10 * nd + 12 * no);
   if (gd < 1) gd = 1;
+  if (grid - nd * gd < no) gd = (grid - no) / nd;  // every block gets a CTA (grid >= nblk)
   if (obl)
     tc_gram_kernel<32, true><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials,
                                                                       part_stride, st, bulk, pairs, gd, lt, blk0);

@@ -12,7 +12,7 @@ import os
 from dataclasses import dataclass, field
 
 MAX_PASSES = 8
-MAX_N = 256  # largest n (FP64, B = I); the other forms take n <= 128
+MAX_N = 256  # largest n (FP64 and tensor-core forms, B = I); the other forms take n <= 128
 
 OK = 0
 E_NONFINITE = -100
@@ -207,8 +207,8 @@ def _b_struct(B, normb):
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_TC = 2  # FP64-accurate: the Gram matrices and the substitution's off-diagonal blocks on the
-             # BF16 tensor cores (exact digit split), FP64 diagonal blocks; n <= 128, B = I or
-             # block-diagonal with blocks of 1, 2, 4 or 8 rows
+             # BF16 tensor cores (exact digit split), FP64 diagonal blocks; n <= 256 with B = I, or
+             # n <= 128 with B block-diagonal with blocks of 1, 2, 4 or 8 rows
 PREC_MIXED_TC = 3  # the mixed form's substitution with the tensor-core Gram matrices
 NORM_X2_TWO_EST = -1.0  # norm_x2 value: ||Q||_2^2 of each shifted pass estimated by the power method
 ALG_ADAPTIVE = 2  # Alg. 2: shift only on breakdown, stop on the orthogonality test

@@ -76,11 +76,17 @@ def test_argument_errors_are_reported_on_the_host(lib):
     assert lib.scqr3_workspace_bytes(30, 5, None, ctypes.byref(o), ctypes.byref(out)) == -12
     # n beyond the FP64 path
     assert lib.scqr3_workspace_bytes(1000, 300, None, None, ctypes.byref(out)) == scqr3.E_UNSUPPORTED
-    # the tensor-core Gram: n <= 128, B = I, m <= 2^31
+    # the tensor-core Gram: n <= 128 (n <= 256 for the FP64-accurate form with
+    # B = I), m <= 2^31
     for prec in (scqr3.PREC_TC, scqr3.PREC_MIXED_TC):
         o = scqr3._Opts(0, prec, 0.0)
-        assert lib.scqr3_workspace_bytes(1000, 129, None, ctypes.byref(o), ctypes.byref(out)) == \
+        assert lib.scqr3_workspace_bytes(1000, 257, None, ctypes.byref(o), ctypes.byref(out)) == \
             scqr3.E_UNSUPPORTED
+        r129 = lib.scqr3_workspace_bytes(1000, 129, None, ctypes.byref(o), ctypes.byref(out))
+        if prec == scqr3.PREC_TC:  # accepted (the size needs the device: E_CUDA on a host without one)
+            assert r129 in (0, scqr3.E_CUDA)
+        else:
+            assert r129 == scqr3.E_UNSUPPORTED
         assert lib.scqr3_workspace_bytes(2 ** 31 + 1, 8, None, ctypes.byref(o), ctypes.byref(out)) == \
             scqr3.E_UNSUPPORTED
         b = scqr3._B(16, ctypes.c_void_p(8), 0.0)  # blocks of 16 rows: FP64 only

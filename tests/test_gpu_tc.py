@@ -64,6 +64,43 @@ def test_shape_sweep(n, m_kind):
     check(Xh, 1e6)
 
 
+@pytest.mark.parametrize("n", [129, 160, 192, 200, 255, 256])
+@pytest.mark.parametrize("m_kind", ["square", "ragged", "tall"])
+def test_wide_shape_sweep(n, m_kind):
+    """128 < n <= 256: the Gram matrix as the ten 64-column block pairs (four
+    diagonal, six off-diagonal) on separate CTA sets, the substitution in
+    32-column diagonal blocks with the off-diagonal products on the tensor
+    cores (up to 28 update launches per pass)."""
+    m = {"square": n, "ragged": 20011, "tall": 60013}[m_kind]
+    Xh = testmat(m, n, 1e6, seed=6300 + n + m)
+    check(Xh, 1e6)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e10, 1e15])
+def test_wide_conditioning(kappa):
+    Xh = testmat(30011, 256, kappa, seed=6350)
+    info, tr = check(Xh, kappa)
+    if kappa <= 1e8:
+        assert info.passes == tr["passes"]
+
+
+def test_wide_matches_fp64_form():
+    """n = 256 at 500,000 rows (each block pair's CTAs cover about 50 groups
+    of 1024 rows): R within 1e-14 of the FP64 DFMA form, orthogonality and
+    residual at the FP64 tolerances."""
+    Xh = testmat(500000, 256, 1e8, seed=6360)
+    X = torch.from_numpy(Xh).cuda()
+    Qt, Rt, it = scqr3.factor(X, precision=TC)
+    Qf, Rf, i_f = scqr3.factor(X)
+    torch.cuda.synchronize()
+    assert it.status == 0 and i_f.status == 0 and it.passes == i_f.passes
+    Rt, Rf = Rt.cpu().numpy(), Rf.cpu().numpy()
+    assert np.linalg.norm(Rt - Rf) / np.linalg.norm(Rf) <= 1e-14
+    Qt = Qt.cpu().numpy()
+    assert np.linalg.norm(Qt.T @ Qt - np.eye(256), 2) <= 1e-13
+    assert np.linalg.norm(Xh - Qt @ Rt) / np.linalg.norm(Xh) <= 1e-13
+
+
 @pytest.mark.parametrize("kappa", [1e2, 1e8, 1e12, 1e15])
 def test_conditioning(kappa):
     """The pass structure follows the oracle's where the decisions are not
@@ -149,7 +186,9 @@ def test_non_finite_and_rejections():
     _, _, info = run(Xh)
     assert info.status == scqr3.E_NONFINITE
     with pytest.raises(scqr3.ScqrError):
-        scqr3.factor(torch.zeros((1000, 129), dtype=torch.float64, device="cuda"), precision=TC)
+        scqr3.factor(torch.zeros((1000, 257), dtype=torch.float64, device="cuda"), precision=TC)
+    with pytest.raises(scqr3.ScqrError):
+        scqr3.factor(torch.zeros((1000, 129), dtype=torch.float64, device="cuda"), precision=scqr3.PREC_MIXED_TC)
     Xh = testmat(5000, 100, 1e4, seed=6501)
     Xh[4321, 99] = np.nan  # a column of the second block
     _, _, info = run(Xh)
