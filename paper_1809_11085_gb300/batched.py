@@ -56,11 +56,19 @@ class BatchedQR:
     Allocates Q_i, R_i (and the per-pass R_k if keep_rpass) and the workspace,
     builds and uploads the plan; run() queues the whole batch (or replays its
     CUDA graph when graph=True).
+
+    precision = scqr3.PREC_FP64 (default) runs the batched kernels of
+    scqr3_factor_batched (persistent tile queues over all matrices, FP64).
+    precision = scqr3.PREC_TC (or PREC_MIXED_TC) queues one scqr3_factor call
+    per matrix with that precision, in order on the stream and on one shared
+    workspace (sized for the largest matrix; the calls follow one another on
+    the stream, so they never use it at the same time); with graph=True the
+    whole sequence is captured once and replayed as one CUDA graph.
     """
 
     def __init__(self, Xs, *, tune=None, max_passes: int = 0, keep_rpass: bool = False,
                  in_place: bool = False, graph: bool = False, shift_scale: float = 0.0,
-                 algorithm: int = 3, tol: float = 0.0):
+                 algorithm: int = 3, tol: float = 0.0, precision: int = scqr3.PREC_FP64):
         import torch
 
         self.Xs = list(Xs)
@@ -75,6 +83,30 @@ class BatchedQR:
         self.Rpass = ([torch.zeros((MAX_PASSES, X.shape[1], X.shape[1]), dtype=torch.float64, device=dev)
                        for X in self.Xs] if keep_rpass else None)
         self.info_buf = torch.zeros((self.count, INFO_BYTES), dtype=torch.uint8, device=dev)
+        self.precision = int(precision)
+        self._plan = None
+        self.graph = None
+        if self.precision != scqr3.PREC_FP64:
+            # one scqr3_factor call per matrix on one shared workspace
+            nbytes = max(scqr3.workspace_bytes(X.shape[0], X.shape[1], None, max_passes) for X in self.Xs)
+            self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+            self.ws_ptr = (self.ws.data_ptr() + 255) & ~255
+            self._opts = scqr3._Opts(int(max_passes), self.precision, 0.0, float(shift_scale), int(algorithm),
+                                     float(tol))
+            self._calls = [(X.data_ptr(), X.shape[0], X.shape[1], X.stride(0), None, self.Qs[i].data_ptr(),
+                            self.Qs[i].stride(0), self.Rs[i].data_ptr(),
+                            self.Rpass[i].data_ptr() if keep_rpass else None, self.ws_ptr, nbytes,
+                            ctypes.byref(self._opts), self.info_buf[i].data_ptr())
+                           for i, X in enumerate(self.Xs)]
+            self.tune = None
+            if graph:
+                self._launch()  # warm-up (and the library's one-time set-up) outside capture
+                torch.cuda.synchronize(dev)
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    self._launch()
+                self.graph = g
+            return
         items = (_Item * self.count)()
         for i, X in enumerate(self.Xs):
             items[i] = _Item(X.data_ptr(), self.Qs[i].data_ptr(), self.Rs[i].data_ptr(),
@@ -111,6 +143,13 @@ class BatchedQR:
         import torch
 
         stream = torch.cuda.current_stream(self.Xs[0].device).cuda_stream
+        if self.precision != scqr3.PREC_FP64:
+            f = lib().scqr3_factor
+            for a in self._calls:
+                r = f(*a, ctypes.c_void_p(stream))
+                if r != OK:
+                    raise ScqrError(r, "scqr3_factor")
+            return
         r = _bind().scqr3_factor_batched(self._plan, ctypes.c_void_p(stream))
         if r != OK:
             raise ScqrError(r, "scqr3_factor_batched")

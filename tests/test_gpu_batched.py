@@ -196,3 +196,39 @@ def test_batch_options_alg2_and_small_shift():
             m, n = xh.shape
             tol = 6 * (m * n + n * (n + 1)) * U if "algorithm" in opts else 1e-13
             assert orth2(Q.cpu().numpy()) <= tol
+
+
+@pytest.mark.parametrize("prec", [scqr3.PREC_TC, scqr3.PREC_MIXED_TC])
+def test_tensor_core_batch_graph(prec):
+    """precision = PREC_TC / PREC_MIXED_TC: one scqr3_factor call per matrix on
+    one shared workspace, captured as one CUDA graph. Each matrix equals the
+    single call of that precision bit for bit (the same kernels and sums; the
+    shared workspace is larger than a single shape needs, which changes no
+    layout), every replay reproduces it, and every matrix meets the FP64
+    tolerances against the oracle (the mixed form its own, looser residual)."""
+    mats = mixed_batch(5600) + [(testmat(6000, 200, 1e8, seed=5650), 1e8)] if prec == scqr3.PREC_TC \
+        else mixed_batch(5600)
+    Xs = [torch.from_numpy(x).cuda() for x, _ in mats]
+    g = batched.BatchedQR(Xs, graph=True, precision=prec)
+    for rep in range(2):
+        for Q in g.Qs:
+            Q.fill_(float("nan"))
+        g.run()
+        torch.cuda.synchronize()
+        infos = g.infos()
+        for (xh, kappa), X, Qb, Rb, inf in zip(mats, Xs, g.Qs, g.Rs, infos):
+            assert inf.status == 0
+            Q1, R1, i1 = scqr3.factor(X, precision=prec)
+            torch.cuda.synchronize()
+            assert i1.passes == inf.passes
+            assert torch.equal(Qb, Q1) and torch.equal(Rb, R1)
+            if rep == 0:
+                n = xh.shape[1]
+                Qh, Rh = Qb.cpu().numpy(), Rb.cpu().numpy()
+                _, Ro, st, _ = oracle.scqr3(xh)
+                assert st == 0
+                assert orth2(Qh) <= 1e-13
+                res = np.linalg.norm(xh - Qh @ Rh) / np.linalg.norm(xh)
+                assert res <= (1e-13 if prec == scqr3.PREC_TC else 64 * n * 2.0 ** -48)
+                tol = max(1e-12, 100 * n * kappa * (U if prec == scqr3.PREC_TC else 2.0 ** -48))
+                assert np.linalg.norm(Rh - Ro) / np.linalg.norm(Ro) <= tol

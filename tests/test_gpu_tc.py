@@ -101,6 +101,51 @@ def test_wide_matches_fp64_form():
     assert np.linalg.norm(Xh - Qt @ Rt) / np.linalg.norm(Xh) <= 1e-13
 
 
+def test_wide_host_form_and_shards():
+    """n = 200 through the host-buffer entry point (row-chunked copies, the
+    first Gram matrix per chunk) and through the row-partitioned calls
+    (uneven blocks, Gram shares summed between the calls): both meet the FP64
+    tolerances and match scqr3_factor's R to rounding."""
+    m, n = 300000, 200
+    Xh = testmat(m, n, 1e6, seed=6370)
+    X = torch.from_numpy(Xh).cuda()
+    Q1, R1, i1 = scqr3.factor(X, precision=TC)
+    torch.cuda.synchronize()
+    R1 = R1.cpu().numpy()
+    Qh, Rh, ih = scqr3.factor_host(torch.from_numpy(Xh).pin_memory(), precision=TC)
+    assert ih.status == 0 and ih.passes == i1.passes
+    Qh, Rh = Qh.numpy(), Rh.numpy()
+    assert np.linalg.norm(Qh.T @ Qh - np.eye(n), 2) <= 1e-13
+    assert np.linalg.norm(Xh - Qh @ Rh) / np.linalg.norm(Xh) <= 1e-13
+    assert np.linalg.norm(Rh - R1) / np.linalg.norm(R1) <= 1e-12
+    bounds = [0, 70001, 70009, 210000, m]
+    Xs = [X[a:b] for a, b in zip(bounds[:-1], bounds[1:])]
+    wss = [scqr3.ShardWorkspace(b - a, n, None, 0.0, TC, 0) for a, b in zip(bounds[:-1], bounds[1:])]
+    Qs = [torch.empty_like(x) for x in Xs]
+    Rs = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in Xs]
+    for x, ws in zip(Xs, wss):
+        scqr3.gram_partial(x, ws, precision=TC)
+    G = sum(ws.G for ws in wss)
+    for k in range(6):
+        for ws in wss:
+            ws.G.copy_(G)
+        for x, q, r, ws in zip(Xs, Qs, Rs, wss):
+            scqr3.apply_pass(k, m, x, q, r, ws, precision=TC)
+        torch.cuda.synchronize()
+        inf = scqr3.Info.from_bytes(wss[0].info.cpu().numpy().tobytes())
+        assert inf.status == 0
+        if not inf.more:
+            break
+        G = sum(ws.G_next for ws in wss)
+    Qs = torch.cat(Qs).cpu().numpy()
+    Rs0 = Rs[0].cpu().numpy()
+    for r in Rs[1:]:
+        assert np.array_equal(r.cpu().numpy(), Rs0)
+    assert np.linalg.norm(Qs.T @ Qs - np.eye(n), 2) <= 1e-13
+    assert np.linalg.norm(Xh - Qs @ Rs0) / np.linalg.norm(Xh) <= 1e-13
+    assert np.linalg.norm(Rs0 - R1) / np.linalg.norm(R1) <= 1e-12
+
+
 @pytest.mark.parametrize("kappa", [1e2, 1e8, 1e12, 1e15])
 def test_conditioning(kappa):
     """The pass structure follows the oracle's where the decisions are not
