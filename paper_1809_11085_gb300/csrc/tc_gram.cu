@@ -18,14 +18,16 @@
 //    four digit pairs (4 * 1024 * 64^2 = 2^24);
 //  * D_d = sum over digit pairs (s, t) with s + t = d, d = 0 .. 7, is read back
 //    from tensor memory every 1024 rows (in two shares, lanes 0..63 of tile d
-//    and lanes 64..127 of tile d - 1, added at the end). The digit sums are exact integers, so
-//    U = D_0 2^21 + D_1 2^14 + D_2 2^7 + D_3 and T = D_4 2^21 + ... + D_7
-//    (per 1024 rows below 2^45.1) are accumulated exactly in int64 over all
-//    of a CTA's rows (below 2^63 up to 2^27.9 rows per CTA; a 288 GB device
-//    holds at most 2^28 rows of 128 columns, spread over at least 45 CTAs per
-//    block), and only the final 2^-35 U + 2^-63 T is formed in FP64: the FP64
-//    pipe, the scarce one, does no work per row. Pairs with s + t > 7 (at
-//    most 7 * 2^12 * 2^-70 < 2^-55 of sigma_j sigma_k per row, zero mean) are
+//    and lanes 64..127 of tile d - 1, added at the end). The digit sums are
+//    exact integers, so U = D_0 2^21 + D_1 2^14 + D_2 2^7 + D_3 and
+//    T = D_4 2^21 + ... + D_7 (per 1024 rows and share below 2^45.1) are
+//    exact in int64; W = 2^17 U + round(T / 2^11) (below 2^62.2; the rounding
+//    of T costs at most 2^-53 sigma_j sigma_k per group, zero mean) is the
+//    group's 2^-35 U + 2^-63 T in units of 2^-52 sigma_j sigma_k, converted to
+//    FP64 once per group and added up in FP64 over the CTA's groups (an FP64
+//    sum of about m / 1024 terms, far inside the bound below). The FP64 pipe,
+//    the scarce one, does no work per row. Pairs with s + t > 7 (at most
+//    7 * 2^12 * 2^-70 < 2^-55 of sigma_j sigma_k per row, zero mean) are
 //    dropped.
 //
 // The result differs from q_j^T q_k by at most about m 2^-54 sigma_j sigma_k
@@ -396,11 +398,14 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   // values (one column, tid % 64), the square pair (4, 4) of d = 8 that the
   // tiles do not hold; added to the diagonal it keeps the split unbiased there
   long long s44 = 0;
-  // exact digit-sum accumulators of this thread's 32 entries: U (d = 0..3)
-  // and T (d = 4..7)
-  long long U[CW], T[CW];
+  // this thread's share of its 32 entries, in units of 2^-52 sigma_j sigma_k:
+  // per 1024-row group the digit sums fold exactly into U (d = 0..3) and
+  // T (d = 4..7), both below 2^45.1; W = 2^17 U + round(T / 2^11) (below
+  // 2^62.2, so 2^-35 U + 2^-63 T to within 2^-53 of sigma_j sigma_k) goes to
+  // FP64 once per group, and the groups add up in FP64
+  double acc[CW];
 #pragma unroll
-  for (int k = 0; k < CW; ++k) U[k] = T[k] = 0;
+  for (int k = 0; k < CW; ++k) acc[k] = 0.0;
 
   uint32_t issued = 0;     // producer: chunks whose rows were requested
   uint32_t committed = 0;  // producer: chunks whose MMAs were committed
@@ -462,6 +467,50 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
       }
       uint8_t* sb = stages + stg * STAGE;
       const double* xs = (const double*)(xst + stg * XSTAGE);
+      if constexpr (!OBL) {
+        // two units per thread at a time (the second empty when units run
+        // out), so that their integer work interleaves
+        for (int u = tid; u < units; u += 2 * THREADS) {
+          const bool two = u + THREADS < units;
+          unsigned long long F[2][8];
+          int jj[2], igg[2];
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int uu = u + h2 * THREADS;
+            const bool live = h2 == 0 || two;
+            const int j = uu & ((1 << lgc) - 1), ig = uu >> lgc;
+            jj[h2] = j;
+            igg[h2] = ig;
+            const int col = j < BW ? colA + j : colB + (j - BW);
+            const int E = Esh[col < NPMAX ? col : 0];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              const int i = ig * 8 + r;
+              double x = 0.0;
+              if (live && col < n && i < rows) x = bulk ? xs[i * n + col] : src[(row0 + i) * lds + col];
+              F[h2][r] = pairs ? tc::biased56_pair((unsigned long long)__double_as_longlong(x), E)
+                               : tc::biased56(x, E);
+            }
+          }
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            if (h2 == 1 && !two) break;
+            if (!offd) {
+#pragma unroll
+              for (int r = 0; r < 8; ++r) {
+                const int d4 = (int)((F[h2][r] >> 21) & 127) - 64;
+                s44 += d4 * d4;
+              }
+            }
+            const int j = jj[h2];
+            uint8_t* dst = sb + (j >> 6) * GK::BREG + ((j & 63) >> 3) * GK::SBO + igg[h2] * LBO + (j & 7) * 16;
+            uint4 w[8];
+            tc::planes8(F[h2], w);
+#pragma unroll
+            for (int sd = 0; sd < 8; ++sd) *(uint4*)(dst + tc::plane_off<KC>(sd)) = w[sd];
+          }
+        }
+      } else
       for (int u = tid; u < units; u += THREADS) {
         const int j = u & ((1 << lgc) - 1), ig = u >> lgc;
         const int col = j < BW ? colA + j : colB + (j - BW);
@@ -530,6 +579,9 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
           // upper rows hold d = e (tiles 0..7), lower rows d = e + 1 (tiles
           // 0..6; tile 7 would be d = 8). D_d enters U with weight
           // 2^(7 (3 - d)) (d <= 3) or T with weight 2^(7 (7 - d)).
+          long long U[8], T[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) U[k] = T[k] = 0;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             if (!upper && e == 7) break;
@@ -541,10 +593,13 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
               const long long dv = (long long)__float2int_rn(__uint_as_float(v[k])) << sh;
-              if (d < 4) U[c + k] += dv;
-              else T[c + k] += dv;
+              if (d < 4) U[k] += dv;
+              else T[k] += dv;
             }
           }
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            acc[c + k] += (double)((long long)((unsigned long long)U[k] << 17) + ((T[k] + 1024) >> 11));
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -564,15 +619,11 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
   // rows 64..127 hold the d + 1 share of the same entries: add them to rows 0..63
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  long long* xch = (long long*)stages;  // 64 x 64 int64 T shares (32 KB) of stage 0,
-  long long* xchu = xch + BW * BW;      // then the U shares (32 KB)
-  long long* s44sh = xchu + BW * BW;    // then the slicers' digit-4 square sums
+  double* xch = (double*)stages;                    // 64 x 64 shares (32 KB) of stage 0,
+  long long* s44sh = (long long*)(xch + BW * BW);  // then the slicers' digit-4 square sums
   if (!producer && !upper) {
 #pragma unroll
-    for (int k = 0; k < CW; ++k) {
-      xch[jr * BW + CW * h + k] = T[k];
-      xchu[jr * BW + CW * h + k] = U[k];
-    }
+    for (int k = 0; k < CW; ++k) xch[jr * BW + CW * h + k] = acc[k];
   }
   if (!producer) s44sh[tid] = s44;
   __syncthreads();
@@ -582,7 +633,7 @@ tc_gram_kernel(const double* __restrict__ src, int64_t lds, Params P, int pass,
     for (int k = 0; k < CW; ++k) {
       const int c = CW * h + k;
       if (offd || c >= jr) {
-        double a = fma(0x1p-35, (double)(U[k] + xchu[jr * BW + c]), 0x1p-63 * (double)(T[k] + xch[jr * BW + c]));
+        double a = 0x1p-52 * (acc[k] + xch[jr * BW + c]);
         if (!offd && c == jr) {  // the diagonal: the square pair (4, 4), weight 2^-70
           long long q = 0;
           for (int t = jr; t < THREADS; t += BW) q += s44sh[t];

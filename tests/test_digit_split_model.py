@@ -408,3 +408,23 @@ def test_gram_mma_program_covers_each_pair_once():
     assert set(read) == want and all(c == 1 for c in read.values())
     # the bench's flop count: N adds up to 1280 per K step
     assert sum(64 * nt for _, _, nt in program) == 1280
+
+
+def test_gram_group_value_fits_and_rounds():
+    """Per 1024-row group the Gram kernel folds its exact digit sums into
+    U = sum_{d<=3} D_d 2^(7(3-d)) and T = sum_{d>=4} D_d 2^(7(7-d)) (|D_d| <=
+    4 * 1024 * 64^2 = 2^24 per share) and converts W = 2^17 U + round(T / 2^11)
+    to FP64: W stays below 2^62.2 (int64), and W 2^-52 differs from
+    2^-35 U + 2^-63 T by at most 2^-53 (in units of sigma_j sigma_k)."""
+    G = 4 * 1024 * 64 * 64
+    rng = np.random.default_rng(24)
+    cases = [[G] * 8, [-G] * 8, [G, -G] * 4] + [list(rng.integers(-G, G + 1, 8)) for _ in range(3000)]
+    for D in cases:
+        D = [int(d) for d in D]
+        U = sum(D[e] * 2 ** (7 * (3 - e)) for e in range(4))
+        T = sum(D[e] * 2 ** (7 * (7 - e)) for e in range(4, 8))
+        assert abs(U) < 2 ** 45.1 and abs(T) < 2 ** 45.1
+        W = (U << 17) + ((T + 1024) >> 11)
+        assert abs(W) < 2 ** 62.2
+        exact = Fraction(U, 2 ** 35) + Fraction(T, 2 ** 63)
+        assert abs(Fraction(W, 2 ** 52) - exact) <= Fraction(1, 2 ** 53)
