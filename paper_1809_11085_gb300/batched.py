@@ -259,11 +259,13 @@ def autotune(Xs, candidates=(2, 4, 8, 16, 32), reps: int = 2, use_cache: bool = 
 
 # --------------------------------------------------------------------------- differentiable batch
 
-def qr_batched(Xs, tune=None):
+def qr_batched(Xs, tune=None, precision: int = scqr3.PREC_FP64):
     """Differentiable batched factorization: returns ([Q_i], [R_i]).
 
-    The forward pass is one batched launch sequence; the backward pass applies
-    the adjoint (scqr3_backward) to each matrix from its Q_i and per-pass R_k.
+    The forward pass is one batched launch sequence (precision as for
+    BatchedQR); the backward pass applies the adjoint (scqr3_backward) to each
+    matrix from its Q_i and per-pass R_k, all queued on the stream with one
+    workspace sized for the largest matrix.
     """
     import torch
 
@@ -273,7 +275,7 @@ def qr_batched(Xs, tune=None):
     class _Fn(torch.autograd.Function):
         @staticmethod
         def forward(ctx, *X):
-            b = BatchedQR([x.detach().contiguous() for x in X], tune=tune, keep_rpass=True)
+            b = BatchedQR([x.detach().contiguous() for x in X], tune=tune, keep_rpass=True, precision=precision)
             b.run()
             infos = b.infos()
             for i, inf in enumerate(infos):
@@ -288,10 +290,12 @@ def qr_batched(Xs, tune=None):
             saved = ctx.saved_tensors
             Qs, Rps = saved[:n], saved[n:]
             dQs, dRs = grads[:n], grads[n:]
+            big = max(range(n), key=lambda i: scqr3.backward_workspace_bytes(*Qs[i].shape))
+            ws = scqr3.BackwardWorkspace(*Qs[big].shape, device=Qs[big].device)
             out = []
             for i in range(n):
                 dQ = dQs[i] if dQs[i] is not None else torch.zeros_like(Qs[i])
-                out.append(scqr3.backward(Qs[i], Rps[i], ctx.passes[i], dQ.contiguous(), dRs[i]))
+                out.append(scqr3.backward(Qs[i], Rps[i], ctx.passes[i], dQ.contiguous(), dRs[i], workspace=ws))
             return tuple(out)
 
     res = _Fn.apply(*Xs)

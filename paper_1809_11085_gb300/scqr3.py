@@ -371,6 +371,14 @@ def timing_end(capacity: int = 4096):
 
 # --------------------------------------------------------------------------- adjoint
 
+def backward_workspace_bytes(m: int, n: int) -> int:
+    out = ctypes.c_size_t(0)
+    r = lib().scqr3_backward_workspace_bytes(int(m), int(n), ctypes.byref(out))
+    if r != OK:
+        raise ScqrError(r, "scqr3_backward_workspace_bytes")
+    return out.value
+
+
 class BackwardWorkspace:
     def __init__(self, m, n, device=None):
         import torch
