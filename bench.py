@@ -909,7 +909,17 @@ def extra_legs(torch, dev, stream, args):
     legs["backward"] = {"workload": "adjoint of the 16777216 x 64 factorization (3 passes)", "ms": round(ms, 2),
                         "rows_per_s": mm / (ms * 1e-3),
                         "tflops": inf.passes * mm * 6 * nn * nn / (ms * 1e-3) / 1e12}
-    del Q, R, dQ, dX, bws, Rpass
+    del bws
+    free()
+    # the same adjoint with its row work on the tensor cores
+    bwt = scqr3.BackwardWorkspace(mm, nn, device=dev, precision=scqr3.PREC_TC)
+    dXt = torch.empty_like(Q)
+    mst = _time(torch, stream, lambda: scqr3.backward(Q, Rpass, inf.passes, dQ, dR, dX=dXt, workspace=bwt))
+    legs["backward"]["tc"] = {"ms": round(mst, 2), "rows_per_s": mm / (mst * 1e-3), "speedup": ms / mst,
+                              "status": bwt.last_status(),
+                              "dX_vs_fp64": (torch.linalg.matrix_norm(dXt - dX) /
+                                             torch.linalg.matrix_norm(dX)).item()}
+    del Q, R, dQ, dX, dXt, bwt, Rpass
     free()
 
     # batched: 512 uneven matrices, one graph vs 512 single calls

@@ -362,6 +362,35 @@ int scqr3_backward(const double *Q, int64_t m, int n, int64_t ldq,
                    int64_t lddq, const double *dR, double *dX, int64_t lddx,
                    void *workspace, size_t workspace_bytes, void *stream);
 
+/* The adjoint with options: opts->precision selects its form (opts NULL:
+ * SCQR3_PREC_FP64).
+ *  SCQR3_PREC_FP64  scqr3_backward (FP64 arithmetic throughout).
+ *  SCQR3_PREC_TC    the same chain rule with the row work on the tensor
+ *         cores, FP64-accurate like the factorization's SCQR3_PREC_TC form:
+ *         the iterate is held as Z = [Q_k | Qbar_k J] (J reverses the column
+ *         order); Qbar_k + 2 Q_k P_k and Q_{k-1} = Q_k R_k are products with
+ *         n x n matrices through the exact digit split (each product within
+ *         2^-56 of the scales of its row and column); Qbar_{k-1} R_k^T = t is
+ *         the row-wise substitution of Eq. (backward2) with U = J R_k^T J
+ *         applied to t J (FP64 diagonal blocks, backward stable row by row);
+ *         M_k J is the upper right block of the tensor-core Gram matrix of Z.
+ *         n <= 128, m <= 2^31 (else SCQR3_E_UNSUPPORTED). The workspace
+ *         holds two m x 2n iterates (16 m n doubles in all).
+ *  other values: SCQR3_E_UNSUPPORTED.
+ * The other arguments are scqr3_backward's (argument codes -1 .. -11 the
+ * same; opts is argument 12). status: NULL or a device int that receives,
+ * in stream order after the adjoint, SCQR3_OK or SCQR3_E_TIMEOUT (a
+ * tensor-core kernel gave up a bounded wait; dX is then not valid).
+ * scqr3_backward_workspace_bytes_ex: the workspace for (m, n, opts); the
+ * tensor-core form needs the device (SCQR3_E_CUDA without one). */
+int scqr3_backward_workspace_bytes_ex(int64_t m, int n, const scqr3_opts *opts,
+                                      size_t *bytes);
+int scqr3_backward_ex(const double *Q, int64_t m, int n, int64_t ldq,
+                      const double *Rpass, int passes, const double *dQ,
+                      int64_t lddq, const double *dR, double *dX, int64_t lddx,
+                      const scqr3_opts *opts, void *workspace,
+                      size_t workspace_bytes, int *status, void *stream);
+
 /* ---------------------------------------------------------------------------
  * scqr3_factor_noalloc: the same factorization (B = I, default options)
  * without a workspace argument, for callers that cannot allocate device

@@ -263,9 +263,10 @@ def qr_batched(Xs, tune=None, precision: int = scqr3.PREC_FP64):
     """Differentiable batched factorization: returns ([Q_i], [R_i]).
 
     The forward pass is one batched launch sequence (precision as for
-    BatchedQR); the backward pass applies the adjoint (scqr3_backward) to each
-    matrix from its Q_i and per-pass R_k, all queued on the stream with one
-    workspace sized for the largest matrix.
+    BatchedQR); the backward pass applies the adjoint (scqr3_backward_ex; on
+    the tensor cores after the PREC_TC form) to each matrix from its Q_i and
+    per-pass R_k, all queued on the stream with one workspace sized for the
+    largest matrix.
     """
     import torch
 
@@ -290,12 +291,15 @@ def qr_batched(Xs, tune=None, precision: int = scqr3.PREC_FP64):
             saved = ctx.saved_tensors
             Qs, Rps = saved[:n], saved[n:]
             dQs, dRs = grads[:n], grads[n:]
-            big = max(range(n), key=lambda i: scqr3.backward_workspace_bytes(*Qs[i].shape))
-            ws = scqr3.BackwardWorkspace(*Qs[big].shape, device=Qs[big].device)
+            bp = scqr3.backward_precision(precision)
+            big = max(range(n), key=lambda i: scqr3.backward_workspace_bytes(*Qs[i].shape, precision=bp))
+            ws = scqr3.BackwardWorkspace(*Qs[big].shape, device=Qs[big].device, precision=bp)
             out = []
             for i in range(n):
                 dQ = dQs[i] if dQs[i] is not None else torch.zeros_like(Qs[i])
                 out.append(scqr3.backward(Qs[i], Rps[i], ctx.passes[i], dQ.contiguous(), dRs[i], workspace=ws))
+            if bp != scqr3.PREC_FP64 and ws.last_status() != scqr3.OK:
+                raise ScqrError(ws.last_status(), "scqr3_backward_ex")
             return tuple(out)
 
     res = _Fn.apply(*Xs)

@@ -370,6 +370,256 @@ static void bw_small(int np, cudaStream_t s, int k, int P, int n, const double* 
   }
 }
 
+// -------------------------------------------------------------------------------------------
+// The tensor-core form (opts.precision = SCQR3_PREC_TC): the same chain rule,
+// with the row work run by the factorization's tensor-core kernels. The
+// iterate of pass k is held as Z = [Q_k | Qbar_k J] (m x 2n, row-major; J
+// reverses the order of the columns), and with t = Qbar_k + 2 Q_k P_k:
+//  * t J = Qbar_k J - Q_k Bt with Bt = -2 P_k J: tc_update_kernel's x - Y B
+//    with a dense B, each product exact to within 2^-56 of the scales of its
+//    row and column (the digit split of the factorization's substitution);
+//  * Qbar_{k-1} R_k^T = t is a back substitution; with U = J R_k^T J, upper
+//    triangular with the entries of R_k, it reads (Qbar_{k-1} J) U = t J: the
+//    row-wise substitution Q := X U^{-1} of Eq. (backward2) that the
+//    factorization runs (FP64 diagonal blocks, off-diagonal products on the
+//    tensor cores; one sweep for 16 < n <= 64), backward stable row by row;
+//  * Q_{k-1} = Q_k R_k: x - Y B with x = 0 and B = -R_k;
+//  * M_{k-1} J = Q_{k-1}^T (Qbar_{k-1} J) is the upper right block of the Gram
+//    matrix of the new Z, which the tensor-core Gram forms (2n <= 256 columns).
+// The n x n algebra is bw_small_kernel's. Pass k's kernels use pass slot 0 of
+// their own DevState, with every solve enabled and no Gram fused into it.
+
+void launch_pass(int np, int grid, cudaStream_t s, const double* src, int64_t lds, double* dst, int64_t ldd,
+                 const Params& P, int pass, const double* rk, const double* lt, double* partials, int part_stride,
+                 DevState* st);
+int tc_grid(int64_t m, int np, int sms);
+void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int w, int pass, const DevState* st,
+                       double* rdiag);
+void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t ldy, const double* x1,
+                      int64_t ldx, double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np,
+                      int r0, int c0, int ldb, int ky, DevState* st, long long wait_ns);
+void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
+                    unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
+                    const double* lt, int64_t blk0, int scan);
+void launch_tc_fused(int sms, cudaStream_t s, const double* X, int64_t ldx, double* Q, int64_t ldq, const Params& P,
+                     int pass, const double* rk, unsigned long long* colmax, DevState* st);
+void set_options(Params* P, const scqr3_opts* opts);
+int tc_kernels_ready(int* sms);
+int pass_kernel_grid(int np, int64_t m);
+bool fused_solve_selected(int n);
+
+__global__ void bwt_init_kernel(DevState* st) {
+  if (threadIdx.x != 0) return;
+  st->status = SCQR3_OK;
+  st->passes = 0;
+  st->plain_in_a_row = 0;
+  st->pad0 = 0;
+  for (int i = 0; i < SCQR3_MAX_PASSES; ++i) {
+    st->run_trsm[i] = 1;
+    st->gram_after[i] = 0;
+  }
+  st->normb = 0.0;
+  st->normb_bits_max = 0.0;
+}
+
+// mode 0: z = [a | b J] (a = Q, b = dQ); mode 1: dx = the right half of z in
+// natural column order (dX = Qbar_0).
+__global__ void bwt_pack_kernel(int mode, int64_t m, int n, const double* __restrict__ a, int64_t lda,
+                                const double* b, int64_t ldb, double* z, double* dx, int64_t lddx) {
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n;
+    const int c = (int)(e - i * n);
+    double* zr = z + i * 2 * n;
+    if (mode == 0) {
+      zr[c] = a[i * lda + c];
+      zr[2 * n - 1 - c] = b[i * ldb + c];
+    } else {
+      dx[i * lddx + c] = zr[2 * n - 1 - c];
+    }
+  }
+}
+
+// M (full np x np, zero padding) from the packed Gram matrix G (npz) of Z:
+// M(r, j) = G(r, 2n - 1 - j).
+__global__ void bwt_gram_to_m_kernel(const double* __restrict__ G, int npz, int n, int np, double* __restrict__ M) {
+  for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
+    const int r = e / np, j = e % np;
+    M[e] = (r < n && j < n) ? G[pk_idx(npz, r, 2 * n - 1 - j)] : 0.0;
+  }
+}
+
+// Pass k's matrices: Bt = -2 P_k J and Bq = -R_k (dense nb x nb, zero outside
+// n x n; P_k packed np, symmetric) and U = J R_k^T J packed nps x nps, the
+// identity in its padding: U(a, b) = R_k(n-1-b, n-1-a).
+__global__ void bwt_mats_kernel(int k, int n, const double* __restrict__ Rpass, const double* __restrict__ Pk,
+                                int np, int nb, double* __restrict__ Bt, double* __restrict__ Bq, int nps,
+                                double* __restrict__ U) {
+  const double* R = Rpass + (int64_t)(k - 1) * n * n;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int a = e / nb, b = e % nb;
+    double t = 0.0, q = 0.0;
+    if (a < n && b < n) {
+      const int c = n - 1 - b;
+      t = -2.0 * Pk[a <= c ? pk_idx(np, a, c) : pk_idx(np, c, a)];
+      q = a <= b ? -R[a * n + b] : 0.0;
+    }
+    Bt[e] = t;
+    Bq[e] = q;
+  }
+  for (int e = threadIdx.x; e < pk_size(nps); e += blockDim.x) {
+    int a = 0;
+    while (pk_row(nps, a + 1) <= e) ++a;
+    const int b = a + (e - pk_row(nps, a));
+    U[e] = b < n ? R[(n - 1 - b) * n + (n - 1 - a)] : (a == b ? 1.0 : 0.0);
+  }
+}
+
+struct BwTcPlan {
+  int np, nps, npz, nb, kw, sms, grid_g, stride_g;
+  size_t st, z0, z1, partials, G, colmax, M, Pk, rk, w, Bt, Bq, U, tcr, total;
+};
+
+static int bwt_plan(int64_t m, int n, BwTcPlan* p) {
+  p->np = bw_padded(n);
+  if (!p->np || m > (int64_t)1 << 31) return SCQR3_E_UNSUPPORTED;  // n <= 128; the Gram's row limit
+  if (tc_kernels_ready(&p->sms) != SCQR3_OK) return SCQR3_E_CUDA;
+  p->nps = n <= 64 ? 64 : 128;
+  p->npz = 2 * n <= 64 ? 64 : 2 * n <= 128 ? 128 : 256;
+  p->nb = (n + 31) / 32 * 32;
+  p->kw = n <= 16 ? 16 : 32;
+  p->grid_g = tc_grid(m, p->npz, p->sms);
+  p->stride_g = pk_size(p->npz) + 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = a256(off + bytes);
+    return o;
+  };
+  const size_t NN = (size_t)p->np * p->np;
+  p->st = take(sizeof(DevState));
+  p->z0 = take(sizeof(double) * (size_t)m * 2 * n);
+  p->z1 = take(sizeof(double) * (size_t)m * 2 * n);
+  p->partials = take(sizeof(double) * (size_t)p->grid_g * p->stride_g);
+  p->G = take(sizeof(double) * p->stride_g);
+  p->colmax = take(sizeof(unsigned long long) * 256);
+  p->M = take(sizeof(double) * NN);
+  p->Pk = take(sizeof(double) * pk_size(p->np));
+  p->rk = take(sizeof(double) * pk_size(p->np));
+  p->w = take(sizeof(double) * NN * 6);
+  p->Bt = take(sizeof(double) * p->nb * p->nb);
+  p->Bq = take(sizeof(double) * p->nb * p->nb);
+  p->U = take(sizeof(double) * pk_size(p->nps));
+  p->tcr = take(sizeof(double) * 8 * pk_size(32));
+  p->total = off;
+  return SCQR3_OK;
+}
+
+static Params bwt_params(int64_t m, int n, int np) {
+  Params P{};
+  P.m = m;
+  P.n = n;
+  P.np = np;
+  P.max_passes = SCQR3_MAX_PASSES;
+  P.tc = 1;
+  P.solve_only = 1;
+  set_options(&P, nullptr);
+  return P;
+}
+
+// (Y J) U = T J row by row: src = T J, dst = Y J (Eq. (backward2) with U).
+static void bwt_substitute(const BwTcPlan& p, cudaStream_t s, const Params& Ps, const double* src, int64_t lds,
+                           double* dst, int64_t ldd, const double* U, double* tcr, double* partials, DevState* st) {
+  const int n = Ps.n;
+  if (fused_solve_selected(n)) {
+    launch_tc_fused(p.sms, s, src, lds, dst, ldd, Ps, 0, U, nullptr, st);
+    return;
+  }
+  const int w = n <= 64 ? 16 : 32, nblk = (n + w - 1) / w;
+  launch_tc_split_r(s, U, p.nps, n, w, 0, st, tcr);
+  for (int J = 0; J < nblk; ++J) {
+    const int wj = n - w * J < w ? n - w * J : w;
+    const int npj = wj <= 16 ? 16 : 32;
+    Params PJ = Ps;
+    PJ.n = wj;
+    PJ.np = npj;
+    const double* in = J == 0 ? src : dst + w * J;
+    const int64_t ldin = J == 0 ? lds : ldd;
+    launch_pass(npj, pass_kernel_grid(npj, Ps.m), s, in, ldin, dst + w * J, ldd, PJ, 0, tcr + J * pk_size(32),
+                nullptr, partials, p.stride_g, st);
+    for (int c0 = w * (J + 1); c0 < n; c0 += 32) {
+      const int n1 = n - c0 < 32 ? n - c0 : 32;
+      const double* x1 = J == 0 ? src + c0 : dst + c0;
+      const int64_t ldx1 = J == 0 ? lds : ldd;
+      launch_tc_update(p.sms, s, w, dst + w * J, ldd, x1, ldx1, dst + c0, ldd, Ps.m, n1, 0, U, p.nps, w * J, c0, 0,
+                       w, st, Ps.wait_ns);
+    }
+  }
+}
+
+static void bwt_run(const BwTcPlan& p, cudaStream_t s, const double* Q, int64_t m, int n, int64_t ldq,
+                    const double* Rpass, int passes, const double* dQ, int64_t lddq, const double* dR, double* dX,
+                    int64_t lddx, char* ws, int* status) {
+  DevState* st = (DevState*)(ws + p.st);
+  double* Z[2] = {(double*)(ws + p.z0), (double*)(ws + p.z1)};
+  double* partials = (double*)(ws + p.partials);
+  double* G = (double*)(ws + p.G);
+  unsigned long long* colmax = (unsigned long long*)(ws + p.colmax);
+  double* M = (double*)(ws + p.M);
+  double* Pk = (double*)(ws + p.Pk);
+  double* rk = (double*)(ws + p.rk);
+  double* w = (double*)(ws + p.w);
+  double* Bt = (double*)(ws + p.Bt);
+  double* Bq = (double*)(ws + p.Bq);
+  double* U = (double*)(ws + p.U);
+  double* tcr = (double*)(ws + p.tcr);
+  const int64_t ldz = 2 * (int64_t)n;
+  const Params Pg = bwt_params(m, 2 * n, p.npz);
+  const Params Ps = bwt_params(m, n, p.nps);
+  const int pg = p.sms * 8;
+  auto gram = [&](const double* z) {  // G = Z^T Z (packed npz), through the partial slots
+    launch_tc_gram(p.grid_g, p.sms, s, z, ldz, Pg, -1, colmax, partials, p.stride_g, st, 0, nullptr, 0, 1);
+    launch_reduce(s, partials, p.grid_g, p.stride_g, G, nullptr, -1);
+  };
+  bwt_init_kernel<<<1, 32, 0, s>>>(st);
+  bwt_pack_kernel<<<pg, 256, 0, s>>>(0, m, n, Q, ldq, dQ, lddq, Z[0], nullptr, 0);
+  gram(Z[0]);
+  int cur = 0;
+  for (int k = passes; k >= 1; --k) {
+    double* A = Z[cur];
+    double* B = Z[cur ^ 1];
+    bwt_gram_to_m_kernel<<<1, 1024, 0, s>>>(G, p.npz, n, p.np, M);
+    bw_small(p.np, s, k, passes, n, Rpass, dR, M, w, Pk, rk);
+    bwt_mats_kernel<<<1, 1024, 0, s>>>(k, n, Rpass, Pk, p.np, p.nb, Bt, Bq, p.nps, U);
+    // t J = Qbar_k J - Q_k Bt, in place in the right half of A
+    for (int J = 0; J * p.kw < n; ++J) {
+      const int ky = n - J * p.kw < p.kw ? n - J * p.kw : p.kw;
+      for (int c0 = 0; c0 < n; c0 += 32) {
+        const int n1 = n - c0 < 32 ? n - c0 : 32;
+        launch_tc_update(p.sms, s, p.kw, A + J * p.kw, ldz, A + n + c0, ldz, A + n + c0, ldz, m, n1, 0, Bt, 0,
+                         J * p.kw, c0, p.nb, ky, st, Ps.wait_ns);
+      }
+    }
+    // Q_{k-1} = Q_k R_k into the left half of B (rows of R_k up to the block's last column)
+    if (k > 1) {
+      for (int c0 = 0; c0 < n; c0 += 32) {
+        const int n1 = n - c0 < 32 ? n - c0 : 32;
+        for (int J = 0; J * p.kw < c0 + n1; ++J) {
+          const int ky = n - J * p.kw < p.kw ? n - J * p.kw : p.kw;
+          launch_tc_update(p.sms, s, p.kw, A + J * p.kw, ldz, J == 0 ? nullptr : B + c0, ldz, B + c0, ldz, m, n1,
+                           0, Bq, 0, J * p.kw, c0, p.nb, ky, st, Ps.wait_ns);
+        }
+      }
+    }
+    // Qbar_{k-1} J = (t J) U^{-1} into the right half of B
+    bwt_substitute(p, s, Ps, A + n, ldz, B + n, ldz, U, tcr, partials, st);
+    if (k > 1) gram(B);
+    cur ^= 1;
+  }
+  bwt_pack_kernel<<<pg, 256, 0, s>>>(1, m, n, nullptr, 0, nullptr, 0, Z[cur], dX, lddx);
+  if (status) cudaMemcpyAsync(status, &st->status, sizeof(int), cudaMemcpyDeviceToDevice, s);
+}
+
 }  // namespace scqr3
 
 using namespace scqr3;
@@ -385,9 +635,8 @@ extern "C" int scqr3_backward_workspace_bytes(int64_t m, int n, size_t* bytes) {
   return SCQR3_OK;
 }
 
-extern "C" int scqr3_backward(const double* Q, int64_t m, int n, int64_t ldq, const double* Rpass,
-                              int passes, const double* dQ, int64_t lddq, const double* dR, double* dX,
-                              int64_t lddx, void* workspace, size_t workspace_bytes, void* stream) {
+static int bw_args(const double* Q, int64_t m, int n, int64_t ldq, const double* Rpass, int passes,
+                   const double* dQ, int64_t lddq, const double* dX, int64_t lddx, const void* workspace) {
   if (!Q) return -1;
   if (m < n || m < 1) return -2;
   if (n < 1) return -3;
@@ -399,6 +648,14 @@ extern "C" int scqr3_backward(const double* Q, int64_t m, int n, int64_t ldq, co
   if (!dX) return -10;
   if (lddx < n) return -11;
   if (!workspace || ((uintptr_t)workspace & 255) != 0) return SCQR3_E_WORKSPACE;
+  return SCQR3_OK;
+}
+
+extern "C" int scqr3_backward(const double* Q, int64_t m, int n, int64_t ldq, const double* Rpass,
+                              int passes, const double* dQ, int64_t lddq, const double* dR, double* dX,
+                              int64_t lddx, void* workspace, size_t workspace_bytes, void* stream) {
+  const int a = bw_args(Q, m, n, ldq, Rpass, passes, dQ, lddq, dX, lddx, workspace);
+  if (a != SCQR3_OK) return a;
   BwPlan p;
   const int r = bw_plan(m, n, &p);
   if (r != SCQR3_OK) return r;
@@ -422,6 +679,44 @@ extern "C" int scqr3_backward(const double* Q, int64_t m, int n, int64_t ldq, co
     bw_rows(p, s, BW_PASS, k, m, n, nullptr, 0, nullptr, 0, qw, dX, lddx, Pk, rk, partials);
     if (k > 1) launch_reduce(s, partials, nparts, NN, M, nullptr, -1);
   }
+  if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
+  return SCQR3_OK;
+}
+
+extern "C" int scqr3_backward_workspace_bytes_ex(int64_t m, int n, const scqr3_opts* opts, size_t* bytes) {
+  if (!bytes) return -4;
+  if (n < 1) return -2;
+  if (m < n) return -1;
+  const int prec = opts ? opts->precision : SCQR3_PREC_FP64;
+  if (prec == SCQR3_PREC_FP64) return scqr3_backward_workspace_bytes(m, n, bytes);
+  if (prec != SCQR3_PREC_TC) return SCQR3_E_UNSUPPORTED;
+  BwTcPlan p;
+  const int r = bwt_plan(m, n, &p);
+  if (r != SCQR3_OK) return r;
+  *bytes = p.total;
+  return SCQR3_OK;
+}
+
+extern "C" int scqr3_backward_ex(const double* Q, int64_t m, int n, int64_t ldq, const double* Rpass, int passes,
+                                 const double* dQ, int64_t lddq, const double* dR, double* dX, int64_t lddx,
+                                 const scqr3_opts* opts, void* workspace, size_t workspace_bytes, int* status,
+                                 void* stream) {
+  const int prec = opts ? opts->precision : SCQR3_PREC_FP64;
+  if (prec != SCQR3_PREC_FP64 && prec != SCQR3_PREC_TC) return SCQR3_E_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == SCQR3_PREC_FP64) {
+    const int r = scqr3_backward(Q, m, n, ldq, Rpass, passes, dQ, lddq, dR, dX, lddx, workspace, workspace_bytes,
+                                 stream);
+    if (r == SCQR3_OK && status && cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return SCQR3_E_CUDA;
+    return r;
+  }
+  const int a = bw_args(Q, m, n, ldq, Rpass, passes, dQ, lddq, dX, lddx, workspace);
+  if (a != SCQR3_OK) return a;
+  BwTcPlan p;
+  const int r = bwt_plan(m, n, &p);
+  if (r != SCQR3_OK) return r;
+  if (workspace_bytes < p.total) return SCQR3_E_WORKSPACE;
+  bwt_run(p, s, Q, m, n, ldq, Rpass, passes, dQ, lddq, dR, dX, lddx, (char*)workspace, status);
   if (cudaGetLastError() != cudaSuccess) return SCQR3_E_CUDA;
   return SCQR3_OK;
 }

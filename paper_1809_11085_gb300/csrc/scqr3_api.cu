@@ -58,7 +58,7 @@ void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int w, i
                        double* rdiag);
 void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t ldy, const double* x1,
                       int64_t ldx, double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np,
-                      int r0, int c0, DevState* st, long long wait_ns);
+                      int r0, int c0, int ldb, int ky, DevState* st, long long wait_ns);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
                     const double* lt, int64_t blk0, int scan);
@@ -631,7 +631,7 @@ void tc_solve_rows(Call& c, int k, const double* rk, const double* src, int64_t 
       const double* x1 = J == 0 ? src + c0 : dst + c0;
       const int64_t ldx1 = J == 0 ? lds : ldd;
       launch_tc_update(sm_count(), c.s, w, dst + w * J, ldd, x1, ldx1, dst + c0, ldd, Pc.m, n1, k, rk, c.P.np,
-                       w * J, c0, c.st, c.P.wait_ns);
+                       w * J, c0, 0, w, c.st, c.P.wait_ns);
     }
   }
 }
@@ -709,6 +709,24 @@ int check_factor_pointers(const double* X, int64_t m, int n, int64_t ldx, const 
 }
 
 }  // namespace
+
+namespace scqr3 {
+
+// For the tensor-core adjoint (adjoint.cu), which runs the factorization's
+// kernels: their attributes set on the current device (once), its SM count,
+// the pass kernel's grid for m rows, and whether the one-sweep substitution
+// serves n columns.
+int tc_kernels_ready(int* sms) {
+  int gm = 0;
+  PassGeom geo;
+  if (device_geo(64, &gm, &geo) != cudaSuccess) return SCQR3_E_CUDA;
+  *sms = sm_count();
+  return SCQR3_OK;
+}
+int pass_kernel_grid(int np, int64_t m) { return pass_grid(np, m); }
+bool fused_solve_selected(int n) { return g_fused_solve.load() != 0 && tc_fused_supported(n); }
+
+}  // namespace scqr3
 
 extern "C" int scqr3_factor(const double* X, int64_t m, int n, int64_t ldx, const scqr3_B* B,
                             double* Q, int64_t ldq, double* R, double* Rpass, void* workspace,

@@ -152,14 +152,16 @@ __global__ void tc_split_r_kernel(const double* __restrict__ rk, int np, int n, 
   }
 }
 
-// x' = x - Y R01 for rows [0, m): y holds Y (K = 16 or 32 columns), x1 and q1
-// the n1 <= N columns to update of the pass's input and output (they may be
-// the same memory); R01 is rows r0 .. r0 + K - 1, columns c0 .. c0 + n1 - 1 of
-// R_k, packed np x np.
+// x' = x - Y R01 for rows [0, m): y holds Y (K = 16 or 32 columns, the first
+// ky of them read, the rest taken as zero), x1 and q1 the n1 <= N columns to
+// update of the pass's input and output (they may be the same memory; x1 null:
+// x = 0); R01 is rows r0 .. r0 + K - 1, columns c0 .. c0 + n1 - 1 of R_k,
+// packed np x np (ldb = 0), or of a dense row-major matrix with row stride ldb
+// (ldb > 0; the adjoint's products).
 template <int K, int N>
 __global__ void __launch_bounds__(tcs::THREADS + 32, 1)
 tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, int64_t ldx, double* q1, int64_t ldq,
-                 int64_t m, int n1, int pass, const double* __restrict__ rk, int np, int r0, int c0,
+                 int64_t m, int n1, int pass, const double* __restrict__ rk, int np, int r0, int c0, int ldb, int ky,
                  DevState* __restrict__ st, long long wait_ns) {
   using namespace tcs;
   using tc::smem_u32;
@@ -181,14 +183,16 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
   const int tis = tid & (SLOT_THREADS - 1);  // thread within the slot
   const int r = tis & (ROWS - 1);  // tile row and tensor-memory lane (warp w serves lanes 32 (w % 4) ..)
   const int hf = tis >> 7;         // which half of the row: K groups hf K/16 ..; columns N/2 hf ..
+  auto bval = [&](int k, int l) -> double {  // entry (k, l) of R01
+    return ldb > 0 ? rk[(int64_t)(r0 + k) * ldb + c0 + l] : rk[pk_idx(np, r0 + k, c0 + l)];
+  };
 
   // column scales of R01 (columns >= n1: zero)
   if (tid < 32) {
     unsigned long long mx = 0;
     if (tid < n1)
       for (int k = 0; k < K; ++k) {
-        const unsigned long long b =
-            (unsigned long long)__double_as_longlong(rk[pk_idx(np, r0 + k, c0 + tid)]) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(bval(k, tid)) & 0x7FFFFFFFFFFFFFFFull;
         mx = mx > b ? mx : b;
       }
     Eb[tid] = tc::split_exp(mx);
@@ -211,7 +215,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
     const int l = u & 31, kg = u >> 5;
     double v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = l < n1 ? rk[pk_idx(np, r0 + 8 * kg + q, c0 + l)] : 0.0;
+    for (int q = 0; q < 8; ++q) v[q] = l < n1 ? bval(8 * kg + q, l) : 0.0;
     tc::cut8(v, Eb[l], bbuf + (l >> 3) * SBO + kg * LBO + (l & 7) * 16, BPLANE);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -259,7 +263,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
           const int rr = (tis + SLOT_THREADS * it) / K, c = tis % K;
-          const bool ok = r0n + rr < m;
+          const bool ok = r0n + rr < m && c < ky;
           const double* g = ok ? y + (r0n + rr) * ldy + c : y;
           asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
                        :: "r"(smem_u32(buf + rr * YPLD + c)), "l"(g), "r"(ok ? 8 : 0) : "memory");
@@ -288,7 +292,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
           const int rr = (tis + SLOT_THREADS * it) / K;
-          t[it] = rr < rows ? y[(row0 + rr) * ldy + (tis % K)] : 0.0;
+          t[it] = (rr < rows && (tis % K) < ky) ? y[(row0 + rr) * ldy + (tis % K)] : 0.0;
         }
 #pragma unroll
         for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) / K) * YLD + (tis % K)] = t[it];
@@ -323,7 +327,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
           const int rr = (tis + SLOT_THREADS * it) / N;
-          t[it] = (rr < rows && c < n1) ? x1[(row0 + rr) * ldx + c] : 0.0;
+          t[it] = (x1 && rr < rows && c < n1) ? x1[(row0 + rr) * ldx + c] : 0.0;
         }
 #pragma unroll
         for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) / N) * YLD + c] = t[it];
@@ -412,16 +416,17 @@ void launch_tc_split_r(cudaStream_t s, const double* rk, int np, int n, int w, i
   tc_split_r_kernel<<<1, 256, 0, s>>>(rk, np, n, w, pass, st, rdiag);
 }
 
-// x1' = x1 - Y R_JK over rows [0, m); Y has k = 16 or 32 columns, n1 in 1 .. 32 columns are
-// updated; R_JK at (r0, c0) of R_k (packed np).
+// x1' = x1 - Y R_JK over rows [0, m); Y has k = 16 or 32 columns (the first
+// ky read), n1 in 1 .. 32 columns are updated; R_JK at (r0, c0) of R_k (packed
+// np; ldb > 0: a dense matrix with row stride ldb).
 void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t ldy, const double* x1,
                       int64_t ldx, double* q1, int64_t ldq, int64_t m, int n1, int pass, const double* rk, int np,
-                      int r0, int c0, DevState* st, long long wait_ns) {
+                      int r0, int c0, int ldb, int ky, DevState* st, long long wait_ns) {
   const int64_t tiles = (m + tcs::ROWS - 1) / tcs::ROWS;
   const int grid = (int)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
 #define SCQR3_UPD(KV, NV)                                                                                   \
   tc_update_kernel<KV, NV><<<grid, tcs::THREADS + 32, tcs::UGeo<KV>::SMEM, s>>>(y, ldy, x1, ldx, q1, ldq, m, n1, \
-                                                                             pass, rk, np, r0, c0, st, wait_ns)
+                                                                             pass, rk, np, r0, c0, ldb, ky, st, wait_ns)
   if (k == 16) {
     if (n1 <= 16) SCQR3_UPD(16, 16);
     else SCQR3_UPD(16, 32);

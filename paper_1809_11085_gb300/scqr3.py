@@ -148,6 +148,11 @@ def lib():
         L.scqr3_backward_workspace_bytes.restype = i32
         L.scqr3_backward.argtypes = [p, i64, i32, i64, p, i32, p, i64, p, p, i64, p, sz, p]
         L.scqr3_backward.restype = i32
+        L.scqr3_backward_workspace_bytes_ex.argtypes = [i64, i32, ctypes.POINTER(_Opts), ctypes.POINTER(sz)]
+        L.scqr3_backward_workspace_bytes_ex.restype = i32
+        L.scqr3_backward_ex.argtypes = [p, i64, i32, i64, p, i32, p, i64, p, p, i64, ctypes.POINTER(_Opts), p, sz,
+                                        p, p]
+        L.scqr3_backward_ex.restype = i32
         L.scqr3_shard_sizes.argtypes = [i64, i32, ctypes.POINTER(_B), ctypes.POINTER(_Opts), ctypes.POINTER(sz),
                                         ctypes.POINTER(sz)]
         L.scqr3_shard_sizes.restype = i32
@@ -371,50 +376,65 @@ def timing_end(capacity: int = 4096):
 
 # --------------------------------------------------------------------------- adjoint
 
-def backward_workspace_bytes(m: int, n: int) -> int:
+def backward_workspace_bytes(m: int, n: int, precision: int = PREC_FP64) -> int:
     out = ctypes.c_size_t(0)
-    r = lib().scqr3_backward_workspace_bytes(int(m), int(n), ctypes.byref(out))
+    _, op = _opts(0, 0.0, precision)
+    r = lib().scqr3_backward_workspace_bytes_ex(int(m), int(n), op, ctypes.byref(out))
     if r != OK:
-        raise ScqrError(r, "scqr3_backward_workspace_bytes")
+        raise ScqrError(r, "scqr3_backward_workspace_bytes_ex")
     return out.value
 
 
 class BackwardWorkspace:
-    def __init__(self, m, n, device=None):
+    """Device workspace of the adjoint for (m, n) and a precision (PREC_FP64:
+    the FP64 row kernel; PREC_TC: the row work on the tensor cores), with the
+    device status word that scqr3_backward_ex writes."""
+
+    def __init__(self, m, n, device=None, precision: int = PREC_FP64):
         import torch
 
-        out = ctypes.c_size_t(0)
-        r = lib().scqr3_backward_workspace_bytes(int(m), int(n), ctypes.byref(out))
-        if r != OK:
-            raise ScqrError(r, "scqr3_backward_workspace_bytes")
-        self.bytes = out.value
+        self.precision = int(precision)
+        self.bytes = backward_workspace_bytes(m, n, self.precision)
         self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=device or "cuda")
         self.ptr = (self.buf.data_ptr() + 255) & ~255
+        self.status = torch.zeros(1, dtype=torch.int32, device=device or "cuda")
+
+    def last_status(self) -> int:
+        """Status of the last adjoint run on this workspace (synchronizes)."""
+        return int(self.status.item())
 
 
 def backward(Q, Rpass, passes: int, dQ, dR=None, *, dX=None, workspace: BackwardWorkspace | None = None,
-             stream=None):
-    """dL/dX of scqr3_factor given dL/dQ and dL/dR, through scqr3_backward."""
+             stream=None, precision: int | None = None):
+    """dL/dX of scqr3_factor given dL/dQ and dL/dR, through scqr3_backward_ex.
+
+    precision: PREC_FP64 or PREC_TC (default: the workspace's, else PREC_FP64).
+    """
     import torch
 
     _check_mat(Q, "Q")
     _check_mat(dQ, "dQ")
     m, n = Q.shape
+    if precision is None:
+        precision = workspace.precision if workspace is not None else PREC_FP64
     if dX is None:
         dX = torch.empty((m, n), dtype=torch.float64, device=Q.device)
     _check_mat(dX, "dX")
     if dR is not None:
         dR = dR.contiguous()
     if workspace is None:
-        workspace = BackwardWorkspace(m, n, device=Q.device)
+        workspace = BackwardWorkspace(m, n, device=Q.device, precision=precision)
+    elif workspace.precision != precision:
+        raise ValueError("the workspace was sized for another precision")
     if stream is None:
         stream = torch.cuda.current_stream(Q.device).cuda_stream
-    r = lib().scqr3_backward(Q.data_ptr(), m, n, Q.stride(0), Rpass.data_ptr(), int(passes),
-                             dQ.data_ptr(), dQ.stride(0), dR.data_ptr() if dR is not None else None,
-                             dX.data_ptr(), dX.stride(0), workspace.ptr, workspace.bytes,
-                             ctypes.c_void_p(stream))
+    _, op = _opts(0, 0.0, precision)
+    r = lib().scqr3_backward_ex(Q.data_ptr(), m, n, Q.stride(0), Rpass.data_ptr(), int(passes),
+                                dQ.data_ptr(), dQ.stride(0), dR.data_ptr() if dR is not None else None,
+                                dX.data_ptr(), dX.stride(0), op, workspace.ptr, workspace.bytes,
+                                workspace.status.data_ptr(), ctypes.c_void_p(stream))
     if r != OK:
-        raise ScqrError(r, "scqr3_backward")
+        raise ScqrError(r, "scqr3_backward_ex")
     return dX
 
 
@@ -425,13 +445,14 @@ def _autograd_function():
         """(Q, R) = shifted CholeskyQR3(X), differentiable; saves Q and the per-pass R_k."""
 
         @staticmethod
-        def forward(ctx, X, max_passes=0):
+        def forward(ctx, X, max_passes=0, precision=PREC_FP64):
             n = X.shape[1]
             Rpass = torch.zeros((MAX_PASSES, n, n), dtype=torch.float64, device=X.device)
-            Q, R, info = factor(X.contiguous(), max_passes=max_passes, Rpass=Rpass)
+            Q, R, info = factor(X.contiguous(), max_passes=max_passes, Rpass=Rpass, precision=precision)
             if info.status not in (OK, E_MAXPASS):
                 raise ScqrError(info.status, "scqr3_factor")
             ctx.passes = info.passes
+            ctx.precision = backward_precision(precision)
             ctx.save_for_backward(Q, Rpass)
             ctx.info = info
             return Q, R
@@ -441,8 +462,11 @@ def _autograd_function():
             Q, Rpass = ctx.saved_tensors
             if dQ is None:
                 dQ = torch.zeros_like(Q)
-            dX = backward(Q, Rpass, ctx.passes, dQ.contiguous(), dR)
-            return dX, None
+            ws = BackwardWorkspace(*Q.shape, device=Q.device, precision=ctx.precision)
+            dX = backward(Q, Rpass, ctx.passes, dQ.contiguous(), dR, workspace=ws)
+            if ctx.precision != PREC_FP64 and ws.last_status() != OK:
+                raise ScqrError(ws.last_status(), "scqr3_backward_ex")
+            return dX, None, None
 
     return SCQR3
 
@@ -450,12 +474,24 @@ def _autograd_function():
 _SCQR3 = None
 
 
-def qr(X, max_passes: int = 0):
-    """Differentiable shifted CholeskyQR3: returns (Q, R) with X = QR."""
+def backward_precision(precision: int) -> int:
+    """The adjoint's form for a forward precision: the tensor-core adjoint for
+    the FP64-accurate tensor-core form with n <= 128, else the FP64 one."""
+    return PREC_TC if precision == PREC_TC else PREC_FP64
+
+
+def qr(X, max_passes: int = 0, precision: int = PREC_FP64):
+    """Differentiable shifted CholeskyQR3: returns (Q, R) with X = QR.
+
+    precision selects the forward form (scqr3_opts.precision); the adjoint
+    runs on the tensor cores after the PREC_TC form (n <= 128), else in FP64.
+    """
     global _SCQR3
     if _SCQR3 is None:
         _SCQR3 = _autograd_function()
-    return _SCQR3.apply(X, max_passes)
+    if precision == PREC_TC and X.shape[1] > 128:
+        raise ScqrError(E_UNSUPPORTED, "the adjoint takes n <= 128")
+    return _SCQR3.apply(X, max_passes, precision)
 
 
 # ----------------------------------------------------------------------------- row-partitioned form

@@ -129,3 +129,34 @@ def test_shard_argument_errors_are_reported_on_the_host(lib):
                                 None, None) == -1
     assert lib.scqr3_apply_pass(0, None, 1000, None, 1000, 16, 16, None, None, 16, None, None, None, 0, None,
                                 None, None) == -2
+
+
+def test_backward_options_are_checked_on_the_host(lib):
+    """scqr3_backward_ex / scqr3_backward_workspace_bytes_ex: the precision and
+    the shape limits of the tensor-core adjoint are rejected before any CUDA
+    call; argument codes follow the prototype (opts is argument 12)."""
+    from paper_1809_11085_gb300 import scqr3
+
+    out = ctypes.c_size_t(0)
+    for prec in (scqr3.PREC_MIXED, scqr3.PREC_MIXED_TC, 7):
+        o = scqr3._Opts(0, prec, 0.0)
+        assert lib.scqr3_backward_workspace_bytes_ex(1000, 16, ctypes.byref(o), ctypes.byref(out)) == \
+            scqr3.E_UNSUPPORTED
+        assert lib.scqr3_backward_ex(ctypes.c_void_p(256), 1000, 16, 16, ctypes.c_void_p(256), 3,
+                                     ctypes.c_void_p(256), 16, None, ctypes.c_void_p(256), 16, ctypes.byref(o),
+                                     ctypes.c_void_p(256), 1 << 30, None, None) == scqr3.E_UNSUPPORTED
+    o = scqr3._Opts(0, scqr3.PREC_TC, 0.0)
+    assert lib.scqr3_backward_workspace_bytes_ex(1000, 129, ctypes.byref(o), ctypes.byref(out)) == \
+        scqr3.E_UNSUPPORTED
+    assert lib.scqr3_backward_workspace_bytes_ex(2 ** 31 + 1, 8, ctypes.byref(o), ctypes.byref(out)) == \
+        scqr3.E_UNSUPPORTED
+    assert lib.scqr3_backward_workspace_bytes_ex(5, 8, ctypes.byref(o), ctypes.byref(out)) == -1
+    assert lib.scqr3_backward_workspace_bytes_ex(5, 0, ctypes.byref(o), ctypes.byref(out)) == -2
+    assert lib.scqr3_backward_workspace_bytes_ex(50, 8, ctypes.byref(o), None) == -4
+    args = [ctypes.c_void_p(256), 1000, 16, 16, ctypes.c_void_p(256), 3, ctypes.c_void_p(256), 16, None,
+            ctypes.c_void_p(256), 16, ctypes.byref(o), ctypes.c_void_p(256), 1 << 30, None, None]
+    for idx, bad, code in [(0, None, -1), (3, 8, -4), (4, None, -5), (5, 0, -6), (6, None, -7), (7, 3, -8),
+                           (9, None, -10), (10, 2, -11), (12, ctypes.c_void_p(8), scqr3.E_WORKSPACE)]:
+        a = list(args)
+        a[idx] = bad
+        assert lib.scqr3_backward_ex(*a) == code, (idx, code)
