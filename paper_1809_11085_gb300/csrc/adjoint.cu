@@ -400,7 +400,7 @@ void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t l
                       int r0, int c0, int ldb, int ky, DevState* st, long long wait_ns);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
-                    const double* lt, int64_t blk0, int scan);
+                    const double* lt, int64_t blk0, int scan, int offd_only);
 void launch_tc_fused(int sms, cudaStream_t s, const double* X, int64_t ldx, double* Q, int64_t ldq, const Params& P,
                      int pass, const double* rk, unsigned long long* colmax, DevState* st);
 void set_options(Params* P, const scqr3_opts* opts);
@@ -577,8 +577,13 @@ static void bwt_run(const BwTcPlan& p, cudaStream_t s, const double* Q, int64_t 
   const Params Pg = bwt_params(m, 2 * n, p.npz);
   const Params Ps = bwt_params(m, n, p.nps);
   const int pg = p.sms * 8;
-  auto gram = [&](const double* z) {  // G = Z^T Z (packed npz), through the partial slots
-    launch_tc_gram(p.grid_g, p.sms, s, z, ldz, Pg, -1, colmax, partials, p.stride_g, st, 0, nullptr, 0, 1);
+  // G = Z^T Z (packed npz) through the partial slots. The columns of Q_k fill
+  // whole 64-column blocks of Z when 64 divides n: then M J lies in the
+  // off-diagonal blocks alone, and only those are formed.
+  const int offd_only = n % 64 == 0 ? 1 : 0;
+  auto gram = [&](const double* z) {
+    launch_tc_gram(p.grid_g, p.sms, s, z, ldz, Pg, -1, colmax, partials, p.stride_g, st, 0, nullptr, 0, 1,
+                   offd_only);
     launch_reduce(s, partials, p.grid_g, p.stride_g, G, nullptr, -1);
   };
   bwt_init_kernel<<<1, 32, 0, s>>>(st);

@@ -61,7 +61,7 @@ void launch_tc_update(int sms, cudaStream_t s, int k, const double* y, int64_t l
                       int r0, int c0, int ldb, int ky, DevState* st, long long wait_ns);
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
-                    const double* lt, int64_t blk0, int scan);
+                    const double* lt, int64_t blk0, int scan, int offd_only);
 cudaError_t tc_fused_setup();
 bool tc_fused_supported(int n);
 void launch_tc_fused(int sms, cudaStream_t s, const double* X, int64_t ldx, double* Q, int64_t ldq, const Params& P,
@@ -543,7 +543,7 @@ int first_gram(Call& c, const double* X, int64_t ldx, int64_t r0, int64_t r1, in
   if (c.tc) {
     const int g = tc_grid(Pc.m, c.P.np, sm_count());
     launch_tc_gram(g, sm_count(), c.s, src, ldx, Pc, -1, c.colmax, part, c.L.part_stride, c.st, 0, c.lt,
-                   c.lt ? r0 / c.P.bs : 0, 1);
+                   c.lt ? r0 / c.P.bs : 0, 1, 0);
     return g;
   }
   if (c.P.np == 256) {
@@ -679,7 +679,7 @@ void after_pass_gram(Call& c, int k, const double* Q, int64_t ldq, double* out) 
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     // the mixed form keeps float pairs between passes
     launch_tc_gram(c.L.tc_grid, sm_count(), c.s, Q, ldq, c.P, k, c.colmax, c.partials, c.L.part_stride, c.st,
-                   c.mixed ? 1 : 0, c.lt, 0, (use_fused(c) && !c.lt) ? 0 : 1);
+                   c.mixed ? 1 : 0, c.lt, 0, (use_fused(c) && !c.lt) ? 0 : 1, 0);
   } else if (c.P.np == 256) {
     tick(c.s, SCQR3_KERNEL_GRAM, k + 1);
     launch_gram256(c.grid, c.s, Q, ldq, c.P, k, c.partials, c.L.part_stride, c.st);

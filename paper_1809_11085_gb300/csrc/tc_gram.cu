@@ -697,9 +697,11 @@ int tc_grid(int64_t m, int np, int sms) {
 // row 0 of src in block blk0.
 // scan = 0: colmax already holds the column maxima of src (the fused
 // substitution that wrote it emitted them), so the scan is skipped.
+// offd_only (np = 128, 256): only the off-diagonal 64-column block pairs are
+// formed (every CTA serves them; the diagonal blocks of the result are zero).
 void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_t lds, const Params& P, int pass,
                     unsigned long long* colmax, double* partials, int part_stride, DevState* st, int pairs,
-                    const double* lt, int64_t blk0, int scan) {
+                    const double* lt, int64_t blk0, int scan, int offd_only) {
   // the slots hold the packed np x np layout; np = 128 and 256 need a CTA per
   // block (3 and 10 blocks)
   const int nblk = P.np == 256 ? 10 : P.np == 128 ? 3 : 1;
@@ -737,6 +739,7 @@ void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_
   int gd = grid >= (nd + no) * g ? g : (10 * grid) / (10 * nd + 12 * no);
   if (gd < 1) gd = 1;
   if (grid - nd * gd < no) gd = (grid - no) / nd;  // every block gets a CTA (grid >= nblk)
+  if (offd_only) gd = 0;
   if (obl)
     tc_gram_kernel<32, true><<<grid, tc::THREADS + 32, tc::SMEM, s>>>(src, lds, P, pass, colmax, partials,
                                                                       part_stride, st, bulk, pairs, gd, lt, blk0);
