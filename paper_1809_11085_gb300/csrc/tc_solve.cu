@@ -16,9 +16,14 @@
 //    digits in [-64, 64] (the balanced split of tc_common.cuh); digit products
 //    are exact in FP32, and tile e of tensor memory sums the pairs (s, t) with
 //    s + t = e over the k columns: at most 8 * 32 * 64^2 = 2^20, exact;
-//  * per entry the tile sums fold exactly into int64, U = sum_{e<=3} D_e
-//    2^{7(3-e)} (< 2^41.1) and T = sum_{e>=4} D_e 2^{7(7-e)}, then
-//    W = 2^21 U + floor(T / 2^7) (truncation below 2^-56 of sigma_i tau_l);
+//  * per entry the tile sums fold exactly into
+//    W = sum_e D_e 2^{7(7-e)-7} = 2^21 U + floor(T / 2^7) with
+//    U = sum_{e<=3} D_e 2^{7(3-e)} and T = sum_{e>=4} D_e 2^{7(7-e)}
+//    (truncation below 2^-56 of sigma_i tau_l), formed pairwise in 32 bits:
+//    |D_e| <= 2^20, so D_e + 1.5 2^23 is exact in FP32 with bit pattern
+//    b_e = 0x4B400000 + D_e, and b_e 2^7 + b_{e+1} - 129 * 0x4B400000 =
+//    D_e 2^7 + D_{e+1} (mod 2^32; below 2^28 in magnitude); then W =
+//    P01 2^35 + P23 2^21 + P45 2^7 + floor(P67 / 2^7);
 //    sigma_i tau_l 2^-56 W is assembled as a double from the bits of W
 //    (integer operations), and x'_il = x_il - that, one FP64 subtraction per
 //    entry.
@@ -176,6 +181,7 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
   __shared__ __align__(8) uint64_t mdone[SLOTS];  // MMAs of the slot's tile done (tcgen05.commit)
   __shared__ uint32_t tslot;
   __shared__ int Eb[32];  // tau_l = 2^Eb[l]
+  __shared__ unsigned long long mxs[SLOTS][2][ROWS];  // K = 32: partial row maxima of the two half rows
   __shared__ volatile int err_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool producer = warp == THREADS / 32;
@@ -272,66 +278,92 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
     if (PREF) prefetch_y(tile_row0(slot), ypre);
+    // K = 32: rows of Y start on 32-byte boundaries (vector loads of half rows)
+    const bool yvec = ((uintptr_t)y & 31) == 0 && (ldy & 3) == 0;
     for (uint32_t j = 0;; ++j) {
       const int64_t row0 = tile_row0(2 * j + slot);
       if (slot_any(slot, row0 < 0 || err_sh)) break;
       const int rows = (int)((m - row0) < ROWS ? (m - row0) : ROWS);
-      const double* yb = ys;
-      int yld = YLD;
-      if (PREF) {
-        // the next tile of this slot into the other buffer; this tile's copies done
-        prefetch_y(tile_row0(2 * (j + 1) + slot), ypre + ((j + 1) & 1) * (ROWS * YPLD));
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        yb = ypre + (j & 1) * (ROWS * YPLD);
-        yld = YPLD;
-      } else {
-        // the tile's Y rows, coalesced (one row of K per warp or half warp),
-        // every load in flight before the first store
-        constexpr int IT = ROWS * K / SLOT_THREADS;
-        double t[IT];
-#pragma unroll
-        for (int it = 0; it < IT; ++it) {
-          const int rr = (tis + SLOT_THREADS * it) / K;
-          t[it] = (rr < rows && (tis % K) < ky) ? y[(row0 + rr) * ldy + (tis % K)] : 0.0;
-        }
-#pragma unroll
-        for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) / K) * YLD + (tis % K)] = t[it];
-      }
-      slot_sync(slot);
-      // the row's scale from all K values; this thread cuts its half
-      unsigned long long mx = 0;
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(yb[r * yld + c]) & 0x7FFFFFFFFFFFFFFFull;
-        mx = mx > b ? mx : b;
-      }
-      const bool finite = (mx >> 52) != 0x7FF;
-      const int E = finite ? tc::split_exp(mx) : 0;
-#pragma unroll
-      for (int kh = 0; kh < K / 16; ++kh) {
-        const int kg = (K / 16) * hf + kh;
-        double v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = yb[r * yld + 8 * kg + q];
-        tc::cut8(v, E, arow + kg * LBO, APLANE);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[slot])) : "memory");
-      slot_sync(slot);  // Y read by every thread of the slot
-      // the tile's rows of x while the tensor core works
+      // the tile's rows of x into ys by asynchronous copies (zeros past m, past
+      // n1 and for x1 null), in flight while Y is cut and multiplied (ys is
+      // free: the previous tile's stores from it ended at the loop's last barrier)
       {
         constexpr int IT = ROWS * N / SLOT_THREADS;
-        double t[IT];
         const int c = tis % N;
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
           const int rr = (tis + SLOT_THREADS * it) / N;
-          t[it] = (x1 && rr < rows && c < n1) ? x1[(row0 + rr) * ldx + c] : 0.0;
+          const bool ok = x1 && rr < rows && c < n1;
+          const double* g = ok ? x1 + (row0 + rr) * ldx + c : y;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
+                       :: "r"(smem_u32(ys + rr * YLD + c)), "l"(g), "r"(ok ? 8 : 0) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
+      unsigned long long mx = 0;
+      bool finite;
+      int E;
+      if constexpr (PREF) {
+        // the next tile of this slot into the other Y buffer; copy groups
+        // pending, oldest first: Y of this tile, x of this tile, Y of the next
+        prefetch_y(tile_row0(2 * (j + 1) + slot), ypre + ((j + 1) & 1) * (ROWS * YPLD));
+        asm volatile("cp.async.wait_group 2;" ::: "memory");
+        slot_sync(slot);
+        const double* yb = ypre + (j & 1) * (ROWS * YPLD);
+        // the row's scale from all K values; this thread cuts its half
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          const unsigned long long b =
+              (unsigned long long)__double_as_longlong(yb[r * YPLD + c]) & 0x7FFFFFFFFFFFFFFFull;
+          mx = mx > b ? mx : b;
+        }
+        finite = (mx >> 52) != 0x7FF;
+        E = finite ? tc::split_exp(mx) : 0;
+#pragma unroll
+        for (int kh = 0; kh < K / 16; ++kh) {
+          const int kg = (K / 16) * hf + kh;
+          double v[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[q] = yb[r * YPLD + 8 * kg + q];
+          tc::cut8(v, E, arow + kg * LBO, APLANE);
+        }
+      } else {
+        // this thread's half row of Y (columns 16 hf .. 16 hf + 15: one
+        // 128-byte line), straight from global memory; the row's scale from
+        // both halves (partial maxima exchanged through shared memory)
+        static_assert(K == 32, "half rows of 16 values");
+        const bool rok = r < rows;
+        const double* yr = y + (row0 + (rok ? r : 0)) * ldy + 16 * hf;
+        double yv[16];
+        if (yvec && rok && 16 * hf + 16 <= ky) {  // four 32-byte loads
+#pragma unroll
+          for (int c = 0; c < 16; c += 4)
+            asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+                         : "=d"(yv[c]), "=d"(yv[c + 1]), "=d"(yv[c + 2]), "=d"(yv[c + 3]) : "l"(yr + c) : "memory");
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) yv[c] = (rok && 16 * hf + c < ky) ? yr[c] : 0.0;
         }
 #pragma unroll
-        for (int it = 0; it < IT; ++it) ys[((tis + SLOT_THREADS * it) / N) * YLD + c] = t[it];
+        for (int c = 0; c < 16; ++c) {
+          const unsigned long long b = (unsigned long long)__double_as_longlong(yv[c]) & 0x7FFFFFFFFFFFFFFFull;
+          mx = mx > b ? mx : b;
+        }
+        mxs[slot][hf][r] = mx;
+        slot_sync(slot);
+        const unsigned long long m0 = mxs[slot][0][r], m1 = mxs[slot][1][r];
+        mx = m0 > m1 ? m0 : m1;
+        finite = (mx >> 52) != 0x7FF;
+        E = finite ? tc::split_exp(mx) : 0;
+        tc::cut8(yv, E, arow + (2 * hf) * LBO, APLANE);
+        tc::cut8(yv + 8, E, arow + (2 * hf + 1) * LBO, APLANE);
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&pfull[slot])) : "memory");
+      // this thread's copies of x done (the barrier below makes all of them visible)
+      if constexpr (PREF) asm volatile("cp.async.wait_group 1;" ::: "memory");
+      else asm volatile("cp.async.wait_group 0;" ::: "memory");
       const bool ok = tc::wait_parity(smem_u32(&mdone[slot]), j & 1, wait_ns);
       if (slot_any(slot, !ok)) {  // also: the tile of x is complete
         err_sh = 1;
@@ -339,27 +371,25 @@ tc_update_kernel(const double* __restrict__ y, int64_t ldy, const double* x1, in
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-      for (int c0 = hf * (N / 2); c0 < (hf + 1) * (N / 2); c0 += 8) {
-        long long U[8], T[8];
+      // four columns at a time: the 8 tile sums of each (one wait for all
+      // 32 words), folded pairwise in 32 bits (see the header)
+      constexpr uint32_t C129 = 0x4B400000u * 129u;  // mod 2^32
 #pragma unroll
-        for (int q = 0; q < 8; ++q) U[q] = T[q] = 0;
+      for (int c4 = hf * (N / 2); c4 < (hf + 1) * (N / 2); c4 += 4) {
+        uint32_t t[8][4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          uint32_t v[8];
-          tc::ld8(tq + 32 * e + c0, v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const int sh = e < 4 ? 7 * (3 - e) : 7 * (7 - e);
+        for (int e = 0; e < 8; ++e) tc::ld4(tq + 32 * e + c4, t[e]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const long long dv = (long long)__float2int_rn(__uint_as_float(v[q])) << sh;
-            if (e < 4) U[q] += dv;
-            else T[q] += dv;
-          }
-        }
+        for (int q = 0; q < 4; ++q) {
+          uint32_t b[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int l = c0 + q;
-          const long long W = (U[q] << 21) + (T[q] >> 7);
+          for (int e = 0; e < 8; ++e) b[e] = __float_as_uint(__uint_as_float(t[e][q]) + 12582912.0f);
+          const long long p01 = (int32_t)(b[0] * 128u + b[1] - C129), p23 = (int32_t)(b[2] * 128u + b[3] - C129);
+          const long long p45 = (int32_t)(b[4] * 128u + b[5] - C129), p67 = (int32_t)(b[6] * 128u + b[7] - C129);
+          const long long W = (long long)(((unsigned long long)p01 << 35) + ((unsigned long long)p23 << 21) +
+                                          ((unsigned long long)p45 << 7)) + (p67 >> 7);
+          const int l = c4 + q;
           const double upd = scaled_int(W, E + Eb[l] - 56);  // sigma_i tau_l 2^-56 W
           ys[r * YLD + l] = finite ? ys[r * YLD + l] - upd : (double)NAN;
         }

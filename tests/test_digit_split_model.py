@@ -354,7 +354,8 @@ def test_digit_fields_from_14_bit_chunks():
 
 
 def test_pairwise_fold_in_32_bits():
-    """The one-sweep substitution folds tile sums |D_e| <= 2^20 as
+    """The one-sweep substitution and the update kernel (K <= 32: at most 8
+    digit pairs x 32 columns x 64^2 per tile) fold tile sums |D_e| <= 2^20 as
     b_e = 0x4B400000 + D_e (the float bits of D_e + 1.5 2^23), pairs
     P = b_e 2^7 + b_(e+1) - 129 * 0x4B400000 in 32-bit wrap-around arithmetic
     (the true value below 2^28), and W = P01 2^35 + P23 2^21 + P45 2^7 +
