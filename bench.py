@@ -54,7 +54,7 @@ PROFILED_BLOCK_BYTES_PER_ROW = 210.3  # pass_kernel<16> on the first 16-column b
 # profiles/tc_gram_kernel_* and profiles/tc_solve_kernels_*; for the separate-launch substitution, the mean
 # over its two update launch shapes), valid for the sources they were taken on.
 PROFILED_TC = {"tc_solve": ("25eb56420f284aac", ("tc_common.cuh", "tc_solve.cu"), 478.7),
-               "tc_gram": ("87f50084639c569f", ("tc_common.cuh", "tc_gram.cu"), 518.8),
+               "tc_gram": ("ece5f37e2cc61b88", ("tc_common.cuh", "tc_gram.cu"), 518.8),
                "tc_fused": ("84d8d80f4c9a751a", ("tc_common.cuh", "tc_fused.cu"), 981.0)}
 
 
