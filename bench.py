@@ -50,25 +50,26 @@ PROFILED_KERNEL_SHA = "b447e14d15d0797f"
 PROFILED_BYTES_PER_ROW = 992.3
 PROFILED_SOLVE_BYTES_PER_ROW = 968.7
 PROFILED_BLOCK_BYTES_PER_ROW = 210.3  # pass_kernel<16> on the first 16-column block of a 64-column X
-# ncu DRAM bytes per row of the tensor-core kernels at 1048576 x 64 (profiles/tc_fused_solve_kernel_*,
-# profiles/tc_gram_kernel_* and profiles/tc_solve_kernels_*; for the separate-launch substitution, the mean
-# over its two update launch shapes), valid for the sources they were taken on.
-PROFILED_TC = {"tc_solve": ("25eb56420f284aac", ("tc_common.cuh", "tc_solve.cu"), 478.7),
-               "tc_gram": ("ece5f37e2cc61b88", ("tc_common.cuh", "tc_gram.cu"), 518.8),
-               "tc_fused": ("84d8d80f4c9a751a", ("tc_common.cuh", "tc_fused.cu"), 981.0)}
+# ncu DRAM bytes per row of one launch of the tensor-core kernels at 1048576 rows: the one-sweep
+# substitution and the Gram at n = 64 (profiles/tc_fused_solve_kernel_*, profiles/tc_gram_kernel_*), the
+# update kernel at n = 128, where every launch has 32 columns of Y and of x (profiles/tc_update_kernel_*);
+# valid for the sources they were taken on and the n they were taken at.
+PROFILED_TC = {"tc_solve": ("9b47d483893e89d6", ("tc_common.cuh", "tc_solve.cu"), 737.7, 128),
+               "tc_gram": ("ece5f37e2cc61b88", ("tc_common.cuh", "tc_gram.cu"), 518.8, 64),
+               "tc_fused": ("84d8d80f4c9a751a", ("tc_common.cuh", "tc_fused.cu"), 981.0, 64)}
 
 
 def profiled_tc_traffic(kind, m, n):
-    """DRAM bytes of one launch of a tensor-core kernel (64-column X), or None."""
+    """DRAM bytes of one launch of a tensor-core kernel at n columns, or None."""
     import hashlib
 
-    sha, files, per_row = PROFILED_TC[kind]
+    sha, files, per_row, n_prof = PROFILED_TC[kind]
     if sha is None:
         return None
     h = hashlib.sha256()
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_1809_11085_gb300", "csrc", f), "rb").read())
-    return per_row * m if h.hexdigest()[:16] == sha and n == 64 else None
+    return per_row * m if h.hexdigest()[:16] == sha and n == n_prof else None
 
 
 def parse():
@@ -88,9 +89,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--legs", default="all", choices=["all", "main", "csr", "none"],
+    ap.add_argument("--legs", default="all", choices=["all", "main", "csr", "backward", "none"],
                     help="main: only the headline workload; all: also the other configurations; "
-                         "csr: the headline plus the sparse-B leg alone")
+                         "csr: the headline plus the sparse-B leg alone; backward: the headline plus "
+                         "the adjoint legs at --m x --n")
     ap.add_argument("--csr-grid", type=int, default=2048,
                     help="side of the 2-D grid whose Laplacian is B in the sparse-B leg (m = side^2)")
     return ap.parse_args()
@@ -655,6 +657,8 @@ def run_gpu(args, rank, world, local_rank):
         legs = extra_legs(torch, dev, stream, args)
     elif args.legs == "csr":
         legs = {"oblique_csr": csr_leg(torch, dev, stream, args.csr_grid)}
+    elif args.legs == "backward":
+        legs = {"backward": backward_leg(torch, dev, stream, m, n)}
 
     accuracy = {"dR_vs_exact": dR_exact,
                 "exact_note": "||R - R_exact||_F / ||R_exact||_F, R_exact = R factor of diag(sigma) V^T "
@@ -800,6 +804,36 @@ def csr_leg(torch, dev, stream, side):
         "csr_gram_frac_fp64_peak": [gram_flops / (t * 1e-3) / 1e12 / FP64_PEAK_DERIVED_TFLOPS for t in gram_ms]}
 
 
+def backward_leg(torch, dev, stream, mm, nn):
+    """The adjoint of the mm x nn factorization (kappa 1e10, 3 passes): the FP64
+    adjoint and the tensor-core one on the same saved state."""
+    from paper_1809_11085_gb300 import scqr3
+    from paper_1809_11085_gb300.testmat import testmat_torch
+
+    X, _, _ = testmat_torch(mm, nn, 1e10, seed=1500, device=dev)
+    Rpass = torch.zeros((scqr3.MAX_PASSES, nn, nn), dtype=torch.float64, device=dev)
+    Q, R, inf = scqr3.factor(X, Rpass=Rpass)
+    dQ = torch.randn(X.shape, dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(3))
+    dR = torch.randn((nn, nn), dtype=torch.float64, device=dev)
+    del X
+    bws = scqr3.BackwardWorkspace(mm, nn, device=dev)
+    dX = torch.empty_like(Q)
+    ms = _time(torch, stream, lambda: scqr3.backward(Q, Rpass, inf.passes, dQ, dR, dX=dX, workspace=bws))
+    leg = {"workload": "adjoint of the %d x %d factorization (%d passes)" % (mm, nn, inf.passes),
+           "ms": round(ms, 2), "rows_per_s": mm / (ms * 1e-3),
+           "tflops": inf.passes * mm * 6 * nn * nn / (ms * 1e-3) / 1e12}
+    del bws
+    torch.cuda.empty_cache()
+    if nn <= 128:  # the same adjoint with its row work on the tensor cores
+        bwt = scqr3.BackwardWorkspace(mm, nn, device=dev, precision=scqr3.PREC_TC)
+        dXt = torch.empty_like(Q)
+        mst = _time(torch, stream, lambda: scqr3.backward(Q, Rpass, inf.passes, dQ, dR, dX=dXt, workspace=bwt))
+        leg["tc"] = {"ms": round(mst, 2), "rows_per_s": mm / (mst * 1e-3), "speedup": ms / mst,
+                     "status": bwt.last_status(),
+                     "dX_vs_fp64": (torch.linalg.matrix_norm(dXt - dX) / torch.linalg.matrix_norm(dX)).item()}
+    return leg
+
+
 def extra_legs(torch, dev, stream, args):
     """The other configurations, one factorization timed each (after one warm-up)."""
     from paper_1809_11085_gb300 import batched, scqr3
@@ -896,30 +930,7 @@ def extra_legs(torch, dev, stream, args):
     free()
 
     # backward pass at the headline size
-    mm, nn = 16777216, 64
-    X, _, _ = testmat_torch(mm, nn, 1e10, seed=1500, device=dev)
-    Rpass = torch.zeros((scqr3.MAX_PASSES, nn, nn), dtype=torch.float64, device=dev)
-    Q, R, inf = scqr3.factor(X, Rpass=Rpass)
-    dQ = torch.randn(X.shape, dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(3))
-    dR = torch.randn((nn, nn), dtype=torch.float64, device=dev)
-    del X
-    bws = scqr3.BackwardWorkspace(mm, nn, device=dev)
-    dX = torch.empty_like(Q)
-    ms = _time(torch, stream, lambda: scqr3.backward(Q, Rpass, inf.passes, dQ, dR, dX=dX, workspace=bws))
-    legs["backward"] = {"workload": "adjoint of the 16777216 x 64 factorization (3 passes)", "ms": round(ms, 2),
-                        "rows_per_s": mm / (ms * 1e-3),
-                        "tflops": inf.passes * mm * 6 * nn * nn / (ms * 1e-3) / 1e12}
-    del bws
-    free()
-    # the same adjoint with its row work on the tensor cores
-    bwt = scqr3.BackwardWorkspace(mm, nn, device=dev, precision=scqr3.PREC_TC)
-    dXt = torch.empty_like(Q)
-    mst = _time(torch, stream, lambda: scqr3.backward(Q, Rpass, inf.passes, dQ, dR, dX=dXt, workspace=bwt))
-    legs["backward"]["tc"] = {"ms": round(mst, 2), "rows_per_s": mm / (mst * 1e-3), "speedup": ms / mst,
-                              "status": bwt.last_status(),
-                              "dX_vs_fp64": (torch.linalg.matrix_norm(dXt - dX) /
-                                             torch.linalg.matrix_norm(dX)).item()}
-    del Q, R, dQ, dX, dXt, bwt, Rpass
+    legs["backward"] = backward_leg(torch, dev, stream, 16777216, 64)
     free()
 
     # batched: 512 uneven matrices, one graph vs 512 single calls
