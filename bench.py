@@ -972,9 +972,49 @@ def extra_legs(torch, dev, stream, args):
                        "tc": {"graph_ms": round(tt, 2), "speedup_vs_fp64_graph": tb / tt,
                               "tflops_6mn2": fl / (tt * 1e-3) / 1e12, "worst_orth": worst_t,
                               "worst_dR_vs_fp64": dR_t, "all_ok": all(i.status == 0 for i in infos_t)}}
-    del bt, Xs, Rb
+    del bt, Rb
+    free()
+    legs["batched"]["backward"] = batched_backward(torch, dev, stream, Xs)
+    del Xs
     free()
     return legs
+
+
+def batched_backward(torch, dev, stream, Xs):
+    """The differentiable batch (batched.qr_batched): the backward pass of
+    loss = sum_i <W1_i, Q_i> + <W2_i, R_i> (W seeded Gaussian) over all the
+    matrices, after the FP64 and after the tensor-core forward (whose adjoint
+    runs on the tensor cores); timed from the start of autograd.grad to its end."""
+    from paper_1809_11085_gb300 import batched, scqr3
+
+    g = torch.Generator(dev).manual_seed(9)
+    W1 = [torch.randn(X.shape, dtype=torch.float64, device=dev, generator=g) for X in Xs]
+    W2 = [torch.randn((X.shape[1], X.shape[1]), dtype=torch.float64, device=dev, generator=g) for X in Xs]
+    out, grads = {}, {}
+    for name, prec, reps in (("fp64", scqr3.PREC_FP64, 1), ("tc", scqr3.PREC_TC, 2)):
+        best = float("inf")
+        for _ in range(reps):
+            Xg = [X.detach().requires_grad_(True) for X in Xs]
+            Qs, Rs = batched.qr_batched(Xg, precision=prec)
+            loss = sum((a * q).sum() + (b * r).sum() for a, q, b, r in zip(W1, Qs, W2, Rs))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record(stream)
+            gs = torch.autograd.grad(loss, Xg)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+            del Qs, Rs, loss, Xg
+        out[name] = {"ms": round(best, 2)}
+        grads[name] = gs
+        torch.cuda.empty_cache()
+    out["tc"]["speedup"] = out["fp64"]["ms"] / out["tc"]["ms"]
+    # both gradients carry the adjoint's O(n kappa u) error (kappa_i up to 1e12 here)
+    out["tc"]["worst_grad_vs_fp64"] = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+                                          for a, b in zip(grads["tc"], grads["fp64"]))
+    out["workload"] = ("backward of sum_i <W1_i, Q_i> + <W2_i, R_i> over the 512 matrices (autograd.grad: the "
+                       "per-matrix adjoints, one workspace, one stream)")
+    return out
 
 
 def main():
