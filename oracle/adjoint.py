@@ -37,6 +37,20 @@ def qr_adjoint(Q: np.ndarray, R: np.ndarray, dQ: np.ndarray, dR: np.ndarray | No
     return _solve_right_transpose(dQ + Q @ C, R)
 
 
+def qr_adjoint_rows(R: np.ndarray, dR: np.ndarray | None, chunks, Q_rows: np.ndarray,
+                    dQ_rows: np.ndarray) -> np.ndarray:
+    """Rows of ``qr_adjoint`` for a Q too tall to hold at once: M = R Rbar^T -
+    Qbar^T Q is summed over the row chunks (Q_c, Qbar_c) that ``chunks`` yields
+    (all rows, each once), then Xbar_i = (Qbar_i + Q_i copyltu(M)) R^{-T} for
+    the given rows Q_rows / dQ_rows. The same closed form as qr_adjoint."""
+    n = R.shape[0]
+    M = R @ (np.zeros((n, n)) if dR is None else dR).T
+    for Qc, dQc in chunks:
+        M = M - dQc.T @ Qc
+    C = np.tril(M) + np.tril(M, -1).T
+    return _solve_right_transpose(dQ_rows + Q_rows @ C, R)
+
+
 def phi(A: np.ndarray) -> np.ndarray:
     """Upper triangle of A with its diagonal halved."""
     return np.triu(A) - 0.5 * np.diag(np.diag(A))

@@ -290,3 +290,32 @@ def test_batched_tensor_core_gradients():
         ref = qr_adjoint(Q.detach().cpu().numpy(), R.detach().cpu().numpy(), W.cpu().numpy(), V.cpu().numpy())
         rel = np.linalg.norm(g.cpu().numpy() - ref) / np.linalg.norm(ref)
         assert rel < 50 * n * 1e6 * U, (m, n, rel)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e10])
+def test_full_size_sampled_rows_against_oracle(kappa):
+    """16,777,216 x 64 (the bench's workload): the tensor-core forward and
+    adjoint; 258 rows of dX (the first, the last and 256 seeded ones) against
+    the oracle's closed form, with M = R dR^T - dQ^T Q summed on the host over
+    1M-row chunks copied from the device."""
+    from oracle.adjoint import qr_adjoint_rows
+
+    m, n = 1 << 24, 64
+    X, _, _ = testmat_torch(m, n, kappa, seed=2800)
+    Rpass = torch.zeros((scqr3.MAX_PASSES, n, n), dtype=torch.float64, device="cuda")
+    Q, R, info = scqr3.factor(X, Rpass=Rpass, precision=TC)
+    del X
+    assert info.status == 0
+    g = torch.Generator("cuda").manual_seed(28)
+    dQ = torch.randn((m, n), dtype=torch.float64, device="cuda", generator=g)
+    dR = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    dX, st = tc_backward(Q, Rpass, info.passes, dQ, dR)
+    assert st == scqr3.OK
+    rows = np.concatenate([[0, m - 1], np.random.default_rng(29).choice(np.arange(1, m - 1), 256, replace=False)])
+    ri = torch.from_numpy(rows).cuda()
+    step = 1 << 20
+    chunks = ((Q[a:a + step].cpu().numpy(), dQ[a:a + step].cpu().numpy()) for a in range(0, m, step))
+    ref = qr_adjoint_rows(R.cpu().numpy(), dR.cpu().numpy(), chunks, Q[ri].cpu().numpy(), dQ[ri].cpu().numpy())
+    got = dX[ri].cpu().numpy()
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel < max(1e-12, 50 * n * kappa * U), rel

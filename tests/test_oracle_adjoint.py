@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle.adjoint import passwise_adjoint, qr_adjoint
+from oracle.adjoint import passwise_adjoint, qr_adjoint, qr_adjoint_rows
 from paper_1809_11085_gb300.testmat import testmat
 
 
@@ -85,3 +85,22 @@ def test_shift_is_irrelevant_to_the_map():
     Q2, R2, _, _ = oracle.scqr3(X, normx2=37.0)  # a much larger shift
     assert np.linalg.norm(R1 - R2) / np.linalg.norm(R1) < 1e-9
     assert np.linalg.norm(Q1 - Q2) < 1e-9
+
+
+def test_row_sampled_closed_form_equals_full():
+    """qr_adjoint_rows (M summed over row chunks, selected rows) gives the
+    selected rows of qr_adjoint, for uneven chunks and with or without dR."""
+    rng = np.random.default_rng(77)
+    m, n = 1000, 12
+    X = rng.standard_normal((m, n)) @ np.diag(np.logspace(0, -4, n))
+    Q, R = np.linalg.qr(X)
+    s = np.sign(np.diag(R))
+    Q, R = Q * s, (R.T * s).T
+    dQ = rng.standard_normal((m, n))
+    rows = np.array([0, 1, 17, 499, 998, 999])
+    for dR in (rng.standard_normal((n, n)), None):
+        full = qr_adjoint(Q, R, dQ, dR)
+        bounds = [0, 1, 300, 301, 777, m]
+        chunks = ((Q[a:b], dQ[a:b]) for a, b in zip(bounds[:-1], bounds[1:]))
+        got = qr_adjoint_rows(R, dR, chunks, Q[rows], dQ[rows])
+        assert np.allclose(got, full[rows], rtol=1e-12, atol=1e-12 * np.abs(full).max())
