@@ -489,7 +489,9 @@ def qr(X, max_passes: int = 0, precision: int = PREC_FP64):
     global _SCQR3
     if _SCQR3 is None:
         _SCQR3 = _autograd_function()
-    if precision == PREC_TC and X.shape[1] > 128:
+    import torch
+
+    if X.shape[1] > 128 and X.requires_grad and torch.is_grad_enabled():
         raise ScqrError(E_UNSUPPORTED, "the adjoint takes n <= 128")
     return _SCQR3.apply(X, max_passes, precision)
 
