@@ -404,6 +404,9 @@ void launch_tc_gram(int grid, int sms, cudaStream_t s, const double* src, int64_
 void launch_tc_fused(int sms, cudaStream_t s, const double* X, int64_t ldx, double* Q, int64_t ldq, const Params& P,
                      int pass, const double* rk, unsigned long long* colmax, DevState* st);
 void set_options(Params* P, const scqr3_opts* opts);
+bool tc_bwprod_supported(int n);
+void launch_tc_bwprod(int sms, cudaStream_t s, double* z, double* zn, int64_t m, const double* bt,
+                      const double* bq, int ldb, bool both, DevState* st, long long wait_ns);
 int tc_kernels_ready(int* sms);
 int pass_kernel_grid(int np, int64_t m);
 bool fused_solve_selected(int n);
@@ -596,23 +599,28 @@ static void bwt_run(const BwTcPlan& p, cudaStream_t s, const double* Q, int64_t 
     bwt_gram_to_m_kernel<<<1, 1024, 0, s>>>(G, p.npz, n, p.np, M);
     bw_small(p.np, s, k, passes, n, Rpass, dR, M, w, Pk, rk);
     bwt_mats_kernel<<<1, 1024, 0, s>>>(k, n, Rpass, Pk, p.np, p.nb, Bt, Bq, p.nps, U);
-    // t J = Qbar_k J - Q_k Bt, in place in the right half of A
-    for (int J = 0; J * p.kw < n; ++J) {
-      const int ky = n - J * p.kw < p.kw ? n - J * p.kw : p.kw;
-      for (int c0 = 0; c0 < n; c0 += 32) {
-        const int n1 = n - c0 < 32 ? n - c0 : 32;
-        launch_tc_update(p.sms, s, p.kw, A + J * p.kw, ldz, A + n + c0, ldz, A + n + c0, ldz, m, n1, 0, Bt, 0,
-                         J * p.kw, c0, p.nb, ky, st, Ps.wait_ns);
+    if (tc_bwprod_supported(n)) {
+      // both products from one cut of Q_k: t J in place, Q_{k-1} into the left half of B
+      launch_tc_bwprod(p.sms, s, A, B, m, Bt, Bq, p.nb, k > 1, st, Ps.wait_ns);
+    } else {
+      // t J = Qbar_k J - Q_k Bt, in place in the right half of A
+      for (int J = 0; J * p.kw < n; ++J) {
+        const int ky = n - J * p.kw < p.kw ? n - J * p.kw : p.kw;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+          const int n1 = n - c0 < 32 ? n - c0 : 32;
+          launch_tc_update(p.sms, s, p.kw, A + J * p.kw, ldz, A + n + c0, ldz, A + n + c0, ldz, m, n1, 0, Bt, 0,
+                           J * p.kw, c0, p.nb, ky, st, Ps.wait_ns);
+        }
       }
-    }
-    // Q_{k-1} = Q_k R_k into the left half of B (rows of R_k up to the block's last column)
-    if (k > 1) {
-      for (int c0 = 0; c0 < n; c0 += 32) {
-        const int n1 = n - c0 < 32 ? n - c0 : 32;
-        for (int J = 0; J * p.kw < c0 + n1; ++J) {
-          const int ky = n - J * p.kw < p.kw ? n - J * p.kw : p.kw;
-          launch_tc_update(p.sms, s, p.kw, A + J * p.kw, ldz, J == 0 ? nullptr : B + c0, ldz, B + c0, ldz, m, n1,
-                           0, Bq, 0, J * p.kw, c0, p.nb, ky, st, Ps.wait_ns);
+      // Q_{k-1} = Q_k R_k into the left half of B (rows of R_k up to the block's last column)
+      if (k > 1) {
+        for (int c0 = 0; c0 < n; c0 += 32) {
+          const int n1 = n - c0 < 32 ? n - c0 : 32;
+          for (int J = 0; J * p.kw < c0 + n1; ++J) {
+            const int ky = n - J * p.kw < p.kw ? n - J * p.kw : p.kw;
+            launch_tc_update(p.sms, s, p.kw, A + J * p.kw, ldz, J == 0 ? nullptr : B + c0, ldz, B + c0, ldz, m, n1,
+                             0, Bq, 0, J * p.kw, c0, p.nb, ky, st, Ps.wait_ns);
+          }
         }
       }
     }

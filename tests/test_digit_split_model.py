@@ -429,3 +429,82 @@ def test_gram_group_value_fits_and_rounds():
         assert abs(W) < 2 ** 62.2
         exact = Fraction(U, 2 ** 35) + Fraction(T, 2 ** 63)
         assert abs(Fraction(W, 2 ** 52) - exact) <= Fraction(1, 2 ** 53)
+
+
+def model_dot7(y, r):
+    """y . r as the adjoint's product kernel forms it: the seven leading digits
+    of each value, tile sums over the pairs s + t <= 6, W = sum_e D_e 2^(42 - 7e),
+    value 2^(Ey + Er - 56) W."""
+    Ey, Er = scale_exp(y), scale_exp(r)
+    if Ey is None or Er is None:
+        return Fraction(0), None, None, 0, 0
+    ya = [digits(v, Ey)[:7] for v in y]
+    rb = [digits(v, Er)[:7] for v in r]
+    D = [0] * 7
+    for a, b in zip(ya, rb):
+        for s in range(7):
+            for t in range(7 - s):
+                D[s + t] += a[s] * b[t]
+    W = sum(D[e] << (42 - 7 * e) for e in range(7))
+    return Fraction(W) * Fraction(2) ** (Ey + Er - 56), Ey, Er, max(abs(d) for d in D), W
+
+
+def test_seven_digit_products_of_the_adjoint_kernel():
+    """The adjoint's product kernel (K = 64, seven digits per value): every tile
+    sum below 2^21 (exact in FP32, and D_e + 1.5 2^23 exact), W below 2^61, and
+    the product within 2^-49 (sigma ||r||_1 + tau ||y||_1) + 64 * 7 * 2^-51
+    sigma tau of the exact dot product, on random, badly scaled and worst-case
+    vectors; the pairwise 32-bit fold gives the same W."""
+    k = 64
+    rng = np.random.default_rng(64)
+    C129 = (0x4B400000 * 129) & 0xFFFFFFFF
+
+    def pair(x, y):
+        p = (x * 128 + y - C129) & 0xFFFFFFFF
+        return p - (1 << 32) if p >= 1 << 31 else p
+
+    E = 1
+    worst = float(Fraction(sum(d << (7 * (DIGITS - 1 - s)) for s, d in enumerate([64] + [-64] * 7)))
+                  * Fraction(2) ** (E - 56))
+    cases = [([worst] * k, [worst] * k)]
+    for trial in range(120):
+        y = rng.standard_normal(k) * np.exp2(rng.integers(-40, 40, size=k) * (trial % 3 == 0))
+        r = rng.standard_normal(k) * np.exp2(rng.integers(-40, 40, size=k) * (trial % 4 == 0))
+        cases.append((list(map(float, y)), list(map(float, r))))
+    for y, r in cases:
+        got, Ey, Er, Dmax, W = model_dot7(y, r)
+        assert Dmax < 2 ** 21 and abs(W) < 2 ** 61
+        exact = sum(Fraction(a) * Fraction(b) for a, b in zip(y, r))
+        sig, tau = Fraction(2) ** Ey, Fraction(2) ** Er
+        bound = (Fraction(2) ** -49 * (sig * sum(Fraction(abs(b)) for b in r) + tau * sum(Fraction(abs(a)) for a in y))
+                 + 64 * 7 * Fraction(2) ** -51 * sig * tau)
+        assert abs(got - exact) <= bound
+        # the kernel's fold: b_e = 0x4B400000 + D_e, pairs in 32 bits, D_6 alone
+        ya = [digits(v, Ey)[:7] for v in y]
+        rb = [digits(v, Er)[:7] for v in r]
+        D = [sum(a[s] * b[e - s] for a, b in zip(ya, rb) for s in range(e + 1)) for e in range(7)]
+        bb = [(0x4B400000 + d) & 0xFFFFFFFF for d in D]
+        d6 = bb[6] - 0x4B400000
+        assert (pair(bb[0], bb[1]) << 35) + (pair(bb[2], bb[3]) << 21) + (pair(bb[4], bb[5]) << 7) + d6 == W
+
+
+def test_adjoint_product_mma_program():
+    """Group g's MMAs: digit s (A) against the planes t = 0 .. 6 - s of the
+    group side by side (N = 32 (7 - s)) from accumulator column 32 s; plane t
+    then lands in columns 32 (s + t) .. +31, tile e = s + t. Every pair with
+    s + t <= 6 is formed once per K step, the first MMA (s = 0) covers all 7
+    tiles, and the 7 tiles fit one 256-column accumulator (two in 512). For
+    the columns 0..31 of Q_{k-1} = Q_k R_k only the K steps 0, 1 (rows 0..31 of
+    R_k) can be non-zero: R_k is upper triangular."""
+    seen = {}
+    for s in range(7):
+        N = 32 * (7 - s)
+        assert N % 16 == 0 and 16 <= N <= 256
+        for t in range(N // 32):
+            col = 32 * s + 32 * t
+            assert col + 32 <= 224
+            seen[(s, t)] = col // 32
+    assert sorted(seen) == [(s, t) for s in range(7) for t in range(7) if s + t <= 6]
+    assert all(e == s + t for (s, t), e in seen.items())
+    R = np.triu(np.ones((64, 64)))
+    assert not R[32:, :32].any()
