@@ -366,13 +366,16 @@ int scqr3_backward(const double *Q, int64_t m, int n, int64_t ldq,
  * SCQR3_PREC_FP64).
  *  SCQR3_PREC_FP64  scqr3_backward (FP64 arithmetic throughout).
  *  SCQR3_PREC_TC    the same chain rule with the row work on the tensor
- *         cores, FP64-accurate like the factorization's SCQR3_PREC_TC form:
- *         the iterate is held as Z = [Q_k | Qbar_k J] (J reverses the column
- *         order); Qbar_k + 2 Q_k P_k and Q_{k-1} = Q_k R_k are products with
- *         n x n matrices through the exact digit split (each product within
- *         2^-56 of the scales of its row and column); Qbar_{k-1} R_k^T = t is
- *         the row-wise substitution of Eq. (backward2) with U = J R_k^T J
- *         applied to t J (FP64 diagonal blocks, backward stable row by row);
+ *         cores: the iterate is held as Z = [Q_k | Qbar_k J] (J reverses the
+ *         column order); Qbar_k + 2 Q_k P_k and Q_{k-1} = Q_k R_k are
+ *         products with n x n matrices through the exact digit split (each
+ *         product within 2^-56 of the scales of its row and column; within
+ *         2^-49 at n = 64, where one kernel forms both products from seven
+ *         digits per value, a perturbation of P_k and R_k of order
+ *         2^-49 of their norms, far inside the adjoint's O(n kappa u) error);
+ *         Qbar_{k-1} R_k^T = t is the row-wise substitution of Eq.
+ *         (backward2) with U = J R_k^T J applied to t J (FP64 diagonal
+ *         blocks, backward stable row by row);
  *         M_k J is the upper right block of the tensor-core Gram matrix of Z.
  *         n <= 128, m <= 2^31 (else SCQR3_E_UNSUPPORTED). The workspace
  *         holds two m x 2n iterates (16 m n doubles in all).
